@@ -1,0 +1,191 @@
+/*
+ * sdsl.h -- C ABI of the GB300 (sm_103a) implementation of the SDSL-Solver
+ * hot path (arXiv 2604.23979): the preconditioned Krylov solve of the sparse
+ * linear systems of an interior-point method.
+ *
+ * The problem statement is the paper's: one linear system A x = b per
+ * interior-point iteration (Algorithm 1), given either in normal-equations
+ * form S = B D^{-1} B^T (Eq. schur; here S = A diag(theta) A^T + rho I with
+ * theta = the IPM scaling D^{-1}) or in augmented form (Eq. augmented; here
+ * K = [[-diag(1/theta), A^T], [A, rho I]]).  The scaling changes every
+ * iteration (Sec. 3.4), which is what sdsl_update_diag models.
+ *
+ * Two parallel methods (Sec. 2.3, 2.4): Block Jacobi (per-block IC(0), PCG)
+ * and bordered block diagonal (per-block ILU(0) + dense Schur complement of
+ * the border, GMRES(m)).  Both build the preconditioner from the numerics-
+ * based filter (Eq. filter) and the diagonal correction (Eq. diagcorr).
+ *
+ * Conventions shared by every entry point:
+ *   - Sparse matrices are CSR: int64 row pointers (nrows+1 entries), int32
+ *     column indices sorted strictly ascending inside each row (no
+ *     duplicates), double values.  Violations return SDSL_ERR_ARG.
+ *   - Pointers named in sdsl_options.mem_space are either all host or all
+ *     device pointers; block pointers are always host arrays.
+ *   - Every call returns a status code; nothing is thrown across the ABI.
+ *     sdsl_last_error() gives a message for the calling thread.
+ *   - Calls on one handle are ordered on the handle's stream and are not
+ *     thread-safe; different handles may be used from different threads.
+ *   - The handle owns all device memory it allocates, until sdsl_free.  The
+ *     caller keeps ownership of every array it passes; setup copies them.
+ */
+#ifndef SDSL_H
+#define SDSL_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sdsl_handle_s* sdsl_handle;
+
+typedef enum {
+  SDSL_OK = 0,
+  SDSL_ERR_ARG = 1,           /* bad size, pointer, option or CSR structure */
+  SDSL_ERR_OOM = 2,           /* device allocation failed */
+  SDSL_ERR_CUDA = 3,          /* a CUDA runtime call failed */
+  SDSL_ERR_BREAKDOWN = 4,     /* factor pivot not positive/finite after every shift, or Krylov breakdown */
+  SDSL_ERR_NOT_CONVERGED = 5, /* maxit reached; x holds the last iterate */
+  SDSL_ERR_TIMEOUT = 6,       /* a bounded device wait gave up */
+  SDSL_ERR_STATE = 7          /* call out of order (e.g. solve before factor) */
+} sdsl_status;
+
+enum { SDSL_FORM_CSR = 0, SDSL_FORM_NORMAL = 1, SDSL_FORM_AUGMENTED = 2 };
+enum { SDSL_BJ_PCG = 0, SDSL_BBD_GMRES = 1 };
+enum { SDSL_MEM_HOST = 0, SDSL_MEM_DEVICE = 1 };
+
+typedef struct {
+  int form;                      /* SDSL_FORM_*: what sdsl_setup receives */
+  int method;                    /* SDSL_BJ_PCG (Sec. 2.3) or SDSL_BBD_GMRES (Sec. 2.4) */
+  int64_t nblocks;               /* number of diagonal blocks (Sec. 2.3 "partition") */
+  const int64_t* block_ptr;      /* host, nblocks+1 row offsets of the blocks; NULL = equal split.
+                                    Augmented form: row blocks of A (last entry = m - border) */
+  const int64_t* col_block_ptr;  /* host, augmented form only: column blocks of A (nblocks+1) */
+  int64_t border;                /* augmented form: number of linking rows of A (the last rows) */
+  double tau;                    /* filter threshold of Eq. (filter), >= 0; 1e-3 in Sec. 3.2 */
+  double delta;                  /* diagonal correction of Eq. (diagcorr), >= 0; 1e-12 in Sec. 3.3 */
+  double rho;                    /* regularisation: rho*I added to S (normal) or the (2,2) block (augmented) */
+  int factor_prec;               /* 64 or 32: storage/apply precision of the factors; the Krylov loop is FP64 */
+  double rtol;                   /* relative residual target ||b - A x|| / ||b|| (1e-8 in Sec. 4) */
+  int64_t maxit;                 /* iteration cap (products with the system matrix) */
+  int restart;                   /* GMRES restart length m */
+  double refactor_ratio;         /* reuse rule (Sec. 3.4): rebuild when iters > ratio * iters after the
+                                    last build; 0 disables automatic rebuilds */
+  int mem_space;                 /* SDSL_MEM_HOST or SDSL_MEM_DEVICE for matrix/vector pointers */
+  void* stream;                  /* cudaStream_t to order all work on; NULL = the legacy default stream */
+  int graph_iters;               /* Krylov iterations captured per CUDA graph launch; 0 = no graphs */
+  int tune;                      /* 1 = time candidate launch shapes at factor time and keep the fastest */
+} sdsl_options;
+
+typedef struct {
+  int64_t iters;          /* products with the system matrix in the last solve */
+  int64_t restarts;       /* PCG true-residual restarts / GMRES cycles */
+  int rebuilt;            /* 1 if the last solve was preceded by an automatic rebuild */
+  int status;             /* sdsl_status of the last solve */
+  double rel_res_true;    /* ||b - A x|| / ||b|| recomputed in FP64 at exit */
+  double rel_res_rec;     /* recurrence (or GMRES estimate) residual at exit */
+  double ms_setup, ms_factor, ms_solve, ms_update;   /* device time of the last call of each kind */
+  int64_t n;              /* system dimension */
+  int64_t nnz_system;     /* nnz of S or K */
+  int64_t nnz_precond;    /* nnz of the filtered, corrected preconditioner matrix P */
+  int64_t nnz_factor;     /* nnz of the triangular factor(s) used per application */
+  int64_t levels_lower, levels_upper;   /* total level count over blocks */
+  int64_t max_levels;     /* largest per-block level count */
+  int64_t shifted_blocks; /* blocks that needed a diagonal shift to factor */
+  int64_t builds;         /* factorizations since setup */
+  double bytes_per_iter;  /* algorithmic HBM bytes of one Krylov iteration (model) */
+} sdsl_stats;
+
+typedef struct {
+  int64_t n, nnz_system, nnz_precond, nblocks, border;
+  int64_t levels_lower, levels_upper;
+  int factored;
+} sdsl_info;
+
+/* Fill *o with the defaults: BJ-PCG, normal form, tau 1e-3, delta 1e-12,
+ * rho 1e-6, FP64 factors, rtol 1e-8, maxit 2000, restart 30, refactor_ratio
+ * 1.5, device pointers, default stream, graph_iters 16, tune 0. */
+void sdsl_default_options(sdsl_options* o);
+
+/* Create a handle and form the system matrix on the device.
+ *   SDSL_FORM_NORMAL:    A is m x n (rowptr/col/val), theta has n entries;
+ *                        S = A diag(theta) A^T + rho I (Eq. schur), dimension m.
+ *                        The pattern of S (symbolic product) is computed once
+ *                        here; the values again on every sdsl_update_diag.
+ *                        Rounding of S_ij, h = max(i,j), l = min(i,j): sum over
+ *                        shared columns k ascending of fma(fl(a_hk theta_k), a_lk, acc)
+ *                        from +0, then S_ii + rho; S is exactly symmetric.
+ *   SDSL_FORM_AUGMENTED: A is m x n with rows grouped by block and the
+ *                        options.border linking rows last, columns grouped by
+ *                        block; K (Eq. augmented) of dimension n+m is assembled
+ *                        in bordered block-diagonal order (Sec. 2.4): for each
+ *                        block its x unknowns then its lambda unknowns, border last.
+ *   SDSL_FORM_CSR:       the n x n system matrix is given directly (m = n);
+ *                        theta must be NULL.  For BJ-PCG it must be symmetric.
+ * Errors: SDSL_ERR_ARG (NULL/negative sizes, bad block pointers, unsorted
+ * CSR), SDSL_ERR_OOM, SDSL_ERR_CUDA.  *out is NULL on error. */
+sdsl_status sdsl_setup(const sdsl_options* opt, int64_t m, int64_t n, const int64_t* rowptr,
+                       const int32_t* col, const double* val, const double* theta, sdsl_handle* out);
+
+/* Build the preconditioner from the current system values (Algorithms 2-3):
+ * filter (Eq. filter, scope: inside the diagonal blocks for Block Jacobi, the
+ * whole matrix for BBD), diagonal correction (Eq. diagcorr), level sets of the
+ * block triangular solves, per-block IC(0) (BJ) or ILU(0) (BBD) with the
+ * shift-retry rule (a block whose factor breaks down is refactored with
+ * diagonal p_ii + alpha p_ii, alpha = 1e-3, 1e-2, 1e-1, 1), and for BBD the
+ * dense Schur complement of the border and its LU.  Errors: SDSL_ERR_BREAKDOWN
+ * if a block fails with every shift. */
+sdsl_status sdsl_factor(sdsl_handle h);
+
+/* Solve A x = b to options.rtol (Krylov loop in FP64 on the device).  b and x
+ * have the system dimension and live in options.mem_space; x is the initial
+ * guess on entry unless x0_zero != 0, and the solution on exit.  If a reuse
+ * rule is set and the last solve exceeded it, the preconditioner is rebuilt
+ * first (st->rebuilt).  st may be NULL.  Errors: SDSL_ERR_STATE before
+ * sdsl_factor, SDSL_ERR_NOT_CONVERGED (x = last iterate), SDSL_ERR_BREAKDOWN. */
+sdsl_status sdsl_solve(sdsl_handle h, const double* b, double* x, int x0_zero, sdsl_stats* st);
+
+/* New IPM scaling theta (Sec. 3.4 preconditioner reuse): recompute the system
+ * values on the device (normal: S on its fixed pattern; augmented: the x
+ * diagonal -1/theta), keep the factors.  theta has n entries in mem_space.
+ * SDSL_ERR_STATE for SDSL_FORM_CSR. */
+sdsl_status sdsl_update_diag(sdsl_handle h, const double* theta);
+
+/* Release everything the handle owns (stream-ordered).  NULL-safe. */
+sdsl_status sdsl_free(sdsl_handle h);
+
+/* Statistics of the handle (counters of the last calls). */
+sdsl_status sdsl_get_stats(sdsl_handle h, sdsl_stats* st);
+sdsl_status sdsl_get_info(sdsl_handle h, sdsl_info* info);
+
+/* Copy-outs for verification (host buffers, sizes from sdsl_get_info):
+ *  sdsl_export_system: the system matrix (n+1, nnz_system, nnz_system);
+ *  sdsl_export_precond: P after filter+correction (n+1, nnz_precond x2) and
+ *    the factor values on P's layout (IC(0): l_ij at j <= i; ILU(0): unit-L
+ *    multipliers at j < i, U at j >= i; factor_prec 32 exports the stored
+ *    FP32 values widened), plus the shift alpha used per block (nblocks);
+ *    any output pointer may be NULL;
+ *  sdsl_export_levels: which = 0 lower / 1 upper; nlev[nblocks] levels per
+ *    block, level_ptr[levels+1] offsets into level_rows[n] (rows ascending
+ *    inside a level, blocks in order);
+ *  sdsl_export_schur: BBD only, the dense border Schur complement (FP64,
+ *    row-major border x border). */
+sdsl_status sdsl_export_system(sdsl_handle h, int64_t* rowptr, int32_t* col, double* val);
+sdsl_status sdsl_export_precond(sdsl_handle h, int64_t* rowptr, int32_t* col, double* pval, double* fval,
+                                double* alpha);
+sdsl_status sdsl_export_levels(sdsl_handle h, int which, int32_t* nlev, int64_t* level_ptr, int32_t* level_rows);
+sdsl_status sdsl_export_schur(sdsl_handle h, double* sb);
+
+/* y = A x with the handle's system matrix (device pointers, FP64). */
+sdsl_status sdsl_spmv(sdsl_handle h, const double* x, double* y);
+
+/* z = M^{-1} r with the current preconditioner (device pointers, FP64). */
+sdsl_status sdsl_precond_apply(sdsl_handle h, const double* r, double* z);
+
+const char* sdsl_status_str(sdsl_status s);
+const char* sdsl_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SDSL_H */

@@ -1,0 +1,911 @@
+// api.cu -- the C ABI of include/sdsl.h: handle life cycle and host
+// orchestration of the kernels (setup -> factor -> solve, update_diag).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.cuh"
+#include "sdsl.h"
+
+using namespace sdsl;
+
+namespace {
+
+thread_local std::string g_err;
+
+sdsl_status fail(sdsl_status s, const std::string& msg) {
+  g_err = msg;
+  return s;
+}
+
+sdsl_status cuda_fail(cudaError_t e, const char* where) {
+  g_err = std::string(where) + ": " + cudaGetErrorString(e);
+  return e == cudaErrorMemoryAllocation ? SDSL_ERR_OOM : SDSL_ERR_CUDA;
+}
+
+#define TRY_CUDA(expr)                                   \
+  do {                                                   \
+    cudaError_t _e = (expr);                             \
+    if (_e != cudaSuccess) return cuda_fail(_e, #expr);  \
+  } while (0)
+
+#define TRY(expr)                          \
+  do {                                     \
+    sdsl_status _s = (expr);               \
+    if (_s != SDSL_OK) return _s;          \
+  } while (0)
+
+// Device allocations grouped by lifetime: `sys` lives until sdsl_free, `pc`
+// is replaced at every preconditioner build.
+struct Arena {
+  std::vector<void*> ptrs;
+  cudaStream_t st = nullptr;
+  template <typename T>
+  sdsl_status get(T** out, size_t count) {
+    *out = nullptr;
+    if (count == 0) count = 1;
+    void* p = nullptr;
+    cudaError_t e = cudaMallocAsync(&p, count * sizeof(T), st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync");
+    ptrs.push_back(p);
+    *out = static_cast<T*>(p);
+    return SDSL_OK;
+  }
+  void release() {
+    for (void* p : ptrs) cudaFreeAsync(p, st);
+    ptrs.clear();
+  }
+};
+
+void ensure_pool(int dev) {
+  static bool done[64] = {};
+  if (dev < 0 || dev >= 64 || done[dev]) return;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    uint64_t thr = UINT64_MAX;  // keep freed blocks for the next handle (serving, repeated setups)
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  }
+  done[dev] = true;
+}
+
+int pow2_lanes(double avg, double per_lane) {
+  int l = 2;
+  while (l < 32 && l * per_lane < avg) l <<= 1;
+  return l;
+}
+
+}  // namespace
+
+struct sdsl_handle_s {
+  sdsl_options opt{};
+  cudaStream_t st = nullptr;       // private stream (capturable)
+  cudaStream_t user = nullptr;     // caller's stream, joined at entry/exit
+  cudaEvent_t ev_a = nullptr, ev_b = nullptr, ev_join = nullptr;
+  int dev = 0, sms = 152;
+  int form = 0, method = 0;
+  int64_t m = 0, n = 0, N = 0;  // input rows/cols, system dimension
+  Arena sys, pc;
+  // input A (normal / augmented) and its transpose
+  int64_t a_nnz = 0;
+  int64_t *a_rp = nullptr, *at_rp = nullptr;
+  int32_t *a_ci = nullptr, *at_ci = nullptr;
+  double *a_v = nullptr, *at_v = nullptr, *theta = nullptr;
+  // system matrix
+  int64_t s_nnz = 0;
+  int64_t* s_rp = nullptr;
+  int32_t* s_ci = nullptr;
+  double* s_v = nullptr;
+  int64_t* xdiag = nullptr;  // augmented: position of every x diagonal
+  // blocks
+  int64_t nblocks = 0, border = 0;
+  std::vector<int64_t> h_bp;  // interior blocks over the system rows
+  int64_t* d_bp = nullptr;
+  int32_t* row_block = nullptr;
+  double* dvals = nullptr;
+  // preconditioner
+  int64_t p_nnz = 0;
+  int64_t *p_rp = nullptr, *p_diag = nullptr, *mir = nullptr;
+  int32_t* p_ci = nullptr;
+  double *p_v = nullptr, *F = nullptr, *dinv = nullptr;
+  float *Ff = nullptr, *dinvf = nullptr;
+  std::vector<double> h_alpha;
+  int32_t *lev_off_lo = nullptr, *lev_ptr_lo = nullptr, *lev_rows_lo = nullptr;
+  int32_t *lev_off_up = nullptr, *lev_ptr_up = nullptr, *lev_rows_up = nullptr;
+  std::vector<int32_t> h_nlev_lo, h_nlev_up;
+  int64_t tot_lo = 0, tot_up = 0;
+  // Krylov workspace
+  double *b = nullptr, *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr;
+  double *part = nullptr, *part_rr = nullptr, *part_rz = nullptr, *scalars = nullptr;
+  int64_t* scan_scratch = nullptr;
+  int* flag = nullptr;
+  PcgState* state = nullptr;
+  PcgState* h_state = nullptr;  // pinned
+  SpmvPlan A{};
+  TriSolve M{};
+  cudaGraphExec_t graph = nullptr;
+  int graph_iters = 0;
+  // reuse bookkeeping (Sec. 3.4)
+  bool factored = false, need_rebuild = false;
+  int64_t iters_post_build = -1;
+  sdsl_stats stats{};
+};
+
+namespace {
+
+struct Scope {  // join the caller's stream on entry and exit
+  sdsl_handle h;
+  explicit Scope(sdsl_handle hh) : h(hh) {
+    cudaEventRecord(h->ev_join, h->user);
+    cudaStreamWaitEvent(h->st, h->ev_join, 0);
+  }
+  ~Scope() {
+    cudaEventRecord(h->ev_join, h->st);
+    cudaStreamWaitEvent(h->user, h->ev_join, 0);
+  }
+};
+
+sdsl_status sync(sdsl_handle h, const char* where) {
+  cudaError_t e = cudaStreamSynchronize(h->st);
+  if (e != cudaSuccess) return cuda_fail(e, where);
+  return SDSL_OK;
+}
+
+template <typename T>
+sdsl_status to_host(sdsl_handle h, T* dst, const T* src, size_t count) {
+  if (count == 0) return SDSL_OK;
+  TRY_CUDA(cudaMemcpyAsync(dst, src, count * sizeof(T), cudaMemcpyDefault, h->st));
+  return SDSL_OK;
+}
+
+template <typename T>
+sdsl_status to_dev(sdsl_handle h, T* dst, const T* src, size_t count) {
+  if (count == 0) return SDSL_OK;
+  TRY_CUDA(cudaMemcpyAsync(dst, src, count * sizeof(T), cudaMemcpyDefault, h->st));
+  return SDSL_OK;
+}
+
+float elapsed(sdsl_handle h) {
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, h->ev_a, h->ev_b);
+  return ms;
+}
+
+// Scan counts[0..n) into row pointers in place (counts has n+1 entries) and
+// return the total on the host.
+sdsl_status scan_total(sdsl_handle h, int64_t* counts, int64_t n, int64_t* total) {
+  TRY_CUDA(exclusive_scan_i64(counts, n, h->scan_scratch, h->st));
+  TRY(to_host(h, total, counts + n, 1));
+  return sync(h, "scan");
+}
+
+sdsl_status alloc_workspace(sdsl_handle h) {
+  const int64_t N = h->N;
+  TRY(h->sys.get(&h->b, N));
+  TRY(h->sys.get(&h->x, N));
+  TRY(h->sys.get(&h->r, N));
+  TRY(h->sys.get(&h->z, N));
+  TRY(h->sys.get(&h->p, N));
+  TRY(h->sys.get(&h->q, N));
+  TRY(h->sys.get(&h->part, 152 * 32 + 64));
+  TRY(h->sys.get(&h->scalars, 16));
+  TRY(h->sys.get(&h->state, 1));
+  if (!h->h_state) TRY_CUDA(cudaMallocHost(&h->h_state, sizeof(PcgState)));
+  TRY_CUDA(cudaMemsetAsync(h->part, 0, sizeof(double) * (152 * 32 + 64), h->st));
+  TRY_CUDA(cudaMemsetAsync(h->state, 0, sizeof(PcgState), h->st));
+  TRY_CUDA(cudaMemsetAsync(h->x, 0, sizeof(double) * (size_t)N, h->st));
+  return SDSL_OK;
+}
+
+sdsl_status check_block_ptr(const int64_t* bp, int64_t nb, int64_t end) {
+  if (!bp) return fail(SDSL_ERR_ARG, "block_ptr is NULL");
+  if (bp[0] != 0) return fail(SDSL_ERR_ARG, "block_ptr[0] must be 0");
+  for (int64_t k = 0; k < nb; ++k)
+    if (bp[k + 1] < bp[k]) return fail(SDSL_ERR_ARG, "block_ptr must be non-decreasing");
+  if (bp[nb] != end) return fail(SDSL_ERR_ARG, "block_ptr[nblocks] does not match the dimension");
+  return SDSL_OK;
+}
+
+// Copy a CSR (rowptr/col/val in mem_space) to the device and validate it.
+sdsl_status load_csr(sdsl_handle h, int64_t nrows, int64_t ncols, const int64_t* rowptr, const int32_t* col,
+                     const double* val, int64_t** rp, int32_t** ci, double** v, int64_t* nnz) {
+  if (!rowptr) return fail(SDSL_ERR_ARG, "rowptr is NULL");
+  int64_t first = 0, last = 0;
+  TRY_CUDA(cudaMemcpy(&first, rowptr, sizeof(int64_t), cudaMemcpyDefault));
+  TRY_CUDA(cudaMemcpy(&last, rowptr + nrows, sizeof(int64_t), cudaMemcpyDefault));
+  if (first != 0 || last < 0) return fail(SDSL_ERR_ARG, "rowptr[0] must be 0 and rowptr[n] >= 0");
+  *nnz = last;
+  if (last > 0 && (!col || !val)) return fail(SDSL_ERR_ARG, "col/val is NULL");
+  if (last >= ((int64_t)1 << 40)) return fail(SDSL_ERR_ARG, "nnz too large");
+  TRY(h->sys.get(rp, nrows + 1));
+  TRY(h->sys.get(ci, last));
+  TRY(h->sys.get(v, last));
+  TRY(to_dev(h, *rp, rowptr, nrows + 1));
+  TRY(to_dev(h, *ci, col, last));
+  TRY(to_dev(h, *v, val, last));
+  TRY_CUDA(cudaMemsetAsync(h->flag, 0, sizeof(int), h->st));
+  TRY_CUDA(check_csr(nrows, ncols, *rp, *ci, h->flag, h->st));
+  int bad = 0;
+  TRY(to_host(h, &bad, h->flag, 1));
+  TRY(sync(h, "check_csr"));
+  if (bad) return fail(SDSL_ERR_ARG, "CSR columns out of range or not strictly ascending in a row");
+  return SDSL_OK;
+}
+
+sdsl_status transpose_input(sdsl_handle h) {
+  TRY(h->sys.get(&h->at_rp, h->n + 1));
+  TRY(h->sys.get(&h->at_ci, h->a_nnz));
+  TRY(h->sys.get(&h->at_v, h->a_nnz));
+  int64_t* cursor = nullptr;
+  Arena tmp;
+  tmp.st = h->st;
+  TRY(tmp.get(&cursor, h->n + 1));
+  TRY_CUDA(transpose_csr(h->m, h->n, h->a_rp, h->a_ci, h->a_v, h->at_rp, h->at_ci, h->at_v, h->scan_scratch, h->st));
+  TRY_CUDA(transpose_fill(h->m, h->n, h->a_rp, h->a_ci, h->a_v, h->at_rp, h->at_ci, h->at_v, cursor, h->st));
+  tmp.release();
+  return SDSL_OK;
+}
+
+sdsl_status form_normal(sdsl_handle h) {
+  const int64_t m = h->m;
+  TRY(h->sys.get(&h->s_rp, m + 1));
+  int32_t* long_rows = nullptr;
+  Arena tmp;
+  tmp.st = h->st;
+  TRY(tmp.get(&long_rows, m));
+  TRY_CUDA(normal_symbolic_count(m, h->a_rp, h->a_ci, h->at_rp, h->at_ci, h->s_rp, long_rows, h->flag + 1, h->st));
+  int nlong = 0;
+  TRY(to_host(h, &nlong, h->flag + 1, 1));
+  TRY(sync(h, "symbolic count"));
+  TRY_CUDA(cudaMemsetAsync(h->flag + 2, 0, sizeof(int), h->st));
+  TRY_CUDA(normal_symbolic_long(false, nlong, long_rows, h->a_rp, h->a_ci, h->at_rp, h->at_ci, h->s_rp, nullptr,
+                                h->flag + 2, h->st));
+  TRY(scan_total(h, h->s_rp, m, &h->s_nnz));
+  int err = 0;
+  TRY(to_host(h, &err, h->flag + 2, 1));
+  TRY(sync(h, "symbolic long"));
+  if (err) { tmp.release(); return fail(SDSL_ERR_ARG, "a row of S has more than 16384 candidate entries"); }
+  TRY(h->sys.get(&h->s_ci, h->s_nnz));
+  TRY(h->sys.get(&h->s_v, h->s_nnz));
+  TRY_CUDA(normal_symbolic_fill(m, h->a_rp, h->a_ci, h->at_rp, h->at_ci, h->s_rp, h->s_ci, h->st));
+  TRY_CUDA(normal_symbolic_long(true, nlong, long_rows, h->a_rp, h->a_ci, h->at_rp, h->at_ci, h->s_rp, h->s_ci,
+                                h->flag + 2, h->st));
+  tmp.release();
+  TRY_CUDA(normal_values(m, h->a_rp, h->a_ci, h->a_v, h->at_rp, h->at_ci, h->at_v, h->theta, h->opt.rho, h->s_rp,
+                         h->s_ci, h->s_v, h->st));
+  return SDSL_OK;
+}
+
+sdsl_status form_augmented(sdsl_handle h, const int64_t* rbp, const int64_t* cbp) {
+  const int64_t m = h->m, n = h->n, nb = h->nblocks, N = m + n;
+  std::vector<int64_t> kbp(nb + 1);
+  kbp[0] = 0;
+  for (int64_t k = 0; k < nb; ++k) kbp[k + 1] = kbp[k] + (cbp[k + 1] - cbp[k]) + (rbp[k + 1] - rbp[k]);
+  h->h_bp = kbp;
+  int64_t *d_rbp, *d_cbp, *pos;
+  Arena tmp;
+  tmp.st = h->st;
+  TRY(tmp.get(&d_rbp, nb + 1));
+  TRY(tmp.get(&d_cbp, nb + 1));
+  TRY(tmp.get(&pos, N));
+  TRY(to_dev(h, d_rbp, rbp, nb + 1));
+  TRY(to_dev(h, d_cbp, cbp, nb + 1));
+  TRY(h->sys.get(&h->d_bp, nb + 1));
+  TRY(to_dev(h, h->d_bp, kbp.data(), nb + 1));
+  TRY_CUDA(bbd_positions(m, n, nb, d_rbp, d_cbp, h->d_bp, pos, h->st));
+  TRY(h->sys.get(&h->s_rp, N + 1));
+  TRY_CUDA(augmented_count(m, n, h->a_rp, h->at_rp, pos, h->s_rp, h->st));
+  TRY(scan_total(h, h->s_rp, N, &h->s_nnz));
+  TRY(h->sys.get(&h->s_ci, h->s_nnz));
+  TRY(h->sys.get(&h->s_v, h->s_nnz));
+  TRY(h->sys.get(&h->xdiag, n));
+  TRY_CUDA(augmented_fill(m, n, h->a_rp, h->a_ci, h->a_v, h->at_rp, h->at_ci, h->at_v, h->theta, h->opt.rho, pos,
+                          h->s_rp, h->s_ci, h->s_v, h->xdiag, h->st));
+  tmp.release();
+  return SDSL_OK;
+}
+
+void choose_spmv_plan(sdsl_handle h) {
+  const double avg = h->N > 0 ? (double)h->s_nnz / (double)h->N : 1.0;
+  h->A.n = h->N;
+  h->A.rp = h->s_rp;
+  h->A.ci = h->s_ci;
+  h->A.v = h->s_v;
+  h->A.lanes = pow2_lanes(avg, 3.0);
+  const int64_t rows_per_cta_min = 64;
+  int64_t g = (h->N + rows_per_cta_min - 1) / rows_per_cta_min;
+  g = std::max<int64_t>(1, std::min<int64_t>(g, (int64_t)h->sms * 8));
+  h->A.grid = (int)g;
+}
+
+sdsl_status destroy_graph(sdsl_handle h) {
+  if (h->graph) {
+    cudaGraphExecDestroy(h->graph);
+    h->graph = nullptr;
+  }
+  return SDSL_OK;
+}
+
+// One PCG iteration = three launches (see krylov.cu).
+sdsl_status enqueue_pcg_iteration(sdsl_handle h) {
+  TRY_CUDA(pcg_spmv(h->A, h->p, h->q, h->part, h->state, h->st));
+  TRY_CUDA(pcg_update_precond(h->M, h->p, h->q, h->x, h->r, h->z, h->part_rr, h->part_rz, h->state, h->st));
+  TRY_CUDA(pcg_direction(h->N, h->z, h->p, h->state, h->st));
+  return SDSL_OK;
+}
+
+sdsl_status build_graph(sdsl_handle h) {
+  destroy_graph(h);
+  const int G = h->opt.graph_iters;
+  if (G <= 0) return SDSL_OK;
+  cudaGraph_t g = nullptr;
+  TRY_CUDA(cudaStreamBeginCapture(h->st, cudaStreamCaptureModeRelaxed));
+  sdsl_status s = SDSL_OK;
+  for (int i = 0; i < G && s == SDSL_OK; ++i) s = enqueue_pcg_iteration(h);
+  cudaError_t e = cudaStreamEndCapture(h->st, &g);
+  if (s != SDSL_OK) { if (g) cudaGraphDestroy(g); return s; }
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+  e = cudaGraphInstantiate(&h->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+  h->graph_iters = G;
+  return SDSL_OK;
+}
+
+sdsl_status build_levels(sdsl_handle h, int dir, int32_t** off, int32_t** ptr, int32_t** rows,
+                         std::vector<int32_t>& nlev_h, int64_t* total, int32_t* cnt, int32_t* lev, int32_t* fa,
+                         int32_t* fb, int32_t* nlev_d) {
+  const int64_t nb = h->nblocks;
+  TRY_CUDA(levels(dir, nb, h->d_bp, h->p_rp, h->p_ci, h->p_diag, cnt, lev, fa, fb, nlev_d, h->st));
+  nlev_h.assign(nb, 0);
+  TRY(to_host(h, nlev_h.data(), nlev_d, nb));
+  TRY(sync(h, "levels"));
+  std::vector<int32_t> off_h(nb + 1, 0);
+  for (int64_t k = 0; k < nb; ++k) off_h[k + 1] = off_h[k] + nlev_h[k];
+  *total = off_h[nb];
+  TRY(h->pc.get(off, nb + 1));
+  TRY(h->pc.get(ptr, *total + 1));
+  TRY(h->pc.get(rows, h->h_bp[nb]));
+  TRY(to_dev(h, *off, off_h.data(), nb + 1));
+  const int32_t end = (int32_t)h->h_bp[nb];
+  TRY(to_dev(h, *ptr + *total, &end, 1));
+  TRY_CUDA(level_lists(nb, h->d_bp, lev, *off, cnt, *ptr, *rows, h->st));
+  return sync(h, "level lists");
+}
+
+sdsl_status factor_impl(sdsl_handle h) {
+  cudaEventRecord(h->ev_a, h->st);
+  h->pc.release();
+  destroy_graph(h);
+  h->factored = false;
+  const int64_t N = h->N, nb = h->nblocks;
+  const int whole = h->method == SDSL_BBD_GMRES ? 1 : 0;
+  // Eq. (filter) + Eq. (diagcorr)
+  TRY_CUDA(diag_values(N, h->s_rp, h->s_ci, h->s_v, h->dvals, h->st));
+  TRY(h->pc.get(&h->p_rp, N + 1));
+  TRY_CUDA(filter_count(N, h->s_rp, h->s_ci, h->s_v, h->dvals, h->row_block, h->d_bp, whole, h->opt.tau, h->p_rp,
+                        h->st));
+  TRY(scan_total(h, h->p_rp, N, &h->p_nnz));
+  TRY(h->pc.get(&h->p_ci, h->p_nnz));
+  TRY(h->pc.get(&h->p_v, h->p_nnz));
+  TRY(h->pc.get(&h->p_diag, N));
+  TRY(h->pc.get(&h->F, h->p_nnz));
+  TRY(h->pc.get(&h->dinv, N));
+  TRY(h->pc.get(&h->mir, h->p_nnz));
+  TRY_CUDA(filter_fill(N, h->s_rp, h->s_ci, h->s_v, h->dvals, h->row_block, h->d_bp, whole, h->opt.tau, h->opt.delta,
+                       h->p_rp, h->p_ci, h->p_v, h->p_diag, h->st));
+  // symmetric pattern is required by the level construction and IC(0)
+  TRY_CUDA(cudaMemsetAsync(h->flag, 0, sizeof(int), h->st));
+  TRY_CUDA(mirror_map(N, h->p_rp, h->p_ci, h->p_diag, h->mir, h->flag, h->st));
+  int bad = 0;
+  TRY(to_host(h, &bad, h->flag, 1));
+  TRY(sync(h, "mirror map"));
+  if (bad) return fail(SDSL_ERR_ARG, "the system matrix must have a symmetric sparsity pattern");
+  // level sets (lower and upper) of the block triangular solves
+  int32_t *cnt, *lev, *fa, *fb, *nlev_d;
+  Arena tmp;
+  tmp.st = h->st;
+  TRY(tmp.get(&cnt, N));
+  TRY(tmp.get(&lev, N));
+  TRY(tmp.get(&fa, N));
+  TRY(tmp.get(&fb, N));
+  TRY(tmp.get(&nlev_d, nb));
+  TRY(build_levels(h, 0, &h->lev_off_lo, &h->lev_ptr_lo, &h->lev_rows_lo, h->h_nlev_lo, &h->tot_lo, cnt, lev, fa, fb,
+                   nlev_d));
+  TRY(build_levels(h, 1, &h->lev_off_up, &h->lev_ptr_up, &h->lev_rows_up, h->h_nlev_up, &h->tot_up, cnt, lev, fa, fb,
+                   nlev_d));
+  tmp.release();
+  // per-block factorization with the shift-retry rule
+  static const double kShifts[5] = {0.0, 1e-3, 1e-2, 1e-1, 1.0};
+  double* d_alpha;
+  int32_t *d_active, *d_status;
+  TRY(h->pc.get(&d_alpha, nb));
+  TRY(h->pc.get(&d_active, nb));
+  TRY(h->pc.get(&d_status, nb));
+  std::vector<int> tries(nb, 0);
+  std::vector<int32_t> active(nb, 1), status(nb, 0);
+  h->h_alpha.assign(nb, 0.0);
+  int64_t shifted = 0;
+  for (int round = 0; round < 5; ++round) {
+    for (int64_t k = 0; k < nb; ++k) h->h_alpha[k] = kShifts[tries[k]];
+    TRY(to_dev(h, d_alpha, h->h_alpha.data(), nb));
+    TRY(to_dev(h, d_active, active.data(), nb));
+    if (h->method == SDSL_BBD_GMRES)
+      TRY_CUDA(ilu0_factor(nb, h->d_bp, h->p_rp, h->p_ci, h->p_v, h->p_diag, h->lev_off_lo, h->lev_ptr_lo,
+                           h->lev_rows_lo, d_alpha, d_active, h->F, h->dinv, d_status, h->st));
+    else
+      TRY_CUDA(ic0_factor(nb, h->d_bp, h->p_rp, h->p_ci, h->p_v, h->p_diag, h->lev_off_lo, h->lev_ptr_lo,
+                          h->lev_rows_lo, d_alpha, d_active, h->F, h->dinv, d_status, h->st));
+    TRY(to_host(h, status.data(), d_status, nb));
+    TRY(sync(h, "factor"));
+    bool any = false;
+    for (int64_t k = 0; k < nb; ++k) {
+      if (active[k] && status[k]) {
+        any = true;
+        tries[k] += 1;
+        if (tries[k] >= 5) {
+          h->h_alpha[k] = -1.0;
+          return fail(SDSL_ERR_BREAKDOWN, "block " + std::to_string(k) + " breaks down with every diagonal shift");
+        }
+      } else {
+        active[k] = 0;
+      }
+    }
+    for (int64_t k = 0; k < nb; ++k) active[k] = active[k] && status[k];
+    if (!any) break;
+  }
+  for (int64_t k = 0; k < nb; ++k) {
+    h->h_alpha[k] = kShifts[tries[k]];
+    shifted += tries[k] > 0;
+  }
+  const bool f32 = h->opt.factor_prec == 32;
+  if (f32) {
+    TRY(h->pc.get(&h->Ff, h->p_nnz));
+    TRY(h->pc.get(&h->dinvf, N));
+  } else {
+    h->Ff = nullptr;
+    h->dinvf = nullptr;
+  }
+  if (h->method == SDSL_BBD_GMRES) {
+    if (f32) {
+      TRY_CUDA(to_float(h->p_nnz, h->F, h->Ff, h->st));
+      TRY_CUDA(to_float(N, h->dinv, h->dinvf, h->st));
+    }
+  } else {
+    TRY_CUDA(ic0_finish(N, h->p_nnz, h->p_rp, h->p_diag, h->mir, h->F, h->dinv, h->Ff, h->dinvf, h->st));
+  }
+  // apply plan
+  int64_t maxb = 0;
+  for (int64_t k = 0; k < nb; ++k) maxb = std::max(maxb, h->h_bp[k + 1] - h->h_bp[k]);
+  TriSolve& M = h->M;
+  M = TriSolve{};
+  M.nblocks = nb;
+  M.bp = h->d_bp;
+  M.prp = h->p_rp;
+  M.pci = h->p_ci;
+  M.pdiag = h->p_diag;
+  M.F = h->F;
+  M.Ff = h->Ff;
+  M.dinv = h->dinv;
+  M.dinvf = h->dinvf;
+  M.lev_off_lo = h->lev_off_lo;
+  M.lev_ptr_lo = h->lev_ptr_lo;
+  M.lev_rows_lo = h->lev_rows_lo;
+  M.lev_off_up = h->lev_off_up;
+  M.lev_ptr_up = h->lev_ptr_up;
+  M.lev_rows_up = h->lev_rows_up;
+  M.unit_lower = h->method == SDSL_BBD_GMRES ? 1 : 0;
+  M.prec = f32 ? 32 : 64;
+  const double avg_half = N > 0 ? (double)(h->p_nnz - N) / (2.0 * (double)N) : 1.0;
+  M.lanes = pow2_lanes(avg_half, 2.0);
+  M.max_block = maxb;
+  if ((size_t)maxb * (f32 ? 4 : 8) > (size_t)200 * 1024) {
+    if (f32) TRY(h->pc.get(&M.yscratch, N));
+    else TRY(h->pc.get(&M.yscratch64, N));
+  }
+  TRY(h->pc.get(&h->part_rr, nb + 32));
+  TRY(h->pc.get(&h->part_rz, nb + 32));
+  choose_spmv_plan(h);
+  if (h->method == SDSL_BJ_PCG) TRY(build_graph(h));
+  cudaEventRecord(h->ev_b, h->st);
+  TRY(sync(h, "factor end"));
+  h->factored = true;
+  h->need_rebuild = false;
+  h->iters_post_build = -1;
+  h->stats.ms_factor = elapsed(h);
+  h->stats.nnz_precond = h->p_nnz;
+  h->stats.nnz_factor = h->method == SDSL_BBD_GMRES ? h->p_nnz : (h->p_nnz + N) / 2;
+  h->stats.levels_lower = h->tot_lo;
+  h->stats.levels_upper = h->tot_up;
+  int64_t mx = 0;
+  for (int64_t k = 0; k < nb; ++k) mx = std::max<int64_t>(mx, std::max(h->h_nlev_lo[k], h->h_nlev_up[k]));
+  h->stats.max_levels = mx;
+  h->stats.shifted_blocks = shifted;
+  h->stats.builds += 1;
+  // algorithmic bytes of one PCG iteration (see the design doc for the model)
+  const double sf = f32 ? 4.0 : 8.0;
+  const double nnzL = (double)h->stats.nnz_factor;
+  h->stats.bytes_per_iter = 12.0 * (double)h->s_nnz + 8.0 * (double)(N + 1) + 2.0 * ((sf + 4.0) * nnzL) +
+                            2.0 * 8.0 * (double)(N + 1) + 8.0 * (double)N * 13.0;
+  return SDSL_OK;
+}
+
+sdsl_status pcg_solve(sdsl_handle h, sdsl_stats* st_out) {
+  const int64_t N = h->N;
+  // ||b||^2 and r = b - S x
+  double* bn2 = h->scalars;
+  TRY_CUDA(norm2_sq(N, h->b, h->part, bn2, reinterpret_cast<unsigned int*>(h->part + 152 * 32), h->st));
+  TRY_CUDA(pcg_init_state(h->state, 0.0, h->opt.maxit, h->st));
+  TRY_CUDA(true_residual(h->A, h->b, h->x, h->r, h->part, h->state, 1, h->st));
+  double bnorm2 = 0.0;
+  TRY(to_host(h, &bnorm2, bn2, 1));
+  TRY(to_host(h, h->h_state, h->state, 1));
+  TRY(sync(h, "pcg init"));
+  const double tol = h->opt.rtol * std::sqrt(bnorm2);
+  const double tol2 = tol * tol;
+  sdsl_stats& S = h->stats;
+  S.iters = 0;
+  S.restarts = 0;
+  if (bnorm2 == 0.0) {
+    TRY_CUDA(cudaMemsetAsync(h->x, 0, sizeof(double) * (size_t)N, h->st));
+    S.rel_res_true = S.rel_res_rec = 0.0;
+    S.status = SDSL_OK;
+    return SDSL_OK;
+  }
+  if (h->h_state->tr <= tol2) {
+    S.rel_res_true = S.rel_res_rec = std::sqrt(h->h_state->tr / bnorm2);
+    S.status = SDSL_OK;
+    return SDSL_OK;
+  }
+  TRY_CUDA(pcg_init_state(h->state, tol2, h->opt.maxit, h->st));
+  TRY_CUDA(precond_apply(h->M, h->r, h->z, h->p, h->part_rr, h->part_rz, h->state, 1, h->st));
+  sdsl_status result = SDSL_ERR_NOT_CONVERGED;
+  for (;;) {
+    if (h->graph) {
+      TRY_CUDA(cudaGraphLaunch(h->graph, h->st));
+    } else {
+      for (int i = 0; i < 8; ++i) TRY(enqueue_pcg_iteration(h));
+    }
+    TRY(to_host(h, h->h_state, h->state, 1));
+    TRY(sync(h, "pcg iterations"));
+    const PcgState& hs = *h->h_state;
+    if (!hs.done) continue;
+    if (hs.done == 3) { result = SDSL_ERR_BREAKDOWN; break; }
+    if (hs.done == 2) { result = SDSL_ERR_NOT_CONVERGED; break; }
+    // recurrence converged: confirm with the true residual
+    TRY_CUDA(true_residual(h->A, h->b, h->x, h->r, h->part, h->state, 0, h->st));
+    TRY(to_host(h, h->h_state, h->state, 1));
+    TRY(sync(h, "true residual"));
+    if (h->h_state->tr <= tol2) { result = SDSL_OK; break; }
+    if (h->h_state->iters >= h->opt.maxit) { result = SDSL_ERR_NOT_CONVERGED; break; }
+    // restart from r = b - S x with a fresh direction
+    S.restarts += 1;
+    TRY_CUDA(true_residual(h->A, h->b, h->x, h->r, h->part, h->state, 1, h->st));
+    TRY_CUDA(precond_apply(h->M, h->r, h->z, h->p, h->part_rr, h->part_rz, h->state, 1, h->st));
+    TRY_CUDA(cudaMemsetAsync(&h->state->done, 0, sizeof(int), h->st));
+  }
+  // final true residual (also for not-converged / breakdown exits)
+  TRY_CUDA(true_residual(h->A, h->b, h->x, h->r, h->part, h->state, 0, h->st));
+  TRY(to_host(h, h->h_state, h->state, 1));
+  TRY(sync(h, "final residual"));
+  S.iters = h->h_state->iters;
+  S.rel_res_true = std::sqrt(h->h_state->tr / bnorm2);
+  S.rel_res_rec = std::sqrt(h->h_state->rr / bnorm2);
+  S.status = result;
+  (void)st_out;
+  if (result == SDSL_OK) return SDSL_OK;
+  return fail(result, result == SDSL_ERR_BREAKDOWN ? "PCG breakdown (p^T S p <= 0 or non-finite)"
+                                                   : "PCG reached maxit before the tolerance");
+}
+
+}  // namespace
+
+// ========================================================================= ABI
+
+extern "C" {
+
+void sdsl_default_options(sdsl_options* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->form = SDSL_FORM_NORMAL;
+  o->method = SDSL_BJ_PCG;
+  o->nblocks = 1;
+  o->tau = 1e-3;
+  o->delta = 1e-12;
+  o->rho = 1e-6;
+  o->factor_prec = 64;
+  o->rtol = 1e-8;
+  o->maxit = 2000;
+  o->restart = 30;
+  o->refactor_ratio = 1.5;
+  o->mem_space = SDSL_MEM_DEVICE;
+  o->graph_iters = 16;
+}
+
+const char* sdsl_status_str(sdsl_status s) {
+  switch (s) {
+    case SDSL_OK: return "ok";
+    case SDSL_ERR_ARG: return "invalid argument";
+    case SDSL_ERR_OOM: return "out of device memory";
+    case SDSL_ERR_CUDA: return "CUDA error";
+    case SDSL_ERR_BREAKDOWN: return "breakdown";
+    case SDSL_ERR_NOT_CONVERGED: return "not converged";
+    case SDSL_ERR_TIMEOUT: return "device wait timed out";
+    case SDSL_ERR_STATE: return "call out of order";
+  }
+  return "unknown status";
+}
+
+const char* sdsl_last_error(void) { return g_err.c_str(); }
+
+sdsl_status sdsl_free(sdsl_handle h) {
+  if (!h) return SDSL_OK;
+  destroy_graph(h);
+  if (h->st) {
+    h->pc.release();
+    h->sys.release();
+    cudaStreamSynchronize(h->st);
+  }
+  if (h->h_state) cudaFreeHost(h->h_state);
+  if (h->ev_a) cudaEventDestroy(h->ev_a);
+  if (h->ev_b) cudaEventDestroy(h->ev_b);
+  if (h->ev_join) cudaEventDestroy(h->ev_join);
+  if (h->st) cudaStreamDestroy(h->st);
+  delete h;
+  return SDSL_OK;
+}
+
+sdsl_status sdsl_setup(const sdsl_options* opt, int64_t m, int64_t n, const int64_t* rowptr, const int32_t* col,
+                       const double* val, const double* theta, sdsl_handle* out) {
+  if (!out) return fail(SDSL_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!opt) return fail(SDSL_ERR_ARG, "options are NULL");
+  if (m < 0 || n < 0 || m >= INT32_MAX || n >= INT32_MAX) return fail(SDSL_ERR_ARG, "m, n must be in [0, 2^31-1)");
+  if (opt->form < SDSL_FORM_CSR || opt->form > SDSL_FORM_AUGMENTED) return fail(SDSL_ERR_ARG, "unknown form");
+  if (opt->method != SDSL_BJ_PCG && opt->method != SDSL_BBD_GMRES) return fail(SDSL_ERR_ARG, "unknown method");
+  if (opt->factor_prec != 64 && opt->factor_prec != 32) return fail(SDSL_ERR_ARG, "factor_prec must be 64 or 32");
+  if (!(opt->tau >= 0.0) || !(opt->delta >= 0.0) || !(opt->rtol > 0.0) || opt->maxit < 0)
+    return fail(SDSL_ERR_ARG, "tau, delta must be >= 0, rtol > 0, maxit >= 0");
+  if (opt->form == SDSL_FORM_CSR && m != n) return fail(SDSL_ERR_ARG, "CSR form needs a square matrix");
+  if (opt->form != SDSL_FORM_CSR && !theta) return fail(SDSL_ERR_ARG, "theta is NULL");
+  if (opt->form == SDSL_FORM_AUGMENTED && opt->method != SDSL_BBD_GMRES)
+    return fail(SDSL_ERR_ARG, "the augmented (indefinite) form needs the BBD-GMRES method");
+  if (opt->method == SDSL_BBD_GMRES && opt->form != SDSL_FORM_AUGMENTED)
+    return fail(SDSL_ERR_ARG, "BBD-GMRES is implemented for the augmented form");
+  const int64_t nb = opt->nblocks < 1 ? 1 : opt->nblocks;
+  const int64_t dimS = opt->form == SDSL_FORM_AUGMENTED ? m + n : m;
+  if (opt->form == SDSL_FORM_AUGMENTED) {
+    if (opt->border < 0 || opt->border > m) return fail(SDSL_ERR_ARG, "border must be in [0, m]");
+    TRY(check_block_ptr(opt->block_ptr, nb, m - opt->border));
+    TRY(check_block_ptr(opt->col_block_ptr, nb, n));
+  } else if (opt->block_ptr) {
+    TRY(check_block_ptr(opt->block_ptr, nb, dimS));
+  }
+  int dev = 0;
+  cudaGetDevice(&dev);
+  ensure_pool(dev);
+  sdsl_handle h = new sdsl_handle_s();
+  h->opt = *opt;
+  h->opt.nblocks = nb;
+  h->dev = dev;
+  cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, dev);
+  h->user = (cudaStream_t)opt->stream;
+  if (cudaStreamCreateWithFlags(&h->st, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreate(&h->ev_a) != cudaSuccess || cudaEventCreate(&h->ev_b) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+    sdsl_free(h);
+    return fail(SDSL_ERR_CUDA, "stream/event creation failed");
+  }
+  h->sys.st = h->pc.st = h->st;
+  h->form = opt->form;
+  h->method = opt->method;
+  h->m = m;
+  h->n = n;
+  h->N = dimS;
+  h->nblocks = nb;
+  h->border = opt->form == SDSL_FORM_AUGMENTED ? opt->border : 0;
+  sdsl_status s = SDSL_OK;
+  {
+    Scope scope(h);
+    cudaEventRecord(h->ev_a, h->st);
+    auto body = [&]() -> sdsl_status {
+      TRY(h->sys.get(&h->flag, 4));
+      TRY(h->sys.get(&h->scan_scratch, scan_scratch_elems(std::max<int64_t>(h->N, n) + 1) + 8));
+      if (h->form == SDSL_FORM_CSR) {
+        TRY(load_csr(h, m, m, rowptr, col, val, &h->s_rp, &h->s_ci, &h->s_v, &h->s_nnz));
+      } else {
+        TRY(load_csr(h, m, n, rowptr, col, val, &h->a_rp, &h->a_ci, &h->a_v, &h->a_nnz));
+        TRY(h->sys.get(&h->theta, n));
+        TRY(to_dev(h, h->theta, theta, n));
+        TRY(transpose_input(h));
+        if (h->form == SDSL_FORM_NORMAL) TRY(form_normal(h));
+        else TRY(form_augmented(h, opt->block_ptr, opt->col_block_ptr));
+      }
+      if (h->form != SDSL_FORM_AUGMENTED) {
+        h->h_bp.resize(nb + 1);
+        if (opt->block_ptr) {
+          std::memcpy(h->h_bp.data(), opt->block_ptr, sizeof(int64_t) * (nb + 1));
+        } else {
+          for (int64_t k = 0; k <= nb; ++k) h->h_bp[k] = (k * dimS) / nb;
+        }
+        TRY(h->sys.get(&h->d_bp, nb + 1));
+        TRY(to_dev(h, h->d_bp, h->h_bp.data(), nb + 1));
+      }
+      TRY(h->sys.get(&h->row_block, h->N));
+      TRY(h->sys.get(&h->dvals, h->N));
+      TRY_CUDA(row_blocks(h->N, nb, h->d_bp, h->row_block, h->st));
+      TRY(alloc_workspace(h));
+      cudaEventRecord(h->ev_b, h->st);
+      return sync(h, "setup end");
+    };
+    s = body();
+  }
+  if (s != SDSL_OK) {
+    std::string msg = g_err;
+    sdsl_free(h);
+    g_err = msg;
+    return s;
+  }
+  h->stats.ms_setup = elapsed(h);
+  h->stats.n = h->N;
+  h->stats.nnz_system = h->s_nnz;
+  *out = h;
+  return SDSL_OK;
+}
+
+sdsl_status sdsl_factor(sdsl_handle h) {
+  if (!h) return fail(SDSL_ERR_ARG, "handle is NULL");
+  Scope scope(h);
+  return factor_impl(h);
+}
+
+sdsl_status sdsl_update_diag(sdsl_handle h, const double* theta) {
+  if (!h) return fail(SDSL_ERR_ARG, "handle is NULL");
+  if (h->form == SDSL_FORM_CSR) return fail(SDSL_ERR_STATE, "update_diag needs the normal or augmented form");
+  if (!theta) return fail(SDSL_ERR_ARG, "theta is NULL");
+  Scope scope(h);
+  cudaEventRecord(h->ev_a, h->st);
+  TRY(to_dev(h, h->theta, theta, h->n));
+  if (h->form == SDSL_FORM_NORMAL)
+    TRY_CUDA(normal_values(h->m, h->a_rp, h->a_ci, h->a_v, h->at_rp, h->at_ci, h->at_v, h->theta, h->opt.rho, h->s_rp,
+                           h->s_ci, h->s_v, h->st));
+  else
+    TRY_CUDA(augmented_theta(h->n, h->theta, h->xdiag, h->s_v, h->st));
+  cudaEventRecord(h->ev_b, h->st);
+  TRY(sync(h, "update_diag"));
+  h->stats.ms_update = elapsed(h);
+  return SDSL_OK;
+}
+
+sdsl_status sdsl_solve(sdsl_handle h, const double* b, double* x, int x0_zero, sdsl_stats* st) {
+  if (!h) return fail(SDSL_ERR_ARG, "handle is NULL");
+  if (!b || !x) return fail(SDSL_ERR_ARG, "b or x is NULL");
+  if (!h->factored) return fail(SDSL_ERR_STATE, "sdsl_solve before sdsl_factor");
+  if (h->method != SDSL_BJ_PCG) return fail(SDSL_ERR_ARG, "BBD-GMRES solve not available in this build");
+  Scope scope(h);
+  int rebuilt = 0;
+  if (h->need_rebuild) {
+    TRY(factor_impl(h));
+    rebuilt = 1;
+  }
+  cudaEventRecord(h->ev_a, h->st);
+  TRY(to_dev(h, h->b, b, h->N));
+  if (x0_zero) TRY_CUDA(cudaMemsetAsync(h->x, 0, sizeof(double) * (size_t)h->N, h->st));
+  else TRY(to_dev(h, h->x, (const double*)x, h->N));
+  sdsl_status s = pcg_solve(h, st);
+  TRY(to_host(h, x, h->x, h->N));
+  cudaEventRecord(h->ev_b, h->st);
+  TRY(sync(h, "solve end"));
+  h->stats.ms_solve = elapsed(h);
+  h->stats.rebuilt = rebuilt;
+  // reuse rule (Sec. 3.4): remember the first solve after a build; request a
+  // rebuild once a later solve needs more than ratio times as many iterations
+  if (s == SDSL_OK || s == SDSL_ERR_NOT_CONVERGED) {
+    if (h->iters_post_build < 0) h->iters_post_build = h->stats.iters;
+    else if (h->opt.refactor_ratio > 0.0 &&
+             (double)h->stats.iters > h->opt.refactor_ratio * (double)h->iters_post_build)
+      h->need_rebuild = true;
+  }
+  if (st) *st = h->stats;
+  return s;
+}
+
+sdsl_status sdsl_get_stats(sdsl_handle h, sdsl_stats* st) {
+  if (!h || !st) return fail(SDSL_ERR_ARG, "NULL argument");
+  *st = h->stats;
+  return SDSL_OK;
+}
+
+sdsl_status sdsl_get_info(sdsl_handle h, sdsl_info* info) {
+  if (!h || !info) return fail(SDSL_ERR_ARG, "NULL argument");
+  info->n = h->N;
+  info->nnz_system = h->s_nnz;
+  info->nnz_precond = h->factored ? h->p_nnz : 0;
+  info->nblocks = h->nblocks;
+  info->border = h->border;
+  info->levels_lower = h->factored ? h->tot_lo : 0;
+  info->levels_upper = h->factored ? h->tot_up : 0;
+  info->factored = h->factored ? 1 : 0;
+  return SDSL_OK;
+}
+
+sdsl_status sdsl_export_system(sdsl_handle h, int64_t* rowptr, int32_t* col, double* val) {
+  if (!h) return fail(SDSL_ERR_ARG, "handle is NULL");
+  Scope scope(h);
+  if (rowptr) TRY(to_host(h, rowptr, h->s_rp, h->N + 1));
+  if (col) TRY(to_host(h, col, h->s_ci, h->s_nnz));
+  if (val) TRY(to_host(h, val, h->s_v, h->s_nnz));
+  return sync(h, "export system");
+}
+
+sdsl_status sdsl_export_precond(sdsl_handle h, int64_t* rowptr, int32_t* col, double* pval, double* fval,
+                                double* alpha) {
+  if (!h) return fail(SDSL_ERR_ARG, "handle is NULL");
+  if (!h->factored) return fail(SDSL_ERR_STATE, "no preconditioner yet");
+  Scope scope(h);
+  if (rowptr) TRY(to_host(h, rowptr, h->p_rp, h->N + 1));
+  if (col) TRY(to_host(h, col, h->p_ci, h->p_nnz));
+  if (pval) TRY(to_host(h, pval, h->p_v, h->p_nnz));
+  if (fval) {
+    if (h->Ff) {
+      std::vector<float> tmp(h->p_nnz);
+      TRY(to_host(h, tmp.data(), h->Ff, h->p_nnz));
+      TRY(sync(h, "export factor"));
+      for (int64_t i = 0; i < h->p_nnz; ++i) fval[i] = tmp[i];
+    } else {
+      TRY(to_host(h, fval, h->F, h->p_nnz));
+    }
+  }
+  if (alpha) std::memcpy(alpha, h->h_alpha.data(), sizeof(double) * h->nblocks);
+  return sync(h, "export precond");
+}
+
+sdsl_status sdsl_export_levels(sdsl_handle h, int which, int32_t* nlev, int64_t* level_ptr, int32_t* level_rows) {
+  if (!h) return fail(SDSL_ERR_ARG, "handle is NULL");
+  if (!h->factored) return fail(SDSL_ERR_STATE, "no preconditioner yet");
+  if (which != 0 && which != 1) return fail(SDSL_ERR_ARG, "which must be 0 or 1");
+  Scope scope(h);
+  const std::vector<int32_t>& nl = which == 0 ? h->h_nlev_lo : h->h_nlev_up;
+  const int64_t tot = which == 0 ? h->tot_lo : h->tot_up;
+  if (nlev) std::memcpy(nlev, nl.data(), sizeof(int32_t) * h->nblocks);
+  if (level_ptr) {
+    std::vector<int32_t> tmp(tot + 1);
+    TRY(to_host(h, tmp.data(), which == 0 ? h->lev_ptr_lo : h->lev_ptr_up, tot + 1));
+    TRY(sync(h, "export levels"));
+    for (int64_t i = 0; i <= tot; ++i) level_ptr[i] = tmp[i];
+  }
+  if (level_rows) TRY(to_host(h, level_rows, which == 0 ? h->lev_rows_lo : h->lev_rows_up, h->h_bp[h->nblocks]));
+  return sync(h, "export levels");
+}
+
+sdsl_status sdsl_export_schur(sdsl_handle h, double* sb) {
+  (void)sb;
+  if (!h) return fail(SDSL_ERR_ARG, "handle is NULL");
+  return fail(SDSL_ERR_STATE, "no Schur complement in this build");
+}
+
+sdsl_status sdsl_spmv(sdsl_handle h, const double* x, double* y) {
+  if (!h || !x || !y) return fail(SDSL_ERR_ARG, "NULL argument");
+  Scope scope(h);
+  SpmvPlan A = h->A;
+  if (!h->factored) {
+    A.n = h->N; A.rp = h->s_rp; A.ci = h->s_ci; A.v = h->s_v; A.lanes = 32; A.grid = h->sms * 4;
+  }
+  TRY_CUDA(spmv(A, x, y, h->st));
+  return SDSL_OK;
+}
+
+sdsl_status sdsl_precond_apply(sdsl_handle h, const double* r, double* z) {
+  if (!h || !r || !z) return fail(SDSL_ERR_ARG, "NULL argument");
+  if (!h->factored) return fail(SDSL_ERR_STATE, "no preconditioner yet");
+  Scope scope(h);
+  TRY_CUDA(precond_apply(h->M, r, z, nullptr, h->part_rr, h->part_rz, h->state, 2, h->st));
+  return SDSL_OK;
+}
+
+}  // extern "C"

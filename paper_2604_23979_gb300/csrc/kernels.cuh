@@ -1,0 +1,138 @@
+// kernels.cuh -- host launchers of the device kernels (internal interface
+// between the C ABI in api.cu and the kernel translation units).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace sdsl {
+
+// ---- setup.cu: system formation (Eq. schur / Eq. augmented)
+cudaError_t check_csr(int64_t nrows, int64_t ncols, const int64_t* rp, const int32_t* ci, int* bad, cudaStream_t st);
+cudaError_t transpose_csr(int64_t m, int64_t n, const int64_t* rp, const int32_t* ci, const double* v, int64_t* trp,
+                          int32_t* tci, double* tv, int64_t* scan_scratch, cudaStream_t st);
+cudaError_t transpose_fill(int64_t m, int64_t n, const int64_t* rp, const int32_t* ci, const double* v,
+                           const int64_t* trp, int32_t* tci, double* tv, int64_t* cursor, cudaStream_t st);
+cudaError_t sort_rows(int64_t nrows, const int64_t* rp, int32_t* ci, double* v, cudaStream_t st);
+cudaError_t normal_symbolic_count(int64_t m, const int64_t* rp, const int32_t* ci, const int64_t* trp,
+                                  const int32_t* tci, int64_t* srp, int32_t* long_rows, int32_t* nlong,
+                                  cudaStream_t st);
+cudaError_t normal_symbolic_long(bool fill, int nlong, const int32_t* long_rows, const int64_t* rp,
+                                 const int32_t* ci, const int64_t* trp, const int32_t* tci, int64_t* srp,
+                                 int32_t* sci, int* err, cudaStream_t st);
+cudaError_t normal_symbolic_fill(int64_t m, const int64_t* rp, const int32_t* ci, const int64_t* trp,
+                                 const int32_t* tci, const int64_t* srp, int32_t* sci, cudaStream_t st);
+cudaError_t normal_values(int64_t m, const int64_t* rp, const int32_t* ci, const double* v, const int64_t* trp,
+                          const int32_t* tci, const double* tv, const double* theta, double rho,
+                          const int64_t* srp, const int32_t* sci, double* sv, cudaStream_t st);
+cudaError_t bbd_positions(int64_t m, int64_t n, int64_t nblocks, const int64_t* rbp, const int64_t* cbp,
+                          const int64_t* kbp, int64_t* pos, cudaStream_t st);
+cudaError_t augmented_count(int64_t m, int64_t n, const int64_t* rp, const int64_t* trp, const int64_t* pos,
+                            int64_t* krp, cudaStream_t st);
+cudaError_t augmented_fill(int64_t m, int64_t n, const int64_t* rp, const int32_t* ci, const double* v,
+                           const int64_t* trp, const int32_t* tci, const double* tv, const double* theta, double rho,
+                           const int64_t* pos, const int64_t* krp, int32_t* kci, double* kv, int64_t* xdiag,
+                           cudaStream_t st);
+cudaError_t augmented_theta(int64_t n, const double* theta, const int64_t* xdiag, double* kv, cudaStream_t st);
+
+// ---- precond.cu: filter (Eq. filter), correction (Eq. diagcorr), levels, factors
+cudaError_t diag_values(int64_t n, const int64_t* rp, const int32_t* ci, const double* v, double* d, cudaStream_t st);
+// whole = 0: keep in-block entries only (Block Jacobi); 1: every entry (BBD)
+cudaError_t filter_count(int64_t n, const int64_t* rp, const int32_t* ci, const double* v, const double* d,
+                         const int32_t* row_block, const int64_t* bp, int whole, double tau, int64_t* prp,
+                         cudaStream_t st);
+cudaError_t filter_fill(int64_t n, const int64_t* rp, const int32_t* ci, const double* v, const double* d,
+                        const int32_t* row_block, const int64_t* bp, int whole, double tau, double delta,
+                        const int64_t* prp, int32_t* pci, double* pv, int64_t* pdiag, cudaStream_t st);
+cudaError_t row_blocks(int64_t n, int64_t nblocks, const int64_t* bp, int32_t* row_block, cudaStream_t st);
+cudaError_t mirror_map(int64_t n, const int64_t* prp, const int32_t* pci, const int64_t* pdiag, int64_t* mir,
+                       int* bad, cudaStream_t st);
+// Level sets of the in-block lower (dir = 0) or upper (dir = 1) triangle.
+cudaError_t levels(int dir, int64_t nblocks, const int64_t* bp, const int64_t* prp, const int32_t* pci,
+                   const int64_t* pdiag, int32_t* cnt, int32_t* lev, int32_t* fa, int32_t* fb, int32_t* nlev,
+                   cudaStream_t st);
+cudaError_t level_lists(int64_t nblocks, const int64_t* bp, const int32_t* lev, const int32_t* lev_off,
+                        int32_t* hist, int32_t* level_ptr, int32_t* level_rows, cudaStream_t st);
+cudaError_t ic0_factor(int64_t nblocks, const int64_t* bp, const int64_t* prp, const int32_t* pci, const double* pv,
+                       const int64_t* pdiag, const int32_t* lev_off, const int32_t* level_ptr,
+                       const int32_t* level_rows, const double* alpha, const int32_t* active, double* F,
+                       double* dinv, int32_t* status, cudaStream_t st);
+cudaError_t ilu0_factor(int64_t nblocks, const int64_t* bp, const int64_t* prp, const int32_t* pci, const double* pv,
+                        const int64_t* pdiag, const int32_t* lev_off, const int32_t* level_ptr,
+                        const int32_t* level_rows, const double* alpha, const int32_t* active, double* F,
+                        double* dinv, int32_t* status, cudaStream_t st);
+// IC(0): copy l_ji to the upper position (i, j); make the FP32 copies.
+cudaError_t ic0_finish(int64_t n, int64_t nnz, const int64_t* prp, const int64_t* pdiag, const int64_t* mir,
+                       double* F, const double* dinv, float* Ff, float* dinvf, cudaStream_t st);
+cudaError_t to_float(int64_t n, const double* a, float* b, cudaStream_t st);
+
+// ---- krylov.cu: SpMV, PCG iteration kernels, residuals
+struct PcgState {
+  double rho;      // r^T z of the current direction
+  double alpha;    // step of the current iteration
+  double beta;
+  double pq;       // p^T q
+  double rr;       // ||r||^2 after the update
+  double rz_new;
+  double tol2;     // (rtol * ||b||)^2
+  double tr;       // ||b - A x||^2 of the last true-residual check
+  long long iters;
+  long long maxit;
+  int done;        // 0 running, 1 recurrence converged, 2 maxit, 3 breakdown
+  int pad;
+  unsigned int ticket[4];
+};
+
+struct TriSolve {  // block triangular factors on the layout of P
+  int64_t nblocks;
+  const int64_t* bp;
+  const int64_t* prp;
+  const int32_t* pci;
+  const int64_t* pdiag;
+  const double* F;      // FP64 factor values (lower: L, upper: L^T or U)
+  const float* Ff;      // FP32 copy (factor_prec 32)
+  const double* dinv;   // 1/l_ii (IC) or 1/u_ii (ILU)
+  const float* dinvf;
+  const int32_t* lev_off_lo;
+  const int32_t* lev_ptr_lo;
+  const int32_t* lev_rows_lo;
+  const int32_t* lev_off_up;
+  const int32_t* lev_ptr_up;
+  const int32_t* lev_rows_up;
+  int unit_lower;       // 1 for ILU(0) (L has a unit diagonal)
+  int prec;             // 64 or 32
+  int lanes;            // lanes per row in the solves (2..32)
+  int64_t max_block;    // largest block (rows) -> shared-memory staging if it fits
+  float* yscratch;      // global staging when the block does not fit in shared memory
+  double* yscratch64;
+};
+
+struct SpmvPlan {
+  int64_t n;
+  const int64_t* rp;
+  const int32_t* ci;
+  const double* v;
+  int lanes;      // lanes per row (2..32)
+  int grid;       // CTAs (fixed => deterministic partial sums)
+};
+
+cudaError_t spmv(const SpmvPlan& A, const double* x, double* y, cudaStream_t st);
+// q = A p, partial p^T q; last CTA: alpha = rho/pq, iters++.
+cudaError_t pcg_spmv(const SpmvPlan& A, const double* p, double* q, double* part, PcgState* s, cudaStream_t st);
+// x += alpha p, r -= alpha q, z = M^{-1} r per block; last CTA: convergence, beta.
+cudaError_t pcg_update_precond(const TriSolve& M, const double* p, const double* q, double* x, double* r, double* z,
+                               double* part_rr, double* part_rz, PcgState* s, cudaStream_t st);
+// p = z + beta p
+cudaError_t pcg_direction(int64_t n, const double* z, double* p, PcgState* s, cudaStream_t st);
+// z = M^{-1} r (no update).  mode 1: also p_out = z, s->rho = r^T z, s->rr =
+// ||r||^2 (PCG start / restart); mode 2: z only.
+cudaError_t precond_apply(const TriSolve& M, const double* r, double* z, double* p_out, double* part_rr,
+                          double* part_rz, PcgState* s, int mode, cudaStream_t st);
+// t = b - A x, ||t||^2 -> s->tr; if write_r, r = t.
+cudaError_t true_residual(const SpmvPlan& A, const double* b, const double* x, double* r, double* part,
+                          PcgState* s, int write_r, cudaStream_t st);
+// ||a||^2 -> *out; part holds up to 608 partials, *ticket must start at 0.
+cudaError_t norm2_sq(int64_t n, const double* a, double* part, double* out, unsigned int* ticket, cudaStream_t st);
+cudaError_t pcg_init_state(PcgState* s, double tol2, long long maxit, cudaStream_t st);
+
+}  // namespace sdsl

@@ -1,0 +1,49 @@
+"""Helpers shared by the GPU parity tests (call the library through its C ABI)."""
+import numpy as np
+
+from paper_2604_23979_gb300 import sdsl
+
+
+def setup(prob, prec=64, graph_iters=16, device=False, **over):
+    o, keep = sdsl.options_for(prob, factor_prec=prec, graph_iters=graph_iters)
+    for k, v in over.items():
+        setattr(o, k, v)
+    A = prob.A
+    arrs = [A.rowptr, A.col, A.val, prob.theta]
+    if device:
+        import torch
+
+        arrs = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in arrs]
+    h = sdsl.sdsl_setup(o, A.nrows, A.ncols, *arrs)
+    return h, (o, keep, arrs)
+
+
+def run_bj(prob, prec=64, graph_iters=16, b=None, x0=None):
+    h, keep = setup(prob, prec, graph_iters)
+    try:
+        sdsl.sdsl_factor(h)
+        b = prob.b if b is None else b
+        x = np.zeros(len(b)) if x0 is None else x0.copy()
+        st = sdsl.sdsl_solve(h, np.ascontiguousarray(b), x, x0_zero=x0 is None)
+        out = dict(x=x, stats=st.as_dict(), S=sdsl.sdsl_export_system(h), P=sdsl.sdsl_export_precond(h),
+                   lev_lo=sdsl.sdsl_export_levels(h, 0), lev_up=sdsl.sdsl_export_levels(h, 1))
+    finally:
+        sdsl.sdsl_free(h)
+    return out
+
+
+def rel(a, b):
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+def relres(S, x, b):
+    """||b - S x|| / ||b|| with the oracle's FP64 SpMV."""
+    import oracle
+
+    return float(np.linalg.norm(b - oracle.spmv(S, x)) / np.linalg.norm(b))
+
+
+def iters_close(gpu, ref):
+    """Iteration counts within max(1, 5 %) of the oracle's."""
+    return abs(gpu - ref) <= max(1, int(np.ceil(0.05 * ref)))

@@ -1,0 +1,295 @@
+"""GPU parity of the Block-Jacobi path against the FP64 oracle, through the C ABI.
+
+Bars: bit-exact system matrix, filtered pattern, corrected values, level sets
+and shift decisions; factor values within a rounding tolerance; solutions with
+a true relative residual <= 1e-8 (recomputed by the oracle's SpMV), within
+1e-6 of the oracle's solution, and iteration counts within max(1, 5 %).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2604_23979_gb300 import sdsl
+from paper_2604_23979_gb300 import workloads as W
+from tests.gpu_util import iters_close, rel, relres, run_bj, setup
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2604_23979_gb300 import build
+
+    build.build()
+    sdsl.load()
+
+
+def bits(a):
+    return np.ascontiguousarray(a, dtype=np.float64).view(np.int64)
+
+
+def check_structures(prob, ref, g):
+    rp, ci, v = g["S"]
+    assert np.array_equal(rp, ref.S.rowptr) and np.array_equal(ci, ref.S.col)
+    assert np.array_equal(bits(v), bits(ref.S.val)), "S values differ bitwise"
+    prp, pci, pv, fv, alpha = g["P"]
+    assert np.array_equal(prp, ref.P.rowptr), "filtered row pointers differ"
+    assert np.array_equal(pci, ref.P.col), "filtered pattern differs"
+    assert np.array_equal(bits(pv), bits(ref.P.val)), "corrected values differ bitwise"
+    assert np.array_equal(alpha, ref.alpha), "shift decisions differ"
+    for which, lev in ((0, ref.lev_lo), (1, ref.lev_up)):
+        nlev, lptr, rows = g["lev_lo"] if which == 0 else g["lev_up"]
+        rn, rp_, rr = oracle.level_lists(prob.block_ptr, lev)
+        assert np.array_equal(nlev, rn), f"level counts differ ({which})"
+        assert np.array_equal(lptr, rp_), f"level pointers differ ({which})"
+        assert np.array_equal(rows, rr), f"level rows differ ({which})"
+    return fv
+
+
+def check_factor(prob, ref, fv, tol):
+    P = ref.P
+    row = np.repeat(np.arange(P.nrows), np.diff(P.rowptr))
+    low = P.col <= row
+    for b in range(len(prob.block_ptr) - 1):
+        s, e = prob.block_ptr[b], prob.block_ptr[b + 1]
+        m = low & (row >= s) & (row < e)
+        if m.any():
+            assert rel(fv[m], ref.F[m]) <= tol, f"factor of block {b} off"
+
+
+def check_solution(prob, ref_state, ref_res, g, iters_exact=True):
+    st = g["stats"]
+    assert st["status"] == 0, st
+    x = g["x"]
+    true_rel = relres(ref_state.S, x, prob.b)
+    assert true_rel <= prob.rtol, true_rel
+    assert rel(x, ref_res.x) <= 1e-6
+    if iters_exact:
+        assert iters_close(st["iters"], ref_res.iters), (st["iters"], ref_res.iters)
+
+
+CASES = {
+    "c1": lambda: W.config1(),
+    "c1-small": lambda: W.config1(m=300, n=750),
+    "c2-5pct": lambda: W.config2(scale=0.05),
+}
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_bj_parity_fp64(case):
+    prob = CASES[case]()
+    ref_state, ref = oracle.bj_solve(prob)
+    assert ref.status == 0
+    g = run_bj(prob, 64)
+    fv = check_structures(prob, ref_state, g)
+    check_factor(prob, ref_state, fv, 1e-10)
+    check_solution(prob, ref_state, ref, g)
+
+
+@pytest.mark.parametrize("case", ["c1", "c2-5pct"])
+def test_bj_parity_fp32_factors(case):
+    """FP32 factors under the FP64 loop: same structures, factor values within
+    FP32 rounding, FP64 true residual <= 1e-8."""
+    prob = CASES[case]()
+    ref_state, ref = oracle.bj_solve(prob)
+    g = run_bj(prob, 32)
+    fv = check_structures(prob, ref_state, g)
+    check_factor(prob, ref_state, fv, 1e-6)
+    check_solution(prob, ref_state, ref, g, iters_exact=False)
+    # the FP32 apply is a slightly different preconditioner: report, bound loosely
+    assert g["stats"]["iters"] <= 1.5 * ref.iters + 5
+
+
+def test_graph_and_plain_launches_agree():
+    prob = W.config1(m=400, n=1000)
+    a = run_bj(prob, 64, graph_iters=0)
+    b = run_bj(prob, 64, graph_iters=16)
+    assert a["stats"]["iters"] == b["stats"]["iters"]
+    assert np.array_equal(bits(a["x"]), bits(b["x"]))
+
+
+def test_deterministic_bits():
+    prob = W.config2(scale=0.02)
+    a = run_bj(prob, 32)
+    b = run_bj(prob, 32)
+    assert np.array_equal(bits(a["x"]), bits(b["x"]))
+
+
+def test_device_and_host_pointers_agree():
+    import torch
+
+    prob = W.config1(m=500, n=1250)
+    host = run_bj(prob, 64)
+    h, keep = setup(prob, 64, device=True)
+    try:
+        sdsl.sdsl_factor(h)
+        b = torch.from_numpy(prob.b).cuda()
+        x = torch.zeros_like(b)
+        st = sdsl.sdsl_solve(h, b, x)
+        torch.cuda.synchronize()
+        assert st.status == 0
+        assert np.array_equal(bits(x.cpu().numpy()), bits(host["x"]))
+    finally:
+        sdsl.sdsl_free(h)
+
+
+def test_zero_rhs_and_exact_guess():
+    prob = W.config1(m=200, n=500)
+    ref_state, ref = oracle.bj_solve(prob)
+    g = run_bj(prob, 64, b=np.zeros(200))
+    assert g["stats"]["iters"] == 0 and not g["x"].any()
+    g = run_bj(prob, 64, x0=ref.x)
+    r0 = oracle.pcg_bj(ref_state.S, ref_state.P, ref_state.F, prob.block_ptr, prob.b, x0=ref.x)
+    assert g["stats"]["iters"] == r0.iters == 0
+
+
+def test_block_shapes_single_jacobi_empty_ragged():
+    base = W.config1(m=257, n=640)
+    for bp in ([0, 257], list(range(258)), [0, 10, 10, 100, 101, 257], [0, 1, 2, 3, 257]):
+        prob = W.config1(m=257, n=640)
+        prob.block_ptr = np.array(bp, dtype=np.int64)
+        ref_state, ref = oracle.bj_solve(prob)
+        g = run_bj(prob, 64)
+        check_structures(prob, ref_state, g)
+        check_solution(prob, ref_state, ref, g)
+    del base
+
+
+def test_empty_rows_of_A():
+    prob = W.config1(m=120, n=300)
+    A = prob.A
+    # drop every entry of rows 5 and 77: S_55 = S_77 = rho
+    keep = np.ones(A.nnz, bool)
+    for r in (5, 77):
+        keep[A.rowptr[r]:A.rowptr[r + 1]] = False
+    rows = np.repeat(np.arange(A.nrows), np.diff(A.rowptr))[keep]
+    A.col, A.val = A.col[keep], A.val[keep]
+    A.rowptr = np.zeros(A.nrows + 1, np.int64)
+    np.cumsum(np.bincount(rows, minlength=A.nrows), out=A.rowptr[1:])
+    ref_state, ref = oracle.bj_solve(prob)
+    g = run_bj(prob, 64)
+    check_structures(prob, ref_state, g)
+    check_solution(prob, ref_state, ref, g)
+
+
+def test_maxit_reached():
+    prob = W.config1(m=300, n=750)
+    prob.maxit = 5
+    ref_state, ref = oracle.bj_solve(prob)
+    assert ref.status == oracle.NOT_CONVERGED and ref.iters == 5
+    g = run_bj(prob, 64)
+    assert g["stats"]["status"] == sdsl.ERR_NOT_CONVERGED and g["stats"]["iters"] == 5
+    assert rel(g["x"], ref.x) <= 1e-9
+
+
+def test_argument_errors():
+    prob = W.config1(m=50, n=120)
+    o, keep = sdsl.options_for(prob)
+    A = prob.A
+    bad = A.col.copy()
+    bad[A.rowptr[3]], bad[A.rowptr[3] + 1] = bad[A.rowptr[3] + 1], bad[A.rowptr[3]]  # unsorted row
+    with pytest.raises(sdsl.SdslError) as e:
+        sdsl.sdsl_setup(o, A.nrows, A.ncols, A.rowptr, bad, A.val, prob.theta)
+    assert e.value.status == sdsl.ERR_ARG
+    bp = np.array([0, 10, 5, 50], np.int64)
+    o.block_ptr, o.nblocks = bp.ctypes.data, 3
+    with pytest.raises(sdsl.SdslError) as e:
+        sdsl.sdsl_setup(o, A.nrows, A.ncols, A.rowptr, A.col, A.val, prob.theta)
+    assert e.value.status == sdsl.ERR_ARG
+    h, keep2 = setup(prob)
+    try:
+        x = np.zeros(50)
+        with pytest.raises(sdsl.SdslError) as e:
+            sdsl.sdsl_solve(h, prob.b, x)
+        assert e.value.status == sdsl.ERR_STATE
+    finally:
+        sdsl.sdsl_free(h)
+
+
+def test_update_diag_values_and_reuse():
+    prob = W.config2(scale=0.02)
+    h, keep = setup(prob, 64)
+    try:
+        sdsl.sdsl_factor(h)
+        x1 = np.zeros(len(prob.b))
+        st1 = sdsl.sdsl_solve(h, prob.b, x1)
+        # unchanged theta: bit-identical solve
+        sdsl.sdsl_update_diag(h, prob.theta)
+        x2 = np.zeros(len(prob.b))
+        st2 = sdsl.sdsl_solve(h, prob.b, x2)
+        assert st1.iters == st2.iters and np.array_equal(bits(x1), bits(x2))
+        # new theta: S recomputed on the fixed pattern, bit-exact; factors kept
+        rng = np.random.default_rng(9)
+        theta2 = np.clip(prob.theta * np.exp(rng.normal(0, 0.5, len(prob.theta))), 1e-8, 1e8)
+        sdsl.sdsl_update_diag(h, theta2)
+        rp, ci, v = sdsl.sdsl_export_system(h)
+        S2 = oracle.normal_matrix(prob.A, theta2, prob.rho)
+        assert np.array_equal(ci, S2.col) and np.array_equal(bits(v), bits(S2.val))
+        x3 = np.zeros(len(prob.b))
+        st3 = sdsl.sdsl_solve(h, prob.b, x3)
+        # oracle: same stale preconditioner (built from theta), new S
+        ref = oracle.bj_setup_factor(prob.A, prob.theta, prob.rho, prob.block_ptr, prob.tau, prob.delta)
+        r3 = oracle.pcg_bj(S2, ref.P, ref.F, prob.block_ptr, prob.b, rtol=prob.rtol, maxit=prob.maxit)
+        assert st3.status == 0 and r3.status == 0
+        assert iters_close(st3.iters, r3.iters), (st3.iters, r3.iters)
+        assert relres(S2, x3, prob.b) <= 1e-8
+    finally:
+        sdsl.sdsl_free(h)
+
+
+def test_reuse_rule_sequence():
+    """Preconditioner reuse across an IPM-like theta sequence (Sec. 3.4): the
+    rebuild decisions of the library equal those of the rule replayed on the
+    oracle (rebuild when iters > 1.5 x the first solve after a build)."""
+    prob, thetas = W.config4(scale=0.002, nblocks=8, steps=8)
+    h, keep = setup(prob, 64)
+    gpu, ora = [], []
+    try:
+        sdsl.sdsl_factor(h)
+        for k, th in enumerate(thetas):
+            if k:
+                sdsl.sdsl_update_diag(h, th)
+            x = np.zeros(len(prob.b))
+            st = sdsl.sdsl_solve(h, prob.b, x)
+            gpu.append((st.iters, st.rebuilt))
+    finally:
+        sdsl.sdsl_free(h)
+    built_state, base, need = None, -1, True
+    for k, th in enumerate(thetas):
+        S = oracle.normal_matrix(prob.A, th, prob.rho)
+        rebuilt = 0
+        if need:
+            built_state = oracle.bj_setup_factor(prob.A, th, prob.rho, prob.block_ptr, prob.tau, prob.delta)
+            base, need, rebuilt = -1, False, int(k > 0)
+        r = oracle.pcg_bj(S, built_state.P, built_state.F, prob.block_ptr, prob.b, rtol=prob.rtol, maxit=prob.maxit)
+        if base < 0:
+            base = r.iters
+        elif r.iters > 1.5 * base:
+            need = True
+        ora.append((r.iters, rebuilt))
+    for (gi, gr), (oi, orb) in zip(gpu, ora):
+        assert iters_close(gi, oi), (gpu, ora)
+        assert gr == orb, (gpu, ora)
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+def test_full_size_config2_sampled(prec):
+    """Full 200k x 500k staircase in the benchmark's launch configuration:
+    S, the filtered pattern, corrected values, level sets and shifts compared in
+    full (bit-exact); factor values on every fourth block; the solution checked
+    by the oracle's FP64 true residual."""
+    prob = W.config2()
+    ref = oracle.bj_setup_factor(prob.A, prob.theta, prob.rho, prob.block_ptr, prob.tau, prob.delta)
+    g = run_bj(prob, prec)
+    fv = check_structures(prob, ref, g)
+    sub = W.NormalProblem(prob.A, prob.theta, prob.b, prob.block_ptr[::4], prob.rho, prob.tau, prob.delta)
+    P = ref.P
+    row = np.repeat(np.arange(P.nrows), np.diff(P.rowptr))
+    low = P.col <= row
+    for b in range(0, len(prob.block_ptr) - 1, 4):
+        s, e = prob.block_ptr[b], prob.block_ptr[b + 1]
+        m = low & (row >= s) & (row < e)
+        assert rel(fv[m], ref.F[m]) <= (1e-10 if prec == 64 else 1e-6)
+    del sub
+    assert g["stats"]["status"] == 0
+    assert relres(ref.S, g["x"], prob.b) <= 1e-8
