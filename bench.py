@@ -1,0 +1,415 @@
+#!/usr/bin/env python
+"""Benchmark of the Block-Jacobi PCG hot path on one GB300 (replicas for N > 1).
+
+Workload: the 200,000 x 500,000 staircase normal-equations system (64 uneven
+diagonal blocks, 8 nonzeros per column, 90 % in-block, theta log-uniform in
+[1e-3, 1e3], delta = 1e-4, tau = 1e-3), synthetic and seeded.  One step =
+one full time-to-1e-8 solve through the C ABI with A, theta and b resident
+in HBM: form S = A diag(theta) A^T + rho I, filter + correct + level sets +
+per-block IC(0) (FP32 factors), graph-captured PCG until the FP64 true
+relative residual is <= 1e-8.  The plain FP64-factor form is timed beside it.
+
+    python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+Prints one JSON line (rank 0).  `value` = solves/s over all ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time-to-1e-8 rel. residual, Krylov-iter HBM GB/s, served solves/s + p99"
+WORKLOAD = "staircase-normal-eq 200000x500000, 8/col 90% in-block, 64 uneven blocks (1k-6k rows), BJ-IC(0) PCG"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--prec", type=int, default=32, choices=[32, 64])
+    ap.add_argument("--scale", type=float, default=1.0, help="workload scale (1.0 = the benchmark size)")
+    ap.add_argument("--quick", action="store_true", help="no CPU baseline, e2e, FP64 form or profile pass")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# --------------------------------------------------------------------------- helpers
+
+def dist_init(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+
+        backend = os.environ.get("SDSL_BENCH_BACKEND", "nccl")
+        if backend == "nccl":
+            import torch
+
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def max_over_ranks(ws, value):
+    if ws == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(value)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate(ws, per_rank_units, per_rank_seconds):
+    """Whole-job throughput: units of all ranks / slowest rank's time."""
+    units = per_rank_units * ws
+    secs = max_over_ranks(ws, per_rank_seconds)
+    return units / secs, secs
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        return False
+
+    def summary(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        try:
+            rows = [r.split(",") for r in open(self.path).read().strip().splitlines() if r.strip()]
+        except OSError:
+            return out
+        finally:
+            try:
+                os.unlink(self.path)
+            except OSError:
+                pass
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except (ValueError, IndexError):
+                continue
+            for name, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(name)
+        if sm:
+            out.update(sm_mhz=statistics.median(sm), sm_max_mhz=max(mx), samples=len(sm))
+        out["reasons"] = sorted(reasons)
+        return out
+
+
+def source_hash():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2604_23979_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def ncu_traffic(kernel):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current kernel sources (else None)."""
+    try:
+        t = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+    except (OSError, ValueError):
+        return None
+    e = t.get(kernel)
+    if not e or e.get("source_hash") != source_hash():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+# --------------------------------------------------------------------------- our arm
+
+def run_ours(args, ws, rank, local):
+    import numpy as np
+    import torch
+
+    from paper_2604_23979_gb300 import build as pbuild
+    from paper_2604_23979_gb300 import sdsl
+    from paper_2604_23979_gb300 import workloads as W
+
+    pbuild.build()
+    sdsl.load()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    prob = W.config2(scale=args.scale)
+    A = prob.A
+    host = [np.ascontiguousarray(a) for a in (A.rowptr, A.col, A.val, prob.theta, prob.b)]
+    d_rp, d_ci, d_v, d_th, d_b = [torch.from_numpy(a).to(dev) for a in host]
+    d_x = torch.zeros_like(d_b)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > 129 MB L2
+    stream = torch.cuda.current_stream(dev)
+
+    def one_solve(prec, profile=False, host_io=False, xbuf=None, bbuf=None, arrays=None):
+        o, keep = sdsl.options_for(prob, factor_prec=prec, graph_iters=16, stream=stream.cuda_stream)
+        o.profile = 1 if profile else 0
+        arrs = arrays if arrays is not None else (d_rp, d_ci, d_v, d_th)
+        h = sdsl.sdsl_setup(o, A.nrows, A.ncols, *arrs)
+        try:
+            sdsl.sdsl_factor(h)
+            st = sdsl.sdsl_solve(h, bbuf if bbuf is not None else d_b, xbuf if xbuf is not None else d_x)
+            setup_st = sdsl.sdsl_get_stats(h)
+        finally:
+            end = torch.cuda.Event(enable_timing=True)
+            end.record(stream)
+            sdsl.sdsl_free(h)
+        return st, setup_st, end
+
+    def timed_steps(prec, k, l2flush=True):
+        times, stats = [], []
+        for _ in range(k):
+            if l2flush:
+                flush.zero_()
+            start = torch.cuda.Event(enable_timing=True)
+            start.record(stream)
+            st, sst, end = one_solve(prec)
+            end.synchronize()
+            times.append(start.elapsed_time(end))
+            stats.append((st, sst))
+        return times, stats
+
+    # warm-up
+    for _ in range(args.warmup):
+        one_solve(args.prec)
+    torch.cuda.synchronize()
+    barrier(ws)
+    torch.cuda.synchronize()
+    launches0 = sdsl.sdsl_kernel_launches()
+    with ClockSampler(local) as clk:
+        t0 = time.perf_counter()
+        times, stats = timed_steps(args.prec, args.steps)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+    barrier(ws)
+    torch.cuda.synchronize()
+    launches = sdsl.sdsl_kernel_launches() - launches0
+    clocks = clk.summary()
+    dev_s = sum(times) / 1000.0
+    value, slowest = aggregate(ws, args.steps, dev_s)
+    last, last_setup = stats[-1]
+    for st, _ in stats:
+        if st.status != 0 or st.rel_res_true > prob.rtol:
+            raise SystemExit(f"solve failed: status {st.status} relres {st.rel_res_true}")
+
+    out = {
+        "metric": METRIC,
+        "value": round(value, 4),
+        "unit": "solves/s",
+        "n_gpus": ws,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(statistics.mean(times), 3),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64 loop, f32 factors" if args.prec == 32 else "f64",
+        "data": "synthetic (seeded staircase LP matrix; the paper's datasets are not available)",
+        "config": {"workload": WORKLOAD if args.scale == 1.0 else WORKLOAD + f" scaled x{args.scale}",
+                   "n": A.nrows, "nnz_A": int(A.nnz), "nnz_S": int(last.nnz_system),
+                   "nnz_P": int(last.nnz_precond), "blocks": int(len(prob.block_ptr) - 1),
+                   "factor_prec": args.prec, "graph_iters": 16, "tol": prob.rtol,
+                   "l2": "256 MB buffer written between steps; working set > L2",
+                   "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU"},
+        "time_to_1e8_ms": round(statistics.median(times), 3),
+        "iters": int(last.iters),
+        "rel_res_true": last.rel_res_true,
+        "phases_ms": {"setup": round(last_setup.ms_setup, 3), "factor": round(last_setup.ms_factor, 3),
+                      "solve": round(last.ms_solve, 3)},
+        "shifted_blocks": int(last.shifted_blocks),
+        "levels_max": int(last.max_levels),
+        "krylov_iter_bytes": last.bytes_per_iter,
+        "krylov_iter_gbs": round(last.bytes_per_iter * last.iters / (last.ms_solve * 1e-3) / 1e9, 1),
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+        "wall_s": round(wall, 3),
+    }
+
+    if not args.quick and rank == 0:
+        # plain FP64 form on the same GPU (the benchmark spec comparison)
+        other = 64 if args.prec == 32 else 32
+        t_other, st_other = timed_steps(other, 2)
+        out["other_form"] = {"factor_prec": other, "time_to_1e8_ms": round(statistics.median(t_other), 3),
+                             "iters": int(st_other[-1][0].iters),
+                             "solve_ms": round(st_other[-1][0].ms_solve, 3),
+                             "factor_ms": round(st_other[-1][1].ms_factor, 3)}
+        # per-kernel device times inside one real solve (profile mode: events around every kernel)
+        pst, _, end = one_solve(args.prec, profile=True)
+        end.synchronize()
+        names = ["k_pcg_spmv", "k_pcg_update", "k_pcg_direction"]
+        tot = [pst.kernel_ms[i] for i in range(3)]
+        nl = [max(1, pst.kernel_launches[i]) for i in range(3)]
+        dom = max(range(3), key=lambda i: tot[i])
+        avg_ms = tot[dom] / nl[dom]
+        peaks, kind = measured_peaks()
+        achieved = pst.kernel_bytes[dom] / (avg_ms * 1e-3) / 1e9
+        out["kernels"] = {names[i]: {"launches": int(nl[i]), "avg_us": round(1000 * tot[i] / nl[i], 2),
+                                     "share": round(tot[i] / sum(tot), 3),
+                                     "alg_bytes_per_launch": pst.kernel_bytes[i],
+                                     "gbs": round(pst.kernel_bytes[i] / (tot[i] / nl[i] * 1e-3) / 1e9, 1)}
+                          for i in range(3)}
+        tr = ncu_traffic(names[dom])
+        out["roofline"] = {"kernel": names[dom], "bound": "hbm", "achieved": round(achieved, 1),
+                           "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 3),
+                           "traffic": tr, "peak_kind": kind,
+                           "note": "achieved = algorithmic bytes per launch / mean CUDA-event launch time in a "
+                                   "profiled solve of this workload"}
+        # end to end through the C ABI with host (pinned) buffers
+        pinned = [torch.from_numpy(a).pin_memory() for a in host[:4]]
+        hb = torch.from_numpy(host[4]).pin_memory()
+        hx = torch.zeros_like(hb).pin_memory()
+        e2e = []
+        for _ in range(2):
+            flush.zero_()
+            start = torch.cuda.Event(enable_timing=True)
+            start.record(stream)
+            st, _, end = one_solve(args.prec, xbuf=hx, bbuf=hb, arrays=pinned)
+            end.synchronize()
+            e2e.append(start.elapsed_time(end))
+        h2d = sum(a.numel() * a.element_size() for a in pinned) + hb.numel() * 8
+        out["e2e"] = {"value": round(1000.0 / statistics.median(e2e), 4), "unit": "solves/s",
+                      "ms_per_step": round(statistics.median(e2e), 3), "h2d_bytes_per_step": int(h2d),
+                      "d2h_bytes_per_step": int(hx.numel() * 8)}
+        if not args.no_cpu_baseline and ws == 1:
+            out["cpu_baseline"] = cpu_baseline(prob, int(last.iters))
+    return out
+
+
+# --------------------------------------------------------------------------- the oracle
+
+def oracle_sample(prob, n_iter=30):
+    """Time the oracle (single-threaded FP64 C) on a bounded sample of the
+    workload: full setup + filter/levels/IC(0), then n_iter PCG iterations."""
+    import oracle
+
+    t0 = time.perf_counter()
+    st = oracle.bj_setup_factor(prob.A, prob.theta, prob.rho, prob.block_ptr, prob.tau, prob.delta)
+    t1 = time.perf_counter()
+    r = oracle.pcg_bj(st.S, st.P, st.F, prob.block_ptr, prob.b, rtol=prob.rtol, maxit=n_iter)
+    t2 = time.perf_counter()
+    return t1 - t0, (t2 - t1) / max(1, r.iters)
+
+
+def oracle_iters(fallback):
+    try:
+        return int(json.load(open(os.path.join(ROOT, "oracle", "reference_counts.json")))["config2"]["iters"]), \
+            "oracle full solve (oracle/reference_counts.json)"
+    except (OSError, ValueError, KeyError):
+        return fallback, "GPU FP64-parity iteration count (oracle count file missing)"
+
+
+def cpu_baseline(prob, gpu_iters):
+    t_sf, t_it = oracle_sample(prob)
+    iters, src = oracle_iters(gpu_iters)
+    t = t_sf + iters * t_it
+    return {"value": round(1.0 / t, 6), "unit": "solves/s", "cores": 1, "kind": "oracle",
+            "sample": f"full setup+filter+levels+IC(0) ({t_sf:.1f} s) + 30 PCG iterations "
+                      f"({t_it * 1000:.1f} ms/iter), extrapolated to {iters} iterations ({src})",
+            "seconds_per_solve": round(t, 2)}
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return None
+    from paper_2604_23979_gb300 import workloads as W
+
+    prob = W.config2(scale=args.scale)
+    iters, src = oracle_iters(None)
+    per = []
+    for i in range(args.warmup + args.steps):
+        t_sf, t_it = oracle_sample(prob, n_iter=10)
+        if i >= args.warmup:
+            per.append((t_sf, t_it))
+    t_sf = statistics.mean(p[0] for p in per)
+    t_it = statistics.mean(p[1] for p in per)
+    n_it = iters if iters is not None else 1288
+    secs = t_sf + n_it * t_it
+    v = 1.0 / secs
+    return {"impl": "reference", "metric": METRIC, "value": round(v, 6), "unit": "solves/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(secs * 1000, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded staircase LP matrix)",
+            "config": {"workload": WORKLOAD, "n": prob.A.nrows},
+            "cpu_baseline": {"value": round(v, 6), "unit": "solves/s", "cores": 1, "kind": "oracle",
+                             "sample": f"each step: full setup+factor + 10 PCG iterations; extrapolated to "
+                                       f"{n_it} iterations ({src})"},
+            "e2e": {"value": round(v, 6), "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_init(args)
+    if args.impl == "reference":
+        out = run_reference(args, ws, rank)
+    else:
+        out = run_ours(args, ws, rank, local)
+    if rank == 0 and out is not None:
+        print(json.dumps(out), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

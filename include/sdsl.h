@@ -75,6 +75,15 @@ typedef struct {
   void* stream;                  /* cudaStream_t to order all work on; NULL = the legacy default stream */
   int graph_iters;               /* Krylov iterations captured per CUDA graph launch; 0 = no graphs */
   int tune;                      /* 1 = time candidate launch shapes at factor time and keep the fastest */
+  int profile;                   /* 1 = time every Krylov kernel with CUDA events (no graphs; slower) */
+  int apply_prec;                /* arithmetic of the triangular solves: 64 or 32; 0 = factor_prec */
+  int flexible;                  /* PCG beta: 0 = rho_new/rho, 1 = flexible z_new^T(r_new - r_old)/rho
+                                    (robust to an FP32 apply); -1 = 1 iff the apply is FP32 */
+  int solve_kernel;              /* block triangular solves: 0 auto, 1 level-synchronous (barrier per
+                                    level), 2 flag-synchronised (rows in level order, per-row ready flags
+                                    in shared memory; needs the block to fit in shared memory) */
+  int spmv_form;                 /* PCG product S p (normal form): 0 auto (fewer HBM bytes), 1 explicit
+                                    CSR of S, 2 factored A (theta o (A^T p)) + rho p */
 } sdsl_options;
 
 typedef struct {
@@ -94,6 +103,13 @@ typedef struct {
   int64_t shifted_blocks; /* blocks that needed a diagonal shift to factor */
   int64_t builds;         /* factorizations since setup */
   double bytes_per_iter;  /* algorithmic HBM bytes of one Krylov iteration (model) */
+  double kernel_ms[4];    /* profile mode: summed device time of the iteration kernels:
+                             [0] SpMV + p^T q, [1] update + preconditioner, [2] direction, [3] other */
+  int64_t kernel_launches[4];
+  double kernel_bytes[4]; /* algorithmic HBM bytes per launch of the kernels above (model) */
+  int64_t spmv_lanes;     /* lanes per row of the SpMV in use */
+  int64_t solve_lanes;    /* lanes per row of the block triangular solves in use */
+  int64_t tuned_spmv_lanes; /* choice of the autotuner (0 if it did not run) */
 } sdsl_stats;
 
 typedef struct {
@@ -104,7 +120,8 @@ typedef struct {
 
 /* Fill *o with the defaults: BJ-PCG, normal form, tau 1e-3, delta 1e-12,
  * rho 1e-6, FP64 factors, rtol 1e-8, maxit 2000, restart 30, refactor_ratio
- * 1.5, device pointers, default stream, graph_iters 16, tune 0. */
+ * 1.5, device pointers, default stream, graph_iters 16, tune 0, profile 0,
+ * apply_prec 0 (= factor_prec), flexible -1 (auto), solve_kernel 0 (auto), spmv_form 0 (auto). */
 void sdsl_default_options(sdsl_options* o);
 
 /* Create a handle and form the system matrix on the device.
@@ -181,6 +198,10 @@ sdsl_status sdsl_spmv(sdsl_handle h, const double* x, double* y);
 
 /* z = M^{-1} r with the current preconditioner (device pointers, FP64). */
 sdsl_status sdsl_precond_apply(sdsl_handle h, const double* r, double* z);
+
+/* Number of kernels this library has launched in the process so far (every
+ * launch, including those inside CUDA graphs, counted once). */
+int64_t sdsl_kernel_launches(void);
 
 const char* sdsl_status_str(sdsl_status s);
 const char* sdsl_last_error(void);

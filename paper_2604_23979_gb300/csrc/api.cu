@@ -13,6 +13,14 @@
 #include "kernels.cuh"
 #include "sdsl.h"
 
+#include <atomic>
+
+namespace sdsl {
+static std::atomic<long long> g_launches{0};
+void count_launch(long long k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+long long launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
+}  // namespace sdsl
+
 using namespace sdsl;
 
 namespace {
@@ -120,8 +128,8 @@ struct sdsl_handle_s {
   std::vector<int32_t> h_nlev_lo, h_nlev_up;
   int64_t tot_lo = 0, tot_up = 0;
   // Krylov workspace
-  double *b = nullptr, *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr;
-  double *part = nullptr, *part_rr = nullptr, *part_rz = nullptr, *scalars = nullptr;
+  double *b = nullptr, *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *u = nullptr;
+  double *part = nullptr, *part_blk = nullptr, *scalars = nullptr;
   int64_t* scan_scratch = nullptr;
   int* flag = nullptr;
   PcgState* state = nullptr;
@@ -130,6 +138,7 @@ struct sdsl_handle_s {
   TriSolve M{};
   cudaGraphExec_t graph = nullptr;
   int graph_iters = 0;
+  cudaEvent_t prof_ev[4] = {nullptr, nullptr, nullptr, nullptr};
   // reuse bookkeeping (Sec. 3.4)
   bool factored = false, need_rebuild = false;
   int64_t iters_post_build = -1;
@@ -192,6 +201,7 @@ sdsl_status alloc_workspace(sdsl_handle h) {
   TRY(h->sys.get(&h->z, N));
   TRY(h->sys.get(&h->p, N));
   TRY(h->sys.get(&h->q, N));
+  if (h->form == SDSL_FORM_NORMAL) TRY(h->sys.get(&h->u, h->n));
   TRY(h->sys.get(&h->part, 152 * 32 + 64));
   TRY(h->sys.get(&h->scalars, 16));
   TRY(h->sys.get(&h->state, 1));
@@ -310,17 +320,61 @@ sdsl_status form_augmented(sdsl_handle h, const int64_t* rbp, const int64_t* cbp
   return SDSL_OK;
 }
 
+int lanes_for(double avg) {  // about 12+ nonzeros per lane (FP64 instruction economy)
+  int lanes = 2;
+  while (lanes < 32 && lanes * 2 * 12.0 <= avg) lanes <<= 1;
+  return lanes;
+}
+
 void choose_spmv_plan(sdsl_handle h) {
   const double avg = h->N > 0 ? (double)h->s_nnz / (double)h->N : 1.0;
+  // Normal equations: the PCG product S p can use the factored form
+  // A (theta o (A^T p)) + rho p -- the same operator, 2 nnz(A) instead of
+  // nnz(S) multiply-adds and HBM entries.  Auto picks it when it moves fewer
+  // bytes; the explicit S stays for the filter and the true residual.
+  const int form = h->opt.spmv_form;
+  const bool can = h->form == SDSL_FORM_NORMAL && h->method == SDSL_BJ_PCG;
+  const bool fewer = 2.0 * (double)h->a_nnz < (double)h->s_nnz;
+  h->A.factored = can && (form == 2 || (form == 0 && fewer)) ? 1 : 0;
+  if (h->A.factored) {
+    h->A.ncols = h->n;
+    h->A.a_rp = h->a_rp; h->A.a_ci = h->a_ci; h->A.a_v = h->a_v;
+    h->A.at_rp = h->at_rp; h->A.at_ci = h->at_ci; h->A.at_v = h->at_v;
+    h->A.theta = h->theta;
+    h->A.rho = h->opt.rho;
+    h->A.u = h->u;
+    h->A.a_lanes = lanes_for(h->m > 0 ? (double)h->a_nnz / (double)h->m : 1.0);
+    h->A.at_lanes = lanes_for(h->n > 0 ? (double)h->a_nnz / (double)h->n : 1.0);
+    int64_t g2 = (h->n + 63) / 64;
+    h->A.at_grid = (int)std::max<int64_t>(1, std::min<int64_t>(g2, (int64_t)h->sms * 8));
+  }
   h->A.n = h->N;
   h->A.rp = h->s_rp;
   h->A.ci = h->s_ci;
   h->A.v = h->s_v;
-  h->A.lanes = pow2_lanes(avg, 3.0);
+  h->A.lanes = lanes_for(avg);
   const int64_t rows_per_cta_min = 64;
   int64_t g = (h->N + rows_per_cta_min - 1) / rows_per_cta_min;
   g = std::max<int64_t>(1, std::min<int64_t>(g, (int64_t)h->sms * 8));
   h->A.grid = (int)g;
+}
+
+// Autotuner: time the SpMV at every lane width on the handle's own matrix
+// and keep the fastest (ties keep the smaller width).
+sdsl_status tune_spmv(sdsl_handle h) {
+  float best = 1e30f;
+  int best_l = h->A.lanes;
+  SpmvPlan P = h->A;
+  TRY_CUDA(cudaMemsetAsync(h->p, 0, sizeof(double) * (size_t)h->N, h->st));
+  for (int l = 2; l <= 32; l <<= 1) {
+    P.lanes = l;
+    float ms = 0.f;
+    TRY_CUDA(time_spmv(P, h->p, h->q, 3, &ms, h->st));
+    if (ms < best * 0.98f) { best = ms; best_l = l; }
+  }
+  h->A.lanes = best_l;
+  h->stats.tuned_spmv_lanes = best_l;
+  return SDSL_OK;
 }
 
 sdsl_status destroy_graph(sdsl_handle h) {
@@ -334,8 +388,29 @@ sdsl_status destroy_graph(sdsl_handle h) {
 // One PCG iteration = three launches (see krylov.cu).
 sdsl_status enqueue_pcg_iteration(sdsl_handle h) {
   TRY_CUDA(pcg_spmv(h->A, h->p, h->q, h->part, h->state, h->st));
-  TRY_CUDA(pcg_update_precond(h->M, h->p, h->q, h->x, h->r, h->z, h->part_rr, h->part_rz, h->state, h->st));
+  TRY_CUDA(pcg_update_precond(h->M, h->p, h->q, h->x, h->r, h->z, h->part_blk, h->state, h->st));
   TRY_CUDA(pcg_direction(h->N, h->z, h->p, h->state, h->st));
+  return SDSL_OK;
+}
+
+// Profile mode: one iteration with CUDA events around each kernel; the
+// device times are accumulated into stats.kernel_ms / kernel_launches.
+sdsl_status profiled_iteration(sdsl_handle h) {
+  cudaEvent_t* e = h->prof_ev;
+  TRY_CUDA(cudaEventRecord(e[0], h->st));
+  TRY_CUDA(pcg_spmv(h->A, h->p, h->q, h->part, h->state, h->st));
+  TRY_CUDA(cudaEventRecord(e[1], h->st));
+  TRY_CUDA(pcg_update_precond(h->M, h->p, h->q, h->x, h->r, h->z, h->part_blk, h->state, h->st));
+  TRY_CUDA(cudaEventRecord(e[2], h->st));
+  TRY_CUDA(pcg_direction(h->N, h->z, h->p, h->state, h->st));
+  TRY_CUDA(cudaEventRecord(e[3], h->st));
+  TRY(sync(h, "profiled iteration"));
+  for (int k = 0; k < 3; ++k) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e[k], e[k + 1]);
+    h->stats.kernel_ms[k] += ms;
+    h->stats.kernel_launches[k] += 1;
+  }
   return SDSL_OK;
 }
 
@@ -344,10 +419,12 @@ sdsl_status build_graph(sdsl_handle h) {
   const int G = h->opt.graph_iters;
   if (G <= 0) return SDSL_OK;
   cudaGraph_t g = nullptr;
+  const long long before = launches_so_far();
   TRY_CUDA(cudaStreamBeginCapture(h->st, cudaStreamCaptureModeRelaxed));
   sdsl_status s = SDSL_OK;
   for (int i = 0; i < G && s == SDSL_OK; ++i) s = enqueue_pcg_iteration(h);
   cudaError_t e = cudaStreamEndCapture(h->st, &g);
+  count_launch(before - launches_so_far());  // captured, not executed: counted per graph launch
   if (s != SDSL_OK) { if (g) cudaGraphDestroy(g); return s; }
   if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
   e = cudaGraphInstantiate(&h->graph, g, 0);
@@ -419,46 +496,75 @@ sdsl_status factor_impl(sdsl_handle h) {
                    nlev_d));
   TRY(build_levels(h, 1, &h->lev_off_up, &h->lev_ptr_up, &h->lev_rows_up, h->h_nlev_up, &h->tot_up, cnt, lev, fa, fb,
                    nlev_d));
-  tmp.release();
-  // per-block factorization with the shift-retry rule
+  // per-block factorization with the shift-retry rule: a block is factored
+  // with diagonal p_ii + alpha p_ii for the first alpha of the ladder whose
+  // factor does not break down
   static const double kShifts[5] = {0.0, 1e-3, 1e-2, 1e-1, 1.0};
-  double* d_alpha;
-  int32_t *d_active, *d_status;
-  TRY(h->pc.get(&d_alpha, nb));
-  TRY(h->pc.get(&d_active, nb));
-  TRY(h->pc.get(&d_status, nb));
+  constexpr int kNS = 5;
   std::vector<int> tries(nb, 0);
-  std::vector<int32_t> active(nb, 1), status(nb, 0);
   h->h_alpha.assign(nb, 0.0);
   int64_t shifted = 0;
-  for (int round = 0; round < 5; ++round) {
-    for (int64_t k = 0; k < nb; ++k) h->h_alpha[k] = kShifts[tries[k]];
-    TRY(to_dev(h, d_alpha, h->h_alpha.data(), nb));
-    TRY(to_dev(h, d_active, active.data(), nb));
-    if (h->method == SDSL_BBD_GMRES)
+  if (h->method == SDSL_BJ_PCG) {
+    // IC(0): every shift of the ladder at once (nblocks x 5 CTAs), then pick
+    double *Fall, *dinv_all, *d_alpha;
+    int32_t *d_status, *d_choice;
+    TRY(tmp.get(&Fall, (size_t)kNS * h->p_nnz));
+    TRY(tmp.get(&dinv_all, (size_t)kNS * N));
+    TRY(h->pc.get(&d_alpha, kNS));
+    TRY(h->pc.get(&d_status, nb * kNS));
+    TRY(h->pc.get(&d_choice, nb));
+    TRY(to_dev(h, d_alpha, kShifts, kNS));
+    TRY_CUDA(ic0_factor_all(nb, h->d_bp, h->p_rp, h->p_ci, h->p_v, h->p_diag, h->lev_off_lo, h->lev_ptr_lo,
+                            h->lev_rows_lo, d_alpha, kNS, h->p_nnz, N, Fall, dinv_all, d_status, h->st));
+    std::vector<int32_t> status(nb * kNS), choice(nb);
+    TRY(to_host(h, status.data(), d_status, nb * kNS));
+    TRY(sync(h, "factor"));
+    for (int64_t k = 0; k < nb; ++k) {
+      int t = 0;
+      while (t < kNS && status[k * kNS + t]) ++t;
+      if (t == kNS) {
+        h->h_alpha[k] = -1.0;
+        tmp.release();
+        return fail(SDSL_ERR_BREAKDOWN, "block " + std::to_string(k) + " breaks down with every diagonal shift");
+      }
+      choice[k] = t;
+      tries[k] = t;
+    }
+    TRY(to_dev(h, d_choice, choice.data(), nb));
+    TRY_CUDA(pick_shift(h->d_bp, h->p_rp, d_choice, h->p_nnz, N, Fall, dinv_all, h->F, h->dinv, h->row_block,
+                        h->h_bp[nb], h->st));
+    tmp.release();
+  } else {
+    double* d_alpha;
+    int32_t *d_active, *d_status;
+    TRY(h->pc.get(&d_alpha, nb));
+    TRY(h->pc.get(&d_active, nb));
+    TRY(h->pc.get(&d_status, nb));
+    std::vector<int32_t> active(nb, 1), status(nb, 0);
+    for (int round = 0; round < kNS; ++round) {
+      for (int64_t k = 0; k < nb; ++k) h->h_alpha[k] = kShifts[tries[k]];
+      TRY(to_dev(h, d_alpha, h->h_alpha.data(), nb));
+      TRY(to_dev(h, d_active, active.data(), nb));
       TRY_CUDA(ilu0_factor(nb, h->d_bp, h->p_rp, h->p_ci, h->p_v, h->p_diag, h->lev_off_lo, h->lev_ptr_lo,
                            h->lev_rows_lo, d_alpha, d_active, h->F, h->dinv, d_status, h->st));
-    else
-      TRY_CUDA(ic0_factor(nb, h->d_bp, h->p_rp, h->p_ci, h->p_v, h->p_diag, h->lev_off_lo, h->lev_ptr_lo,
-                          h->lev_rows_lo, d_alpha, d_active, h->F, h->dinv, d_status, h->st));
-    TRY(to_host(h, status.data(), d_status, nb));
-    TRY(sync(h, "factor"));
-    bool any = false;
-    for (int64_t k = 0; k < nb; ++k) {
-      if (active[k] && status[k]) {
-        any = true;
-        tries[k] += 1;
-        if (tries[k] >= 5) {
-          h->h_alpha[k] = -1.0;
-          return fail(SDSL_ERR_BREAKDOWN, "block " + std::to_string(k) + " breaks down with every diagonal shift");
+      TRY(to_host(h, status.data(), d_status, nb));
+      TRY(sync(h, "factor"));
+      bool any = false;
+      for (int64_t k = 0; k < nb; ++k) {
+        if (active[k] && status[k]) {
+          any = true;
+          if (++tries[k] >= kNS) {
+            h->h_alpha[k] = -1.0;
+            return fail(SDSL_ERR_BREAKDOWN, "block " + std::to_string(k) + " breaks down with every diagonal shift");
+          }
+        } else {
+          active[k] = 0;
         }
-      } else {
-        active[k] = 0;
       }
+      if (!any) break;
     }
-    for (int64_t k = 0; k < nb; ++k) active[k] = active[k] && status[k];
-    if (!any) break;
   }
+  tmp.release();
   for (int64_t k = 0; k < nb; ++k) {
     h->h_alpha[k] = kShifts[tries[k]];
     shifted += tries[k] > 0;
@@ -508,10 +614,68 @@ sdsl_status factor_impl(sdsl_handle h) {
     if (f32) TRY(h->pc.get(&M.yscratch, N));
     else TRY(h->pc.get(&M.yscratch64, N));
   }
-  TRY(h->pc.get(&h->part_rr, nb + 32));
-  TRY(h->pc.get(&h->part_rz, nb + 32));
+  TRY(h->pc.get(&h->part_blk, 3 * nb + 32));
+  // level-ordered packed triangles for the flag-synchronised solves
+  const int apply = h->opt.apply_prec == 0 ? (f32 ? 32 : 64) : h->opt.apply_prec;
+  M.apply_prec = apply;
+  M.flexible = h->opt.flexible < 0 ? (apply == 32 ? 1 : 0) : (h->opt.flexible ? 1 : 0);
+  M.threads = 1024;
+  const bool fits = sf_smem_bytes(maxb, apply == 32 ? 4 : 8) <= (size_t)200 * 1024;
+  if (h->opt.solve_kernel == 2 && !fits)
+    return fail(SDSL_ERR_ARG, "flag-synchronised solves need the largest block to fit in shared memory");
+  M.sync_free = (h->opt.solve_kernel == 2 || (h->opt.solve_kernel == 0 && fits)) ? 1 : 0;
+  if (M.sync_free) {
+    const double avg_half2 = N > 0 ? (double)(h->p_nnz - N) / (2.0 * (double)N) : 1.0;
+    M.lanes = std::max(4, pow2_lanes(avg_half2, 4.0));
+    const int RW = 32 / M.lanes;
+    const int64_t nrows = h->h_bp[nb];
+    const size_t vs = f32 ? 4 : 8;
+    std::vector<int32_t> lptr, lrows, sched;
+    std::vector<int64_t> pos(nb + 1);
+    for (int dir = 0; dir < 2; ++dir) {
+      const int64_t tot = dir == 0 ? h->tot_lo : h->tot_up;
+      const std::vector<int32_t>& nl = dir == 0 ? h->h_nlev_lo : h->h_nlev_up;
+      lptr.resize(tot + 1);
+      lrows.resize(nrows);
+      TRY(to_host(h, lptr.data(), dir == 0 ? h->lev_ptr_lo : h->lev_ptr_up, tot + 1));
+      TRY(to_host(h, lrows.data(), dir == 0 ? h->lev_rows_lo : h->lev_rows_up, nrows));
+      TRY(sync(h, "schedule"));
+      // rows in level order, every level padded to whole warp tiles (-1)
+      sched.clear();
+      int64_t L = 0;
+      for (int64_t k = 0; k < nb; ++k) {
+        pos[k] = (int64_t)sched.size();
+        for (int32_t l = 0; l < nl[k]; ++l, ++L) {
+          for (int32_t q = lptr[L]; q < lptr[L + 1]; ++q) sched.push_back(lrows[q]);
+          while (sched.size() % RW) sched.push_back(-1);
+        }
+      }
+      pos[nb] = (int64_t)sched.size();
+      const int64_t npos = pos[nb];
+      int32_t *d_sched, *col, *prow;
+      int64_t *off, *d_pos;
+      void *val, *pdv;
+      TRY(h->pc.get(&d_sched, npos));
+      TRY(h->pc.get(&d_pos, nb + 1));
+      TRY(to_dev(h, d_sched, sched.data(), npos));
+      TRY(to_dev(h, d_pos, pos.data(), nb + 1));
+      TRY(h->pc.get(&off, npos + 1));
+      TRY_CUDA(pack_count(dir, npos, h->row_block, h->d_bp, h->p_rp, h->p_ci, h->p_diag, d_sched, off, h->st));
+      int64_t tot_e = 0;
+      TRY(scan_total(h, off, npos, &tot_e));
+      TRY(h->pc.get(&col, tot_e));
+      TRY(h->pc.get(reinterpret_cast<unsigned char**>(&val), tot_e * vs));
+      TRY(h->pc.get(reinterpret_cast<unsigned char**>(&pdv), npos * vs));
+      TRY(h->pc.get(&prow, npos));
+      TRY_CUDA(pack_fill(dir, npos, h->row_block, h->d_bp, h->p_rp, h->p_ci, h->p_diag, d_sched, h->F, h->dinv,
+                         f32 ? 32 : 64, off, col, val, pdv, prow, h->st));
+      if (dir == 0) { M.fwd_off = off; M.fwd_col = col; M.fwd_val = val; M.fwd_dinv = pdv; M.fwd_row = prow; M.fwd_pos = d_pos; }
+      else { M.bwd_off = off; M.bwd_col = col; M.bwd_val = val; M.bwd_dinv = pdv; M.bwd_row = prow; M.bwd_pos = d_pos; }
+    }
+  }
   choose_spmv_plan(h);
-  if (h->method == SDSL_BJ_PCG) TRY(build_graph(h));
+  if (h->opt.tune) TRY(tune_spmv(h));
+  if (h->method == SDSL_BJ_PCG && !h->opt.profile) TRY(build_graph(h));
   cudaEventRecord(h->ev_b, h->st);
   TRY(sync(h, "factor end"));
   h->factored = true;
@@ -520,6 +684,8 @@ sdsl_status factor_impl(sdsl_handle h) {
   h->stats.ms_factor = elapsed(h);
   h->stats.nnz_precond = h->p_nnz;
   h->stats.nnz_factor = h->method == SDSL_BBD_GMRES ? h->p_nnz : (h->p_nnz + N) / 2;
+  h->stats.spmv_lanes = h->A.lanes;
+  h->stats.solve_lanes = h->M.lanes;
   h->stats.levels_lower = h->tot_lo;
   h->stats.levels_upper = h->tot_up;
   int64_t mx = 0;
@@ -527,11 +693,25 @@ sdsl_status factor_impl(sdsl_handle h) {
   h->stats.max_levels = mx;
   h->stats.shifted_blocks = shifted;
   h->stats.builds += 1;
-  // algorithmic bytes of one PCG iteration (see the design doc for the model)
+  // Algorithmic HBM bytes per launch of the three PCG kernels: every array
+  // the kernel must touch, once (gathers of vector entries counted once).
+  //  SpMV:    values + columns of S (12 B/nnz), row pointers, read p, write q.
+  //  update:  read p, q, x, r; write x, r, z; strict lower and upper factor
+  //           values + columns; inverse diagonal; row pointers and diagonal
+  //           positions (read by both solves); level row lists (both solves).
+  //  direct.: read z, p; write p.
   const double sf = f32 ? 4.0 : 8.0;
-  const double nnzL = (double)h->stats.nnz_factor;
-  h->stats.bytes_per_iter = 12.0 * (double)h->s_nnz + 8.0 * (double)(N + 1) + 2.0 * ((sf + 4.0) * nnzL) +
-                            2.0 * 8.0 * (double)(N + 1) + 8.0 * (double)N * 13.0;
+  const double Nd = (double)N;
+  const double offd = (double)(h->p_nnz - N);
+  h->stats.kernel_bytes[0] = 12.0 * (double)h->s_nnz + 8.0 * (Nd + 1.0) + 16.0 * Nd;
+  if (h->A.factored)  // A^T p (+theta, u) then A u (+p, q): both CSR streams once
+    h->stats.kernel_bytes[0] = 24.0 * (double)h->a_nnz + 8.0 * ((double)h->n + 1.0) + 8.0 * (Nd + 1.0) +
+                               8.0 * Nd + 24.0 * (double)h->n + 16.0 * Nd;
+  h->stats.kernel_bytes[1] = 56.0 * Nd + (sf + 4.0) * offd + sf * Nd + 2.0 * 8.0 * (Nd + 1.0) + 2.0 * 8.0 * Nd +
+                             2.0 * 4.0 * Nd;
+  h->stats.kernel_bytes[2] = 24.0 * Nd;
+  h->stats.kernel_bytes[3] = 0.0;
+  h->stats.bytes_per_iter = h->stats.kernel_bytes[0] + h->stats.kernel_bytes[1] + h->stats.kernel_bytes[2];
   return SDSL_OK;
 }
 
@@ -563,17 +743,21 @@ sdsl_status pcg_solve(sdsl_handle h, sdsl_stats* st_out) {
     return SDSL_OK;
   }
   TRY_CUDA(pcg_init_state(h->state, tol2, h->opt.maxit, h->st));
-  TRY_CUDA(precond_apply(h->M, h->r, h->z, h->p, h->part_rr, h->part_rz, h->state, 1, h->st));
+  TRY_CUDA(precond_apply(h->M, h->r, h->z, h->p, h->part_blk, h->state, 1, h->st));
   sdsl_status result = SDSL_ERR_NOT_CONVERGED;
   for (;;) {
-    if (h->graph) {
+    if (h->opt.profile) {
+      TRY(profiled_iteration(h));
+    } else if (h->graph) {
       TRY_CUDA(cudaGraphLaunch(h->graph, h->st));
+      count_launch(3LL * h->graph_iters);
     } else {
       for (int i = 0; i < 8; ++i) TRY(enqueue_pcg_iteration(h));
     }
     TRY(to_host(h, h->h_state, h->state, 1));
     TRY(sync(h, "pcg iterations"));
     const PcgState& hs = *h->h_state;
+    if (hs.err) return fail(SDSL_ERR_TIMEOUT, "a triangular-solve wait exceeded its bound");
     if (!hs.done) continue;
     if (hs.done == 3) { result = SDSL_ERR_BREAKDOWN; break; }
     if (hs.done == 2) { result = SDSL_ERR_NOT_CONVERGED; break; }
@@ -586,7 +770,7 @@ sdsl_status pcg_solve(sdsl_handle h, sdsl_stats* st_out) {
     // restart from r = b - S x with a fresh direction
     S.restarts += 1;
     TRY_CUDA(true_residual(h->A, h->b, h->x, h->r, h->part, h->state, 1, h->st));
-    TRY_CUDA(precond_apply(h->M, h->r, h->z, h->p, h->part_rr, h->part_rz, h->state, 1, h->st));
+    TRY_CUDA(precond_apply(h->M, h->r, h->z, h->p, h->part_blk, h->state, 1, h->st));
     TRY_CUDA(cudaMemsetAsync(&h->state->done, 0, sizeof(int), h->st));
   }
   // final true residual (also for not-converged / breakdown exits)
@@ -625,6 +809,8 @@ void sdsl_default_options(sdsl_options* o) {
   o->refactor_ratio = 1.5;
   o->mem_space = SDSL_MEM_DEVICE;
   o->graph_iters = 16;
+  o->apply_prec = 0;
+  o->flexible = -1;
 }
 
 const char* sdsl_status_str(sdsl_status s) {
@@ -643,6 +829,8 @@ const char* sdsl_status_str(sdsl_status s) {
 
 const char* sdsl_last_error(void) { return g_err.c_str(); }
 
+int64_t sdsl_kernel_launches(void) { return (int64_t)launches_so_far(); }
+
 sdsl_status sdsl_free(sdsl_handle h) {
   if (!h) return SDSL_OK;
   destroy_graph(h);
@@ -655,6 +843,8 @@ sdsl_status sdsl_free(sdsl_handle h) {
   if (h->ev_a) cudaEventDestroy(h->ev_a);
   if (h->ev_b) cudaEventDestroy(h->ev_b);
   if (h->ev_join) cudaEventDestroy(h->ev_join);
+  for (cudaEvent_t e : h->prof_ev)
+    if (e) cudaEventDestroy(e);
   if (h->st) cudaStreamDestroy(h->st);
   delete h;
   return SDSL_OK;
@@ -669,6 +859,12 @@ sdsl_status sdsl_setup(const sdsl_options* opt, int64_t m, int64_t n, const int6
   if (opt->form < SDSL_FORM_CSR || opt->form > SDSL_FORM_AUGMENTED) return fail(SDSL_ERR_ARG, "unknown form");
   if (opt->method != SDSL_BJ_PCG && opt->method != SDSL_BBD_GMRES) return fail(SDSL_ERR_ARG, "unknown method");
   if (opt->factor_prec != 64 && opt->factor_prec != 32) return fail(SDSL_ERR_ARG, "factor_prec must be 64 or 32");
+  if (opt->solve_kernel < 0 || opt->solve_kernel > 2) return fail(SDSL_ERR_ARG, "solve_kernel must be 0, 1 or 2");
+  if (opt->spmv_form < 0 || opt->spmv_form > 2) return fail(SDSL_ERR_ARG, "spmv_form must be 0, 1 or 2");
+  if (opt->apply_prec != 0 && opt->apply_prec != 64 && opt->apply_prec != 32)
+    return fail(SDSL_ERR_ARG, "apply_prec must be 0, 32 or 64");
+  if (opt->factor_prec == 64 && opt->apply_prec == 32)
+    return fail(SDSL_ERR_ARG, "an FP32 apply needs FP32 factors (factor_prec 32)");
   if (!(opt->tau >= 0.0) || !(opt->delta >= 0.0) || !(opt->rtol > 0.0) || opt->maxit < 0)
     return fail(SDSL_ERR_ARG, "tau, delta must be >= 0, rtol > 0, maxit >= 0");
   if (opt->form == SDSL_FORM_CSR && m != n) return fail(SDSL_ERR_ARG, "CSR form needs a square matrix");
@@ -697,7 +893,9 @@ sdsl_status sdsl_setup(const sdsl_options* opt, int64_t m, int64_t n, const int6
   h->user = (cudaStream_t)opt->stream;
   if (cudaStreamCreateWithFlags(&h->st, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreate(&h->ev_a) != cudaSuccess || cudaEventCreate(&h->ev_b) != cudaSuccess ||
-      cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+      cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreate(&h->prof_ev[0]) != cudaSuccess || cudaEventCreate(&h->prof_ev[1]) != cudaSuccess ||
+      cudaEventCreate(&h->prof_ev[2]) != cudaSuccess || cudaEventCreate(&h->prof_ev[3]) != cudaSuccess) {
     sdsl_free(h);
     return fail(SDSL_ERR_CUDA, "stream/event creation failed");
   }
@@ -904,7 +1102,7 @@ sdsl_status sdsl_precond_apply(sdsl_handle h, const double* r, double* z) {
   if (!h || !r || !z) return fail(SDSL_ERR_ARG, "NULL argument");
   if (!h->factored) return fail(SDSL_ERR_STATE, "no preconditioner yet");
   Scope scope(h);
-  TRY_CUDA(precond_apply(h->M, r, z, nullptr, h->part_rr, h->part_rz, h->state, 2, h->st));
+  TRY_CUDA(precond_apply(h->M, r, z, nullptr, h->part_blk, h->state, 2, h->st));
   return SDSL_OK;
 }
 

@@ -79,6 +79,11 @@ __device__ __forceinline__ int64_t bsearch_i32(const int32_t* __restrict__ a, in
   return -1;
 }
 
+// Process-wide count of kernel launches made by this library (every
+// `<<<...>>>` launch site calls count_launch once per launch).
+void count_launch(long long k = 1);
+long long launches_so_far();
+
 // Exclusive prefix sum (in place) of an int64 array of length n+1 whose first
 // n entries are counts; entry n receives the total.  Three launches:
 // chunk sums, scan of chunk sums, chunk-local scan.

@@ -53,10 +53,17 @@ cudaError_t levels(int dir, int64_t nblocks, const int64_t* bp, const int64_t* p
                    cudaStream_t st);
 cudaError_t level_lists(int64_t nblocks, const int64_t* bp, const int32_t* lev, const int32_t* lev_off,
                         int32_t* hist, int32_t* level_ptr, int32_t* level_rows, cudaStream_t st);
-cudaError_t ic0_factor(int64_t nblocks, const int64_t* bp, const int64_t* prp, const int32_t* pci, const double* pv,
-                       const int64_t* pdiag, const int32_t* lev_off, const int32_t* level_ptr,
-                       const int32_t* level_rows, const double* alpha, const int32_t* active, double* F,
-                       double* dinv, int32_t* status, cudaStream_t st);
+// IC(0) of every block with every shift of the retry ladder at once: CTA
+// (b, t) writes block b's factor for alpha[t] into Fall + t*nnz, dinv_all +
+// t*n, and status[b*nshift + t] (1 = breakdown).  pick_shift copies the
+// chosen shift's factor of each block into F / dinv.
+cudaError_t ic0_factor_all(int64_t nblocks, const int64_t* bp, const int64_t* prp, const int32_t* pci,
+                           const double* pv, const int64_t* pdiag, const int32_t* lev_off, const int32_t* level_ptr,
+                           const int32_t* level_rows, const double* alpha, int nshift, int64_t nnz, int64_t n,
+                           double* Fall, double* dinv_all, int32_t* status, cudaStream_t st);
+cudaError_t pick_shift(const int64_t* bp, const int64_t* prp, const int32_t* choice, int64_t nnz, int64_t n,
+                       const double* Fall, const double* dinv_all, double* F, double* dinv, const int32_t* rb,
+                       int64_t nrows, cudaStream_t st);
 cudaError_t ilu0_factor(int64_t nblocks, const int64_t* bp, const int64_t* prp, const int32_t* pci, const double* pv,
                         const int64_t* pdiag, const int32_t* lev_off, const int32_t* level_ptr,
                         const int32_t* level_rows, const double* alpha, const int32_t* active, double* F,
@@ -79,7 +86,8 @@ struct PcgState {
   long long iters;
   long long maxit;
   int done;        // 0 running, 1 recurrence converged, 2 maxit, 3 breakdown
-  int pad;
+  int err;         // 1 = a bounded device wait gave up (SDSL_ERR_TIMEOUT)
+  double zq;       // z_new^T q (flexible beta)
   unsigned int ticket[4];
 };
 
@@ -105,7 +113,42 @@ struct TriSolve {  // block triangular factors on the layout of P
   int64_t max_block;    // largest block (rows) -> shared-memory staging if it fits
   float* yscratch;      // global staging when the block does not fit in shared memory
   double* yscratch64;
+  // Level-ordered packed copies of the strict triangles for the flag-
+  // synchronised solves: position q of block b (row lev_rows[q]) owns entries
+  // [off[q], off[q+1]) with block-local columns; values and inverse diagonal in
+  // the storage precision (float or double).
+  const int64_t* fwd_off;
+  const int32_t* fwd_col;
+  const void* fwd_val;
+  const void* fwd_dinv;
+  const int32_t* fwd_row;   // block-local row of position q
+  const int64_t* bwd_off;
+  const int32_t* bwd_col;
+  const void* bwd_val;
+  const void* bwd_dinv;
+  const int32_t* bwd_row;
+  const int64_t* fwd_pos;   // per block: first position of its padded schedule (nblocks+1)
+  const int64_t* bwd_pos;
+  int sync_free;        // 1: packed flag-synchronised solves (block fits in shared memory)
+  int apply_prec;       // arithmetic of the apply: 64 or 32
+  int flexible;         // 1: beta = -alpha z_new^T q / rho (robust to an inexact FP32 apply)
+  int threads;          // CTA size of the solve kernel
 };
+
+// Packed level-ordered triangle of one direction (dir 0 = strict lower in
+// lower-level order, 1 = strict upper in upper-level order).  pack_count
+// writes the entry count of every position into off[0..npos); the caller
+// scans it into offsets; pack_fill copies columns (block-local), values and
+// inverse diagonals (float if prec == 32 else double) and block-local rows.
+// lev_rows here is the padded schedule: the global row of every position, or
+// -1 for a padding position (levels are padded to whole warp tiles).
+cudaError_t pack_count(int dir, int64_t npos, const int32_t* row_block, const int64_t* bp, const int64_t* prp,
+                       const int32_t* pci, const int64_t* pdiag, const int32_t* lev_rows, int64_t* off,
+                       cudaStream_t st);
+cudaError_t pack_fill(int dir, int64_t npos, const int32_t* row_block, const int64_t* bp, const int64_t* prp,
+                      const int32_t* pci, const int64_t* pdiag, const int32_t* lev_rows, const double* F,
+                      const double* dinv, int prec, const int64_t* off, int32_t* col, void* val, void* pdinv,
+                      int32_t* prow, cudaStream_t st);
 
 struct SpmvPlan {
   int64_t n;
@@ -114,20 +157,34 @@ struct SpmvPlan {
   const double* v;
   int lanes;      // lanes per row (2..32)
   int grid;       // CTAs (fixed => deterministic partial sums)
+  // factored form of the normal-equation operator, S p = A (theta o (A^T p)) + rho p
+  int factored;   // 1: the PCG products use the factored form
+  int64_t ncols;  // columns of A
+  const int64_t* a_rp;  const int32_t* a_ci;  const double* a_v;    // A (m x n)
+  const int64_t* at_rp; const int32_t* at_ci; const double* at_v;   // A^T (n x m)
+  const double* theta;
+  double rho;
+  double* u;      // scratch, n entries
+  int at_lanes, a_lanes;
+  int at_grid;
 };
 
 cudaError_t spmv(const SpmvPlan& A, const double* x, double* y, cudaStream_t st);
+cudaError_t time_spmv(const SpmvPlan& A, const double* x, double* y, int reps, float* ms, cudaStream_t st);
 // q = A p, partial p^T q; last CTA: alpha = rho/pq, iters++.
 cudaError_t pcg_spmv(const SpmvPlan& A, const double* p, double* q, double* part, PcgState* s, cudaStream_t st);
 // x += alpha p, r -= alpha q, z = M^{-1} r per block; last CTA: convergence, beta.
+// part: 3 sections of nblocks partial sums [||r||^2 | r^T z | z^T q].
 cudaError_t pcg_update_precond(const TriSolve& M, const double* p, const double* q, double* x, double* r, double* z,
-                               double* part_rr, double* part_rz, PcgState* s, cudaStream_t st);
+                               double* part, PcgState* s, cudaStream_t st);
+// Dynamic shared memory of the flag-synchronised solve for a block size.
+size_t sf_smem_bytes(int64_t max_block, size_t tc_size);
 // p = z + beta p
 cudaError_t pcg_direction(int64_t n, const double* z, double* p, PcgState* s, cudaStream_t st);
 // z = M^{-1} r (no update).  mode 1: also p_out = z, s->rho = r^T z, s->rr =
 // ||r||^2 (PCG start / restart); mode 2: z only.
-cudaError_t precond_apply(const TriSolve& M, const double* r, double* z, double* p_out, double* part_rr,
-                          double* part_rz, PcgState* s, int mode, cudaStream_t st);
+cudaError_t precond_apply(const TriSolve& M, const double* r, double* z, double* p_out, double* part, PcgState* s,
+                          int mode, cudaStream_t st);
 // t = b - A x, ||t||^2 -> s->tr; if write_r, r = t.
 cudaError_t true_residual(const SpmvPlan& A, const double* b, const double* x, double* r, double* part,
                           PcgState* s, int write_r, cudaStream_t st);

@@ -49,7 +49,27 @@ __device__ __forceinline__ double row_dot(const int64_t* __restrict__ rp, const 
   double acc = 0.0;
   if (valid) {
     const int64_t s = rp[i], e = rp[i + 1];
-    for (int64_t t = s + sub; t < e; t += V) acc = __fma_rn(v[t], __ldg(x + ci[t]), acc);
+    int64_t t = s + sub;
+    // Four independent column/value loads in flight per lane before the
+    // gathers (memory-level parallelism) and four independent accumulators
+    // (no FMA latency chain).  S is streamed (evict-first); x is gathered
+    // through the read-only path and stays in L2.  On GB300 the FP64 pipe is
+    // a co-bound of this kernel, so few lanes per row (long per-lane runs,
+    // one shuffle reduction per row) keep FP64 instructions close to one
+    // per nonzero.
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    for (; t + 3 * V < e; t += 4 * V) {
+      const int32_t c0 = __ldcs(ci + t), c1 = __ldcs(ci + t + V), c2 = __ldcs(ci + t + 2 * V),
+                    c3 = __ldcs(ci + t + 3 * V);
+      const double v0 = __ldcs(v + t), v1 = __ldcs(v + t + V), v2 = __ldcs(v + t + 2 * V), v3 = __ldcs(v + t + 3 * V);
+      const double x0 = __ldg(x + c0), x1 = __ldg(x + c1), x2 = __ldg(x + c2), x3 = __ldg(x + c3);
+      a0 = __fma_rn(v0, x0, a0);
+      a1 = __fma_rn(v1, x1, a1);
+      a2 = __fma_rn(v2, x2, a2);
+      a3 = __fma_rn(v3, x3, a3);
+    }
+    for (; t < e; t += V) a0 = __fma_rn(__ldcs(v + t), __ldg(x + __ldcs(ci + t)), a0);
+    acc = (a0 + a1) + (a2 + a3);
   }
   return group_sum<V>(acc);
 }
@@ -96,6 +116,67 @@ __global__ void __launch_bounds__(kThreads) k_pcg_spmv(int64_t n, const int64_t*
       loc = __fma_rn(p[i], acc, loc);
     }
   }
+  const double tot = block_sum(loc, sh);
+  if (threadIdx.x == 0) part[blockIdx.x] = tot;
+  if (last_block(&s->ticket[0])) {
+    if (threadIdx.x < 32) {
+      const double pq = warp_fixed_sum(part, gridDim.x);
+      if (threadIdx.x == 0) {
+        s->pq = pq;
+        s->alpha = s->rho / pq;
+        s->iters += 1;
+        if (!(pq > 0.0) || !isfinite(pq)) s->done = 3;
+        s->ticket[0] = 0;
+      }
+    }
+  }
+}
+
+// Factored normal-equation product, first half: u = theta o (A^T p).
+template <int V>
+__global__ void __launch_bounds__(kThreads) k_at_theta(int64_t n, const int64_t* __restrict__ at_rp,
+                                                       const int32_t* __restrict__ at_ci,
+                                                       const double* __restrict__ at_v,
+                                                       const double* __restrict__ theta,
+                                                       const double* __restrict__ p, double* __restrict__ u,
+                                                       const PcgState* __restrict__ s) {
+  if (s && s->done) return;
+  int64_t r0, r1;
+  cta_rows(n, r0, r1);
+  const int g = threadIdx.x / V, sub = threadIdx.x % V, ng = kThreads / V;
+  for (int64_t base = r0; base < r1; base += ng) {
+    const int64_t k = base + g;
+    const bool valid = k < r1;
+    const double acc = row_dot<V>(at_rp, at_ci, at_v, p, k, sub, valid);
+    if (valid && sub == 0) u[k] = theta[k] * acc;
+  }
+}
+
+// Second half: q = A u + rho p, partial p^T q; last CTA: alpha, iters.
+template <int V>
+__global__ void __launch_bounds__(kThreads) k_a_u_dot(int64_t m, const int64_t* __restrict__ a_rp,
+                                                      const int32_t* __restrict__ a_ci,
+                                                      const double* __restrict__ a_v, const double* __restrict__ u,
+                                                      double rho, const double* __restrict__ p,
+                                                      double* __restrict__ q, double* __restrict__ part,
+                                                      PcgState* __restrict__ s, int pcg) {
+  if (pcg && s->done) return;
+  __shared__ double sh[kThreads / 32];
+  int64_t r0, r1;
+  cta_rows(m, r0, r1);
+  const int g = threadIdx.x / V, sub = threadIdx.x % V, ng = kThreads / V;
+  double loc = 0.0;
+  for (int64_t base = r0; base < r1; base += ng) {
+    const int64_t i = base + g;
+    const bool valid = i < r1;
+    const double acc = row_dot<V>(a_rp, a_ci, a_v, u, i, sub, valid);
+    if (valid && sub == 0) {
+      const double qi = __fma_rn(rho, p[i], acc);
+      q[i] = qi;
+      loc = __fma_rn(p[i], qi, loc);
+    }
+  }
+  if (!pcg) return;
   const double tot = block_sum(loc, sh);
   if (threadIdx.x == 0) part[blockIdx.x] = tot;
   if (last_block(&s->ticket[0])) {
@@ -211,15 +292,57 @@ __device__ __forceinline__ void block_solve(const TriSolve& M, const T* __restri
   }
 }
 
+// Shared epilogue of the update kernels: z, the block partials of
+// ||r||^2, r^T z and z^T q, and (last CTA) the scalars of the next launch.
+// part holds three sections of nblocks entries: [rr | rz | zq].
+__device__ __forceinline__ void update_epilogue(const TriSolve& M, double rrb, double rzb, double zqb,
+                                                double* __restrict__ part, PcgState* __restrict__ s, int mode,
+                                                bool timed_out) {
+  const int b = blockIdx.x;
+  const int nb = (int)M.nblocks;
+  if (threadIdx.x == 0) {
+    part[b] = rrb;
+    part[nb + b] = rzb;
+    part[2 * nb + b] = zqb;
+    if (timed_out) s->err = 1;
+  }
+  if (mode == 2) return;
+  if (last_block(&s->ticket[2])) {
+    if (threadIdx.x < 32) {
+      const double rrt = warp_fixed_sum(part, nb);
+      const double rzt = warp_fixed_sum(part + nb, nb);
+      const double zqt = warp_fixed_sum(part + 2 * nb, nb);
+      if (threadIdx.x == 0) {
+        s->rr = rrt;
+        s->rz_new = rzt;
+        s->zq = zqt;
+        if (mode == 0) {
+          if (rrt <= s->tol2) s->done = 1;
+          else if (s->iters >= s->maxit) s->done = 2;
+          else if (!isfinite(rzt) || !isfinite(rrt)) s->done = 3;
+          // standard beta = rho_new / rho; flexible (Polak-Ribiere) beta =
+          // z_new^T (r_new - r_old) / rho = -alpha z_new^T q / rho
+          s->beta = M.flexible ? -s->alpha * zqt / s->rho : rzt / s->rho;
+          s->rho = rzt;
+        } else {
+          s->rho = rzt;
+        }
+        s->ticket[2] = 0;
+      }
+    }
+  }
+}
+
+// Level-synchronous variant (any block size): y staged in shared memory if
+// the largest block fits, else in a global scratch vector.
 // mode 0: PCG update + preconditioner; mode 1: z = M^{-1} r only, then
 // rho = r^T z and p = z (start / restart of PCG); mode 2: z = M^{-1} r only.
 template <typename T, int V, bool kSmem>
 __global__ void __launch_bounds__(kThreads) k_pcg_update(TriSolve M, const double* __restrict__ p,
                                                          const double* __restrict__ q, double* __restrict__ x,
                                                          double* __restrict__ r, double* __restrict__ z,
-                                                         double* __restrict__ pp, double* __restrict__ part_rr,
-                                                         double* __restrict__ part_rz, PcgState* __restrict__ s,
-                                                         int mode) {
+                                                         double* __restrict__ pp, double* __restrict__ part,
+                                                         PcgState* __restrict__ s, int mode) {
   if (mode == 0 && s->done) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double sh[kThreads / 32];
@@ -253,39 +376,186 @@ __global__ void __launch_bounds__(kThreads) k_pcg_update(TriSolve M, const doubl
   const double rrb = block_sum(rr, sh);
   __syncthreads();
   block_solve<T, V>(M, F, dinv, b, s0, ybuf);
-  double rz = 0.0;
+  double rz = 0.0, zq = 0.0;
   for (int64_t i = s0 + threadIdx.x; i < e0; i += blockDim.x) {
     const double zi = (double)ybuf[i - s0];
     z[i] = zi;
     if (mode == 1) pp[i] = zi;
     rz = __fma_rn(r[i], zi, rz);
+    if (mode == 0) zq = __fma_rn(zi, q[i], zq);
   }
   const double rzb = block_sum(rz, sh);
-  if (threadIdx.x == 0) {
-    part_rr[b] = rrb;
-    part_rz[b] = rzb;
-  }
-  if (mode == 2) return;
-  if (last_block(&s->ticket[2])) {
-    if (threadIdx.x < 32) {
-      const double rrt = warp_fixed_sum(part_rr, gridDim.x);
-      const double rzt = warp_fixed_sum(part_rz, gridDim.x);
-      if (threadIdx.x == 0) {
-        s->rr = rrt;
-        s->rz_new = rzt;
-        if (mode == 0) {
-          if (rrt <= s->tol2) s->done = 1;
-          else if (s->iters >= s->maxit) s->done = 2;
-          else if (!isfinite(rzt) || !isfinite(rrt)) s->done = 3;
-          s->beta = rzt / s->rho;
-          s->rho = rzt;
-        } else {
-          s->rho = rzt;
-        }
-        s->ticket[2] = 0;
-      }
+  const double zqb = block_sum(zq, sh);
+  update_epilogue(M, rrb, rzb, zqb, part, s, mode, false);
+}
+
+// Sum over the V lanes of this thread's group only, so that the groups of a
+// warp stay independent while they wait on flags.
+template <int V, typename T>
+__device__ __forceinline__ T group_sum_own(T v) {
+  if (V == 32) return warp_sum(v);
+  const unsigned mask = ((1u << V) - 1u) << (lane_id() & ~(unsigned)(V - 1));
+#pragma unroll
+  for (int o = V / 2; o > 0; o >>= 1) v += __shfl_xor_sync(mask, v, o);
+  return v;
+}
+
+constexpr int kSpinLimit = 1 << 26;  // ~1 s of polling: a wait that long is a bug, reported as TIMEOUT
+constexpr int kPre = 4;              // entries per lane prefetched one position ahead
+
+template <typename TS, typename TC>
+struct RowPre {  // registers of one prefetched position
+  int i;
+  int64_t a, e;
+  TC d;
+  int j[kPre];
+  TC v[kPre];
+};
+
+template <typename TS, typename TC, int V>
+__device__ __forceinline__ void load_pos(RowPre<TS, TC>& R, const int64_t* __restrict__ off,
+                                         const int32_t* __restrict__ col, const TS* __restrict__ val,
+                                         const TS* __restrict__ pdinv, const int32_t* __restrict__ prow, int64_t q,
+                                         int sub) {
+  R.i = prow[q];
+  R.a = off[q];
+  R.e = off[q + 1];
+  R.d = (TC)pdinv[q];
+#pragma unroll
+  for (int k = 0; k < kPre; ++k) {
+    const int64_t t = R.a + sub + (int64_t)k * V;
+    if (t < R.e) {
+      R.j[k] = col[t];
+      R.v[k] = (TC)val[t];
+    } else {
+      R.j[k] = -1;
+      R.v[k] = TC(0);
     }
   }
+}
+
+// One flag-synchronised sweep over a block.  The block's rows are listed in
+// level order, each level padded to a whole number of warp tiles of RW = 32/V
+// rows (padding positions have row -1), so the rows of one tile belong to one
+// level and never depend on each other.  Warp w takes tiles w, w+W, ... in
+// increasing order.  A tile waits until every column its rows read is final
+// (flag == epoch, polled warp-uniformly with __all_sync: no divergent
+// spinning inside a warp), then each group of V lanes finishes its row and
+// publishes value and flag.  Every dependency of a tile lies in a lower level,
+// i.e. in an earlier tile, so the earliest unfinished tile can always
+// proceed and the sweep cannot deadlock; each wait is bounded anyway.
+template <typename TS, typename TC, int V>
+__device__ void sweep(const int64_t* __restrict__ off, const int32_t* __restrict__ col, const TS* __restrict__ val,
+                      const TS* __restrict__ pdinv, const int32_t* __restrict__ prow, int64_t q0, int64_t npos,
+                      volatile TC* y, volatile int* flag, int epoch, bool unit, int* timeout) {
+  constexpr int RW = 32 / V;
+  const int lane = lane_id(), w = threadIdx.x >> 5, W = blockDim.x >> 5;
+  const int slot = lane / V, sub = lane % V;
+  const int64_t ntiles = npos / RW;
+  if (w >= ntiles) return;
+  RowPre<TS, TC> nx;
+  load_pos<TS, TC, V>(nx, off, col, val, pdinv, prow, q0 + (int64_t)w * RW + slot, sub);
+  for (int64_t t = w; t < ntiles; t += W) {
+    const RowPre<TS, TC> cur = nx;
+    if (t + W < ntiles) load_pos<TS, TC, V>(nx, off, col, val, pdinv, prow, q0 + (t + W) * RW + slot, sub);
+    int spins = 0;
+    bool ready;
+    do {
+      ready = true;
+#pragma unroll
+      for (int k = 0; k < kPre; ++k)
+        if (cur.j[k] >= 0 && flag[cur.j[k]] < epoch) ready = false;
+      if (++spins > kSpinLimit) { *timeout = 1; ready = true; }
+    } while (!__all_sync(0xffffffffu, ready));
+    __threadfence_block();
+    TC acc = TC(0);
+#pragma unroll
+    for (int k = 0; k < kPre; ++k)
+      if (cur.j[k] >= 0) acc = fma(cur.v[k], (TC)y[cur.j[k]], acc);
+    // rows longer than kPre*V entries: warp-uniform chunks of V
+    const int64_t extra = cur.e - cur.a - (int64_t)kPre * V;
+    const int chunks = extra > 0 ? (int)((extra + V - 1) / V) : 0;
+    const int maxc = __reduce_max_sync(0xffffffffu, chunks);
+    for (int c = 0; c < maxc; ++c) {
+      const int64_t tt = cur.a + (int64_t)(kPre + c) * V + sub;
+      const bool valid = tt < cur.e;
+      const int j = valid ? col[tt] : -1;
+      const TC v = valid ? (TC)val[tt] : TC(0);
+      int sp = 0;
+      bool rd;
+      do {
+        rd = (j < 0) || flag[j] >= epoch;
+        if (++sp > kSpinLimit) { *timeout = 1; rd = true; }
+      } while (!__all_sync(0xffffffffu, rd));
+      __threadfence_block();
+      if (j >= 0) acc = fma(v, (TC)y[j], acc);
+    }
+    acc = group_sum<V>(acc);
+    if (sub == 0 && cur.i >= 0) {
+      TC yi = (TC)y[cur.i] - acc;
+      if (!unit) yi *= cur.d;
+      y[cur.i] = yi;
+      __threadfence_block();
+      flag[cur.i] = epoch;
+    }
+  }
+}
+
+// Flag-synchronised variant: y (compute precision TC) and the ready flags of
+// the block in shared memory; packed level-ordered factors (storage TS).
+template <typename TS, typename TC, int V>
+__global__ void __launch_bounds__(1024) k_pcg_update_sf(TriSolve M, const double* __restrict__ p,
+                                                        const double* __restrict__ q, double* __restrict__ x,
+                                                        double* __restrict__ r, double* __restrict__ z,
+                                                        double* __restrict__ pp, double* __restrict__ part,
+                                                        PcgState* __restrict__ s, int mode) {
+  if (mode == 0 && s->done) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double sh[32];
+  __shared__ int timeout;
+  const int b = blockIdx.x;
+  const int64_t s0 = M.bp[b], e0 = M.bp[b + 1];
+  volatile TC* y = reinterpret_cast<volatile TC*>(smem_raw);
+  volatile int* flag = reinterpret_cast<volatile int*>(smem_raw + (((size_t)M.max_block * sizeof(TC) + 15) & ~(size_t)15));
+  if (threadIdx.x == 0) timeout = 0;
+  double rr = 0.0;
+  if (mode == 0) {
+    const double a = s->alpha;
+    for (int64_t i = s0 + threadIdx.x; i < e0; i += blockDim.x) {
+      const double ri = __fma_rn(-a, q[i], r[i]);
+      x[i] = __fma_rn(a, p[i], x[i]);
+      r[i] = ri;
+      rr = __fma_rn(ri, ri, rr);
+      y[i - s0] = (TC)ri;
+      flag[i - s0] = 0;
+    }
+  } else {
+    for (int64_t i = s0 + threadIdx.x; i < e0; i += blockDim.x) {
+      const double ri = r[i];
+      rr = __fma_rn(ri, ri, rr);
+      y[i - s0] = (TC)ri;
+      flag[i - s0] = 0;
+    }
+  }
+  const double rrb = block_sum(rr, sh);
+  __syncthreads();
+  sweep<TS, TC, V>(M.fwd_off, M.fwd_col, static_cast<const TS*>(M.fwd_val), static_cast<const TS*>(M.fwd_dinv),
+                   M.fwd_row, M.fwd_pos[b], M.fwd_pos[b + 1] - M.fwd_pos[b], y, flag, 1, M.unit_lower != 0, &timeout);
+  __syncthreads();
+  sweep<TS, TC, V>(M.bwd_off, M.bwd_col, static_cast<const TS*>(M.bwd_val), static_cast<const TS*>(M.bwd_dinv),
+                   M.bwd_row, M.bwd_pos[b], M.bwd_pos[b + 1] - M.bwd_pos[b], y, flag, 2, false, &timeout);
+  __syncthreads();
+  double rz = 0.0, zq = 0.0;
+  for (int64_t i = s0 + threadIdx.x; i < e0; i += blockDim.x) {
+    const double zi = (double)y[i - s0];
+    z[i] = zi;
+    if (mode == 1) pp[i] = zi;
+    rz = __fma_rn(r[i], zi, rz);
+    if (mode == 0) zq = __fma_rn(zi, q[i], zq);
+  }
+  const double rzb = block_sum(rz, sh);
+  const double zqb = block_sum(zq, sh);
+  update_epilogue(M, rrb, rzb, zqb, part, s, mode, timeout != 0);
 }
 
 __global__ void k_pcg_direction(int64_t n, const double* __restrict__ z, double* __restrict__ p,
@@ -323,24 +593,39 @@ inline unsigned grid_for(int64_t work, int per_block, int cap = 152 * 16) {
 
 template <typename T, int V>
 cudaError_t launch_update(const TriSolve& M, const double* p, const double* q, double* x, double* r, double* z,
-                          double* pp, double* part_rr, double* part_rz, PcgState* s, int mode, cudaStream_t st) {
+                          double* pp, double* part, PcgState* s, int mode, cudaStream_t st) {
   const size_t need = (size_t)M.max_block * sizeof(T);
   if (need <= (size_t)200 * 1024) {
     auto kern = k_pcg_update<T, V, true>;
     SDSL_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need));
-    kern<<<(unsigned)M.nblocks, kThreads, need, st>>>(M, p, q, x, r, z, pp, part_rr, part_rz, s, mode);
+    kern<<<(unsigned)M.nblocks, kThreads, need, st>>>(M, p, q, x, r, z, pp, part, s, mode); count_launch();
   } else {
-    k_pcg_update<T, V, false><<<(unsigned)M.nblocks, kThreads, 0, st>>>(M, p, q, x, r, z, pp, part_rr, part_rz, s,
-                                                                        mode);
+    k_pcg_update<T, V, false><<<(unsigned)M.nblocks, kThreads, 0, st>>>(M, p, q, x, r, z, pp, part, s, mode); count_launch();
   }
   return cudaGetLastError();
 }
 
+template <typename TS, typename TC, int V>
+cudaError_t launch_update_sf(const TriSolve& M, const double* p, const double* q, double* x, double* r, double* z,
+                             double* pp, double* part, PcgState* s, int mode, cudaStream_t st) {
+  const size_t need = sf_smem_bytes(M.max_block, sizeof(TC));
+  auto kern = k_pcg_update_sf<TS, TC, V>;
+  SDSL_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need));
+  kern<<<(unsigned)M.nblocks, M.threads, need, st>>>(M, p, q, x, r, z, pp, part, s, mode); count_launch();
+  return cudaGetLastError();
+}
+
 cudaError_t update_any(const TriSolve& M, const double* p, const double* q, double* x, double* r, double* z,
-                       double* pp, double* part_rr, double* part_rz, PcgState* s, int mode, cudaStream_t st) {
+                       double* pp, double* part, PcgState* s, int mode, cudaStream_t st) {
   return by_lanes(M.lanes, [&](auto V) -> cudaError_t {
-    if (M.prec == 32) return launch_update<float, decltype(V)::value>(M, p, q, x, r, z, pp, part_rr, part_rz, s, mode, st);
-    return launch_update<double, decltype(V)::value>(M, p, q, x, r, z, pp, part_rr, part_rz, s, mode, st);
+    constexpr int kV = decltype(V)::value;
+    if (M.sync_free) {
+      if (M.prec == 64) return launch_update_sf<double, double, kV>(M, p, q, x, r, z, pp, part, s, mode, st);
+      if (M.apply_prec == 64) return launch_update_sf<float, double, kV>(M, p, q, x, r, z, pp, part, s, mode, st);
+      return launch_update_sf<float, float, kV>(M, p, q, x, r, z, pp, part, s, mode, st);
+    }
+    if (M.prec == 32) return launch_update<float, kV>(M, p, q, x, r, z, pp, part, s, mode, st);
+    return launch_update<double, kV>(M, p, q, x, r, z, pp, part, s, mode, st);
   });
 }
 
@@ -348,49 +633,86 @@ cudaError_t update_any(const TriSolve& M, const double* p, const double* q, doub
 
 cudaError_t spmv(const SpmvPlan& A, const double* x, double* y, cudaStream_t st) {
   return by_lanes(A.lanes, [&](auto V) -> cudaError_t {
-    k_spmv<decltype(V)::value><<<A.grid, kThreads, 0, st>>>(A.n, A.rp, A.ci, A.v, x, y);
+    k_spmv<decltype(V)::value><<<A.grid, kThreads, 0, st>>>(A.n, A.rp, A.ci, A.v, x, y); count_launch();
+    return cudaGetLastError();
+  });
+}
+
+// Mean device time of `reps` launches of the SpMV with the plan's lane width
+// (the autotuner's probe; x and y are scratch vectors of length n).
+cudaError_t time_spmv(const SpmvPlan& A, const double* x, double* y, int reps, float* ms, cudaStream_t st) {
+  cudaEvent_t a, b;
+  SDSL_CUDA_TRY(cudaEventCreate(&a));
+  SDSL_CUDA_TRY(cudaEventCreate(&b));
+  SDSL_CUDA_TRY(spmv(A, x, y, st));  // warm
+  SDSL_CUDA_TRY(cudaEventRecord(a, st));
+  for (int i = 0; i < reps; ++i) SDSL_CUDA_TRY(spmv(A, x, y, st));
+  SDSL_CUDA_TRY(cudaEventRecord(b, st));
+  SDSL_CUDA_TRY(cudaEventSynchronize(b));
+  SDSL_CUDA_TRY(cudaEventElapsedTime(ms, a, b));
+  *ms /= (float)reps;
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  return cudaSuccess;
+}
+
+cudaError_t factored_product(const SpmvPlan& A, const double* p, double* q, double* part, PcgState* s, int pcg,
+                             cudaStream_t st) {
+  SDSL_CUDA_TRY(by_lanes(A.at_lanes, [&](auto V) -> cudaError_t {
+    k_at_theta<decltype(V)::value><<<A.at_grid, kThreads, 0, st>>>(A.ncols, A.at_rp, A.at_ci, A.at_v, A.theta, p, A.u,
+                                                                   pcg ? s : nullptr); count_launch();
+    return cudaGetLastError();
+  }));
+  return by_lanes(A.a_lanes, [&](auto V) -> cudaError_t {
+    k_a_u_dot<decltype(V)::value><<<A.grid, kThreads, 0, st>>>(A.n, A.a_rp, A.a_ci, A.a_v, A.u, A.rho, p, q, part, s,
+                                                               pcg); count_launch();
     return cudaGetLastError();
   });
 }
 
 cudaError_t pcg_spmv(const SpmvPlan& A, const double* p, double* q, double* part, PcgState* s, cudaStream_t st) {
+  if (A.factored) return factored_product(A, p, q, part, s, 1, st);
   return by_lanes(A.lanes, [&](auto V) -> cudaError_t {
-    k_pcg_spmv<decltype(V)::value><<<A.grid, kThreads, 0, st>>>(A.n, A.rp, A.ci, A.v, p, q, part, s);
+    k_pcg_spmv<decltype(V)::value><<<A.grid, kThreads, 0, st>>>(A.n, A.rp, A.ci, A.v, p, q, part, s); count_launch();
     return cudaGetLastError();
   });
 }
 
 cudaError_t pcg_update_precond(const TriSolve& M, const double* p, const double* q, double* x, double* r, double* z,
-                               double* part_rr, double* part_rz, PcgState* s, cudaStream_t st) {
-  return update_any(M, p, q, x, r, z, nullptr, part_rr, part_rz, s, 0, st);
+                               double* part, PcgState* s, cudaStream_t st) {
+  return update_any(M, p, q, x, r, z, nullptr, part, s, 0, st);
 }
 
-cudaError_t precond_apply(const TriSolve& M, const double* r, double* z, double* p_out, double* part_rr,
-                          double* part_rz, PcgState* s, int mode, cudaStream_t st) {
-  return update_any(M, nullptr, nullptr, nullptr, const_cast<double*>(r), z, p_out, part_rr, part_rz, s, mode, st);
+size_t sf_smem_bytes(int64_t max_block, size_t tc_size) {
+  return (((size_t)max_block * tc_size + 15) & ~(size_t)15) + (size_t)max_block * sizeof(int);
+}
+
+cudaError_t precond_apply(const TriSolve& M, const double* r, double* z, double* p_out, double* part, PcgState* s,
+                          int mode, cudaStream_t st) {
+  return update_any(M, nullptr, nullptr, nullptr, const_cast<double*>(r), z, p_out, part, s, mode, st);
 }
 
 cudaError_t pcg_direction(int64_t n, const double* z, double* p, PcgState* s, cudaStream_t st) {
-  k_pcg_direction<<<grid_for(n, kThreads), kThreads, 0, st>>>(n, z, p, s);
+  k_pcg_direction<<<grid_for(n, kThreads), kThreads, 0, st>>>(n, z, p, s); count_launch();
   return cudaGetLastError();
 }
 
 cudaError_t true_residual(const SpmvPlan& A, const double* b, const double* x, double* r, double* part,
                           PcgState* s, int write_r, cudaStream_t st) {
   return by_lanes(A.lanes, [&](auto V) -> cudaError_t {
-    k_residual<decltype(V)::value><<<A.grid, kThreads, 0, st>>>(A.n, A.rp, A.ci, A.v, b, x, r, part, s, write_r);
+    k_residual<decltype(V)::value><<<A.grid, kThreads, 0, st>>>(A.n, A.rp, A.ci, A.v, b, x, r, part, s, write_r); count_launch();
     return cudaGetLastError();
   });
 }
 
 cudaError_t norm2_sq(int64_t n, const double* a, double* part, double* out, unsigned int* ticket, cudaStream_t st) {
   const unsigned g = grid_for(n, kThreads, 152 * 4);
-  k_norm2<<<g, kThreads, 0, st>>>(n, a, part, out, ticket);
+  k_norm2<<<g, kThreads, 0, st>>>(n, a, part, out, ticket); count_launch();
   return cudaGetLastError();
 }
 
 cudaError_t pcg_init_state(PcgState* s, double tol2, long long maxit, cudaStream_t st) {
-  k_init_state<<<1, 1, 0, st>>>(s, tol2, maxit);
+  k_init_state<<<1, 1, 0, st>>>(s, tol2, maxit); count_launch();
   return cudaGetLastError();
 }
 

@@ -247,18 +247,26 @@ __global__ void k_level_lists(const int64_t* __restrict__ bp, const int32_t* __r
 // IC(0), row oriented: for each k < i of row i (ascending),
 //   l_ik = (p_ik - sum_{j<k} l_ij l_kj) / l_kk,  l_ii = sqrt(p~_ii - sum l_ij^2),
 // p~_ii = p_ii + alpha p_ii (shift of the retry rule).  Rows of one level are
-// independent; a warp takes one row, lanes split the inner products.
-__global__ void k_ic0(const int64_t* __restrict__ bp, const int64_t* __restrict__ prp,
+// independent; a warp takes one row and keeps its columns and values in
+// shared memory while lanes split the inner products over row k.
+// Grid: nblocks x nshift CTAs; CTA (b, t) factors block b with shift
+// alpha[t] into F + t * nnz (all shifts of the retry ladder run at once).
+constexpr int kIcWarps = 32;
+constexpr int kIcCap = 192;  // row entries staged in shared memory per warp
+__global__ void __launch_bounds__(kIcWarps * 32) k_ic0(const int64_t* __restrict__ bp, const int64_t* __restrict__ prp,
                       const int32_t* __restrict__ pci, const double* __restrict__ pv,
                       const int64_t* __restrict__ pdiag, const int32_t* __restrict__ lev_off,
                       const int32_t* __restrict__ level_ptr, const int32_t* __restrict__ level_rows,
-                      const double* __restrict__ alpha, const int32_t* __restrict__ active, double* __restrict__ F,
-                      double* __restrict__ dinv, int32_t* __restrict__ status) {
-  const int b = blockIdx.x;
-  if (!active[b]) return;
+                      const double* __restrict__ alpha, int nshift, int64_t nnz, int64_t n,
+                      double* __restrict__ Fall, double* __restrict__ dinv_all, int32_t* __restrict__ status) {
+  const int b = blockIdx.x / nshift, sh = blockIdx.x % nshift;
+  double* __restrict__ F = Fall + (int64_t)sh * nnz;
+  double* __restrict__ dinv = dinv_all + (int64_t)sh * n;
   const int64_t s = bp[b];
-  const double al = alpha[b];
+  const double al = alpha[sh];
   __shared__ int failed;
+  __shared__ int32_t scol[kIcWarps][kIcCap];
+  __shared__ double sval[kIcWarps][kIcCap];
   if (threadIdx.x == 0) failed = 0;
   __syncthreads();
   const int lane = lane_id(), w = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -269,21 +277,36 @@ __global__ void k_ic0(const int64_t* __restrict__ bp, const int64_t* __restrict_
       const int64_t lo = prp[i], dg = pdiag[i];
       int64_t t0 = lo;
       while (t0 < dg && pci[t0] < s) ++t0;  // first in-block entry
-      for (int64_t t = t0; t < dg; ++t) {
-        const int64_t k = pci[t];
+      const int64_t len = dg - t0;
+      const bool staged = len <= kIcCap;
+      int32_t* cols = scol[w];
+      double* vals = sval[w];
+      if (staged)
+        for (int64_t q = lane; q < len; q += 32) cols[q] = pci[t0 + q];
+      __syncwarp();
+      for (int64_t t = 0; t < len; ++t) {
+        const int64_t k = pci[t0 + t];
         double acc = 0.0;
-        for (int64_t q = prp[k] + lane; q < pdiag[k]; q += 32) {
+        const int64_t kd = pdiag[k];
+        for (int64_t q = prp[k] + lane; q < kd; q += 32) {
           const int32_t j = pci[q];
           if (j < s) continue;
-          const int64_t pos = bsearch_i32(pci, t0, t, j);
-          if (pos >= 0) acc = __fma_rn(F[pos], F[q], acc);
+          const int64_t pos = staged ? bsearch_i32(cols, 0, t, j) : bsearch_i32(pci + t0, 0, t, j);
+          if (pos >= 0) acc = __fma_rn(staged ? vals[pos] : F[t0 + pos], F[q], acc);
         }
         acc = warp_sum(acc);
-        if (lane == 0) F[t] = (pv[t] - acc) / F[pdiag[k]];
+        if (lane == 0) {
+          const double l = (pv[t0 + t] - acc) / F[kd];
+          if (staged) vals[t] = l; else F[t0 + t] = l;
+        }
         __syncwarp();
       }
       double sq = 0.0;
-      for (int64_t t = t0 + lane; t < dg; t += 32) sq = __fma_rn(F[t], F[t], sq);
+      for (int64_t q = lane; q < len; q += 32) {
+        const double l = staged ? vals[q] : F[t0 + q];
+        sq = __fma_rn(l, l, sq);
+        if (staged) F[t0 + q] = l;
+      }
       sq = warp_sum(sq);
       if (lane == 0) {
         const double pd = al == 0.0 ? pv[dg] : __dadd_rn(pv[dg], __dmul_rn(al, pv[dg]));
@@ -303,7 +326,20 @@ __global__ void k_ic0(const int64_t* __restrict__ bp, const int64_t* __restrict_
     __syncthreads();
     if (failed) break;
   }
-  if (threadIdx.x == 0) status[b] = failed;
+  if (threadIdx.x == 0) status[b * nshift + sh] = failed;
+}
+
+// Copy the factor of the chosen shift of every block into F / dinv.
+__global__ void k_pick_shift(const int64_t* __restrict__ bp, const int64_t* __restrict__ prp,
+                             const int32_t* __restrict__ choice, int64_t nnz, int64_t n,
+                             const double* __restrict__ Fall, const double* __restrict__ dinv_all,
+                             double* __restrict__ F, double* __restrict__ dinv, const int32_t* __restrict__ rb,
+                             int64_t nrows) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nrows; i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t c = choice[rb[i]];
+    for (int64_t t = prp[i]; t < prp[i + 1]; ++t) F[t] = Fall[(int64_t)c * nnz + t];
+    dinv[i] = dinv_all[(int64_t)c * n + i];
+  }
 }
 
 // ILU(0), IKJ order restricted to the in-block pattern: for each k < i of row
@@ -360,6 +396,58 @@ __global__ void k_ilu0(const int64_t* __restrict__ bp, const int64_t* __restrict
   if (threadIdx.x == 0) status[b] = failed;
 }
 
+// One thread per position q of the level lists: row i = lev_rows[q] of block
+// b = row_block[i]; its in-block strict entries in the solve direction.
+__global__ void k_pack_count(int dir, int64_t npos, const int32_t* __restrict__ rb, const int64_t* __restrict__ bp,
+                             const int64_t* __restrict__ prp, const int32_t* __restrict__ pci,
+                             const int64_t* __restrict__ pdiag, const int32_t* __restrict__ lev_rows,
+                             int64_t* __restrict__ off) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < npos; q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = lev_rows[q];
+    if (i < 0) { off[q] = 0; continue; }  // padding position
+    const int32_t b = rb[i];
+    const int64_t s = bp[b], e = bp[b + 1];
+    int64_t c = 0;
+    if (dir == 0) {
+      for (int64_t t = prp[i]; t < pdiag[i]; ++t) c += pci[t] >= s;
+    } else {
+      for (int64_t t = pdiag[i] + 1; t < prp[i + 1]; ++t) c += pci[t] < e;
+    }
+    off[q] = c;
+  }
+}
+
+template <typename TS>
+__global__ void k_pack_fill(int dir, int64_t npos, const int32_t* __restrict__ rb, const int64_t* __restrict__ bp,
+                            const int64_t* __restrict__ prp, const int32_t* __restrict__ pci,
+                            const int64_t* __restrict__ pdiag, const int32_t* __restrict__ lev_rows,
+                            const double* __restrict__ F, const double* __restrict__ dinv,
+                            const int64_t* __restrict__ off, int32_t* __restrict__ col, TS* __restrict__ val,
+                            TS* __restrict__ pdinv, int32_t* __restrict__ prow) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < npos; q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = lev_rows[q];
+    if (i < 0) {  // padding position: no entries, no row
+      pdinv[q] = (TS)1;
+      prow[q] = -1;
+      continue;
+    }
+    const int32_t b = rb[i];
+    const int64_t s = bp[b], e = bp[b + 1];
+    int64_t at = off[q];
+    const int64_t t0 = dir == 0 ? prp[i] : pdiag[i] + 1;
+    const int64_t t1 = dir == 0 ? pdiag[i] : prp[i + 1];
+    for (int64_t t = t0; t < t1; ++t) {
+      const int32_t j = pci[t];
+      if (j < s || j >= e) continue;
+      col[at] = (int32_t)(j - s);
+      val[at] = (TS)F[t];
+      ++at;
+    }
+    pdinv[q] = (TS)dinv[i];
+    prow[q] = (int32_t)(i - s);
+  }
+}
+
 __global__ void k_ic0_finish(int64_t n, const int64_t* __restrict__ prp, const int64_t* __restrict__ pdiag,
                              const int64_t* __restrict__ mir, double* __restrict__ F) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -374,12 +462,12 @@ __global__ void k_to_float(int64_t n, const double* __restrict__ a, float* __res
 }  // namespace
 
 cudaError_t diag_values(int64_t n, const int64_t* rp, const int32_t* ci, const double* v, double* d, cudaStream_t st) {
-  k_diag_values<<<grid_for(n, 256), 256, 0, st>>>(n, rp, ci, v, d);
+  k_diag_values<<<grid_for(n, 256), 256, 0, st>>>(n, rp, ci, v, d); count_launch();
   return cudaGetLastError();
 }
 
 cudaError_t row_blocks(int64_t n, int64_t nblocks, const int64_t* bp, int32_t* row_block, cudaStream_t st) {
-  k_row_blocks<<<grid_for(n, 256), 256, 0, st>>>(n, nblocks, bp, row_block);
+  k_row_blocks<<<grid_for(n, 256), 256, 0, st>>>(n, nblocks, bp, row_block); count_launch();
   return cudaGetLastError();
 }
 
@@ -388,7 +476,7 @@ cudaError_t filter_count(int64_t n, const int64_t* rp, const int32_t* ci, const 
                          cudaStream_t st) {
   (void)bp;
   k_filter<false><<<grid_for(n, 8), 256, 0, st>>>(n, rp, ci, v, d, row_block, whole, tau, 0.0, prp, nullptr, nullptr,
-                                                  nullptr);
+                                                  nullptr); count_launch();
   return cudaGetLastError();
 }
 
@@ -397,13 +485,13 @@ cudaError_t filter_fill(int64_t n, const int64_t* rp, const int32_t* ci, const d
                         const int64_t* prp, int32_t* pci, double* pv, int64_t* pdiag, cudaStream_t st) {
   (void)bp;
   k_filter<true><<<grid_for(n, 8), 256, 0, st>>>(n, rp, ci, v, d, row_block, whole, tau, delta,
-                                                 const_cast<int64_t*>(prp), pci, pv, pdiag);
+                                                 const_cast<int64_t*>(prp), pci, pv, pdiag); count_launch();
   return cudaGetLastError();
 }
 
 cudaError_t mirror_map(int64_t n, const int64_t* prp, const int32_t* pci, const int64_t* pdiag, int64_t* mir,
                        int* bad, cudaStream_t st) {
-  k_mirror_map<<<grid_for(n, 256), 256, 0, st>>>(n, prp, pci, pdiag, mir, bad);
+  k_mirror_map<<<grid_for(n, 256), 256, 0, st>>>(n, prp, pci, pdiag, mir, bad); count_launch();
   return cudaGetLastError();
 }
 
@@ -411,24 +499,32 @@ cudaError_t levels(int dir, int64_t nblocks, const int64_t* bp, const int64_t* p
                    const int64_t* pdiag, int32_t* cnt, int32_t* lev, int32_t* fa, int32_t* fb, int32_t* nlev,
                    cudaStream_t st) {
   if (nblocks == 0) return cudaSuccess;
-  k_levels<<<(unsigned)nblocks, 512, 0, st>>>(dir, bp, prp, pci, pdiag, cnt, lev, fa, fb, nlev);
+  k_levels<<<(unsigned)nblocks, 512, 0, st>>>(dir, bp, prp, pci, pdiag, cnt, lev, fa, fb, nlev); count_launch();
   return cudaGetLastError();
 }
 
 cudaError_t level_lists(int64_t nblocks, const int64_t* bp, const int32_t* lev, const int32_t* lev_off,
                         int32_t* hist, int32_t* level_ptr, int32_t* level_rows, cudaStream_t st) {
   if (nblocks == 0) return cudaSuccess;
-  k_level_lists<<<(unsigned)nblocks, 256, 0, st>>>(bp, lev, lev_off, hist, level_ptr, level_rows);
+  k_level_lists<<<(unsigned)nblocks, 256, 0, st>>>(bp, lev, lev_off, hist, level_ptr, level_rows); count_launch();
   return cudaGetLastError();
 }
 
-cudaError_t ic0_factor(int64_t nblocks, const int64_t* bp, const int64_t* prp, const int32_t* pci, const double* pv,
-                       const int64_t* pdiag, const int32_t* lev_off, const int32_t* level_ptr,
-                       const int32_t* level_rows, const double* alpha, const int32_t* active, double* F,
-                       double* dinv, int32_t* status, cudaStream_t st) {
+cudaError_t ic0_factor_all(int64_t nblocks, const int64_t* bp, const int64_t* prp, const int32_t* pci,
+                           const double* pv, const int64_t* pdiag, const int32_t* lev_off, const int32_t* level_ptr,
+                           const int32_t* level_rows, const double* alpha, int nshift, int64_t nnz, int64_t n,
+                           double* Fall, double* dinv_all, int32_t* status, cudaStream_t st) {
   if (nblocks == 0) return cudaSuccess;
-  k_ic0<<<(unsigned)nblocks, 1024, 0, st>>>(bp, prp, pci, pv, pdiag, lev_off, level_ptr, level_rows, alpha, active, F,
-                                            dinv, status);
+  k_ic0<<<(unsigned)(nblocks * nshift), kIcWarps * 32, 0, st>>>(bp, prp, pci, pv, pdiag, lev_off, level_ptr,
+                                                               level_rows, alpha, nshift, nnz, n, Fall, dinv_all,
+                                                               status); count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t pick_shift(const int64_t* bp, const int64_t* prp, const int32_t* choice, int64_t nnz, int64_t n,
+                       const double* Fall, const double* dinv_all, double* F, double* dinv, const int32_t* rb,
+                       int64_t nrows, cudaStream_t st) {
+  k_pick_shift<<<grid_for(nrows, 256), 256, 0, st>>>(bp, prp, choice, nnz, n, Fall, dinv_all, F, dinv, rb, nrows); count_launch();
   return cudaGetLastError();
 }
 
@@ -438,25 +534,48 @@ cudaError_t ilu0_factor(int64_t nblocks, const int64_t* bp, const int64_t* prp, 
                         double* dinv, int32_t* status, cudaStream_t st) {
   if (nblocks == 0) return cudaSuccess;
   k_ilu0<<<(unsigned)nblocks, 1024, 0, st>>>(bp, prp, pci, pv, pdiag, lev_off, level_ptr, level_rows, alpha, active,
-                                             F, dinv, status);
+                                             F, dinv, status); count_launch();
   return cudaGetLastError();
 }
 
 cudaError_t ic0_finish(int64_t n, int64_t nnz, const int64_t* prp, const int64_t* pdiag, const int64_t* mir,
                        double* F, const double* dinv, float* Ff, float* dinvf, cudaStream_t st) {
-  k_ic0_finish<<<grid_for(n, 256), 256, 0, st>>>(n, prp, pdiag, mir, F);
+  k_ic0_finish<<<grid_for(n, 256), 256, 0, st>>>(n, prp, pdiag, mir, F); count_launch();
   SDSL_CUDA_TRY(cudaGetLastError());
   if (Ff) {
-    k_to_float<<<grid_for(nnz, 256), 256, 0, st>>>(nnz, F, Ff);
+    k_to_float<<<grid_for(nnz, 256), 256, 0, st>>>(nnz, F, Ff); count_launch();
     SDSL_CUDA_TRY(cudaGetLastError());
-    k_to_float<<<grid_for(n, 256), 256, 0, st>>>(n, dinv, dinvf);
+    k_to_float<<<grid_for(n, 256), 256, 0, st>>>(n, dinv, dinvf); count_launch();
     SDSL_CUDA_TRY(cudaGetLastError());
   }
   return cudaSuccess;
 }
 
+cudaError_t pack_count(int dir, int64_t npos, const int32_t* row_block, const int64_t* bp, const int64_t* prp,
+                       const int32_t* pci, const int64_t* pdiag, const int32_t* lev_rows, int64_t* off,
+                       cudaStream_t st) {
+  k_pack_count<<<grid_for(npos, 256), 256, 0, st>>>(dir, npos, row_block, bp, prp, pci, pdiag, lev_rows, off); count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t pack_fill(int dir, int64_t npos, const int32_t* row_block, const int64_t* bp, const int64_t* prp,
+                      const int32_t* pci, const int64_t* pdiag, const int32_t* lev_rows, const double* F,
+                      const double* dinv, int prec, const int64_t* off, int32_t* col, void* val, void* pdinv,
+                      int32_t* prow, cudaStream_t st) {
+  if (prec == 32) {
+    k_pack_fill<float><<<grid_for(npos, 256), 256, 0, st>>>(dir, npos, row_block, bp, prp, pci, pdiag, lev_rows, F,
+                                                            dinv, off, col, static_cast<float*>(val),
+                                                            static_cast<float*>(pdinv), prow); count_launch();
+  } else {
+    k_pack_fill<double><<<grid_for(npos, 256), 256, 0, st>>>(dir, npos, row_block, bp, prp, pci, pdiag, lev_rows,
+                                                             F, dinv, off, col, static_cast<double*>(val),
+                                                             static_cast<double*>(pdinv), prow); count_launch();
+  }
+  return cudaGetLastError();
+}
+
 cudaError_t to_float(int64_t n, const double* a, float* b, cudaStream_t st) {
-  k_to_float<<<grid_for(n, 256), 256, 0, st>>>(n, a, b);
+  k_to_float<<<grid_for(n, 256), 256, 0, st>>>(n, a, b); count_launch();
   return cudaGetLastError();
 }
 

@@ -105,20 +105,20 @@ int64_t scan_scratch_elems(int64_t n) { return (n + kChunk - 1) / kChunk + 1; }
 cudaError_t exclusive_scan_i64(int64_t* data, int64_t n, int64_t* scratch, cudaStream_t st) {
   const int64_t nchunks = (n + kChunk - 1) / kChunk;
   if (nchunks > 0) {
-    k_chunk_sums<<<(unsigned)nchunks, kScanThreads, 0, st>>>(data, n, scratch);
+    k_chunk_sums<<<(unsigned)nchunks, kScanThreads, 0, st>>>(data, n, scratch); count_launch();
     SDSL_CUDA_TRY(cudaGetLastError());
   }
-  k_scan_sums<<<1, 1024, 0, st>>>(scratch, nchunks, data, n);
+  k_scan_sums<<<1, 1024, 0, st>>>(scratch, nchunks, data, n); count_launch();
   SDSL_CUDA_TRY(cudaGetLastError());
   if (nchunks > 0) {
-    k_chunk_scan<<<(unsigned)nchunks, kScanThreads, 0, st>>>(data, n, scratch);
+    k_chunk_scan<<<(unsigned)nchunks, kScanThreads, 0, st>>>(data, n, scratch); count_launch();
     SDSL_CUDA_TRY(cudaGetLastError());
   }
   return cudaSuccess;
 }
 
 cudaError_t exclusive_scan_i32(const int32_t* in, int32_t* out, int64_t n, cudaStream_t st) {
-  k_scan_i32<<<1, 1024, 0, st>>>(in, out, n);
+  k_scan_i32<<<1, 1024, 0, st>>>(in, out, n); count_launch();
   return cudaGetLastError();
 }
 

@@ -330,14 +330,14 @@ inline unsigned grid_for(int64_t work, int per_block, int cap = 152 * 32) {
 
 cudaError_t check_csr(int64_t nrows, int64_t ncols, const int64_t* rp, const int32_t* ci, int* bad,
                       cudaStream_t st) {
-  k_check_csr<<<grid_for(nrows, 256), 256, 0, st>>>(nrows, ncols, rp, ci, bad);
+  k_check_csr<<<grid_for(nrows, 256), 256, 0, st>>>(nrows, ncols, rp, ci, bad); count_launch();
   return cudaGetLastError();
 }
 
 cudaError_t transpose_csr(int64_t m, int64_t n, const int64_t* rp, const int32_t* ci, const double* v, int64_t* trp,
                           int32_t* tci, double* tv, int64_t* scan_scratch, cudaStream_t st) {
   SDSL_CUDA_TRY(cudaMemsetAsync(trp, 0, sizeof(int64_t) * (size_t)(n + 1), st));
-  k_transpose_count<<<grid_for(m, 256), 256, 0, st>>>(m, rp, ci, reinterpret_cast<unsigned long long*>(trp));
+  k_transpose_count<<<grid_for(m, 256), 256, 0, st>>>(m, rp, ci, reinterpret_cast<unsigned long long*>(trp)); count_launch();
   SDSL_CUDA_TRY(cudaGetLastError());
   SDSL_CUDA_TRY(exclusive_scan_i64(trp, n, scan_scratch, st));
   // cursor: reuse the scan scratch? it is small; use tci's neighbour buffer from the caller instead
@@ -348,14 +348,14 @@ cudaError_t transpose_fill(int64_t m, int64_t n, const int64_t* rp, const int32_
                            const int64_t* trp, int32_t* tci, double* tv, int64_t* cursor, cudaStream_t st) {
   SDSL_CUDA_TRY(cudaMemcpyAsync(cursor, trp, sizeof(int64_t) * (size_t)n, cudaMemcpyDeviceToDevice, st));
   k_transpose_fill<<<grid_for(m, 256), 256, 0, st>>>(m, rp, ci, v, reinterpret_cast<unsigned long long*>(cursor),
-                                                     tci, tv);
+                                                     tci, tv); count_launch();
   SDSL_CUDA_TRY(cudaGetLastError());
-  k_sort_segments<<<grid_for(n, 256), 256, 0, st>>>(n, trp, tci, tv);
+  k_sort_segments<<<grid_for(n, 256), 256, 0, st>>>(n, trp, tci, tv); count_launch();
   return cudaGetLastError();
 }
 
 cudaError_t sort_rows(int64_t nrows, const int64_t* rp, int32_t* ci, double* v, cudaStream_t st) {
-  k_sort_segments<<<grid_for(nrows, 256), 256, 0, st>>>(nrows, rp, ci, v);
+  k_sort_segments<<<grid_for(nrows, 256), 256, 0, st>>>(nrows, rp, ci, v); count_launch();
   return cudaGetLastError();
 }
 
@@ -364,7 +364,7 @@ cudaError_t normal_symbolic_count(int64_t m, const int64_t* rp, const int32_t* c
                                   cudaStream_t st) {
   SDSL_CUDA_TRY(cudaMemsetAsync(nlong, 0, sizeof(int32_t), st));
   k_sym_warp<false><<<grid_for(m, kSetupWarps), kSetupWarps * 32, 0, st>>>(m, rp, ci, trp, tci, srp, nullptr,
-                                                                           long_rows, nlong);
+                                                                           long_rows, nlong); count_launch();
   return cudaGetLastError();
 }
 
@@ -375,10 +375,10 @@ cudaError_t normal_symbolic_long(bool fill, int nlong, const int32_t* long_rows,
   const size_t smem = sizeof(int32_t) * kLongCap;
   if (fill) {
     SDSL_CUDA_TRY(cudaFuncSetAttribute(k_sym_long<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_sym_long<true><<<nlong, 1024, smem, st>>>(long_rows, rp, ci, trp, tci, srp, sci, err);
+    k_sym_long<true><<<nlong, 1024, smem, st>>>(long_rows, rp, ci, trp, tci, srp, sci, err); count_launch();
   } else {
     SDSL_CUDA_TRY(cudaFuncSetAttribute(k_sym_long<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_sym_long<false><<<nlong, 1024, smem, st>>>(long_rows, rp, ci, trp, tci, srp, sci, err);
+    k_sym_long<false><<<nlong, 1024, smem, st>>>(long_rows, rp, ci, trp, tci, srp, sci, err); count_launch();
   }
   return cudaGetLastError();
 }
@@ -387,7 +387,7 @@ cudaError_t normal_symbolic_fill(int64_t m, const int64_t* rp, const int32_t* ci
                                  const int32_t* tci, const int64_t* srp, int32_t* sci, cudaStream_t st) {
   k_sym_warp<true><<<grid_for(m, kSetupWarps), kSetupWarps * 32, 0, st>>>(m, rp, ci, trp, tci,
                                                                           const_cast<int64_t*>(srp), sci, nullptr,
-                                                                          nullptr);
+                                                                          nullptr); count_launch();
   return cudaGetLastError();
 }
 
@@ -395,19 +395,19 @@ cudaError_t normal_values(int64_t m, const int64_t* rp, const int32_t* ci, const
                           const int32_t* tci, const double* tv, const double* theta, double rho,
                           const int64_t* srp, const int32_t* sci, double* sv, cudaStream_t st) {
   k_normal_values<<<grid_for(m, kSetupWarps), kSetupWarps * 32, 0, st>>>(m, rp, ci, v, trp, tci, tv, theta, rho, srp,
-                                                                         sci, sv);
+                                                                         sci, sv); count_launch();
   return cudaGetLastError();
 }
 
 cudaError_t bbd_positions(int64_t m, int64_t n, int64_t nblocks, const int64_t* rbp, const int64_t* cbp,
                           const int64_t* kbp, int64_t* pos, cudaStream_t st) {
-  k_bbd_positions<<<grid_for(n + m, 256), 256, 0, st>>>(m, n, nblocks, rbp, cbp, kbp, pos);
+  k_bbd_positions<<<grid_for(n + m, 256), 256, 0, st>>>(m, n, nblocks, rbp, cbp, kbp, pos); count_launch();
   return cudaGetLastError();
 }
 
 cudaError_t augmented_count(int64_t m, int64_t n, const int64_t* rp, const int64_t* trp, const int64_t* pos,
                             int64_t* krp, cudaStream_t st) {
-  k_aug_count<<<grid_for(n + m, 256), 256, 0, st>>>(m, n, rp, trp, pos, krp);
+  k_aug_count<<<grid_for(n + m, 256), 256, 0, st>>>(m, n, rp, trp, pos, krp); count_launch();
   return cudaGetLastError();
 }
 
@@ -415,16 +415,16 @@ cudaError_t augmented_fill(int64_t m, int64_t n, const int64_t* rp, const int32_
                            const int64_t* trp, const int32_t* tci, const double* tv, const double* theta, double rho,
                            const int64_t* pos, const int64_t* krp, int32_t* kci, double* kv, int64_t* xdiag,
                            cudaStream_t st) {
-  k_aug_fill<<<grid_for(n + m, 256), 256, 0, st>>>(m, n, rp, ci, v, trp, tci, tv, theta, rho, pos, krp, kci, kv);
+  k_aug_fill<<<grid_for(n + m, 256), 256, 0, st>>>(m, n, rp, ci, v, trp, tci, tv, theta, rho, pos, krp, kci, kv); count_launch();
   SDSL_CUDA_TRY(cudaGetLastError());
-  k_sort_segments<<<grid_for(n + m, 256), 256, 0, st>>>(n + m, krp, kci, kv);
+  k_sort_segments<<<grid_for(n + m, 256), 256, 0, st>>>(n + m, krp, kci, kv); count_launch();
   SDSL_CUDA_TRY(cudaGetLastError());
-  k_aug_xdiag<<<grid_for(n, 256), 256, 0, st>>>(n, pos, krp, kci, xdiag);
+  k_aug_xdiag<<<grid_for(n, 256), 256, 0, st>>>(n, pos, krp, kci, xdiag); count_launch();
   return cudaGetLastError();
 }
 
 cudaError_t augmented_theta(int64_t n, const double* theta, const int64_t* xdiag, double* kv, cudaStream_t st) {
-  k_aug_theta<<<grid_for(n, 256), 256, 0, st>>>(n, theta, xdiag, kv);
+  k_aug_theta<<<grid_for(n, 256), 256, 0, st>>>(n, theta, xdiag, kv); count_launch();
   return cudaGetLastError();
 }
 

@@ -29,7 +29,8 @@ class sdsl_options(C.Structure):
         ("col_block_ptr", C.c_void_p), ("border", C.c_int64), ("tau", C.c_double), ("delta", C.c_double),
         ("rho", C.c_double), ("factor_prec", C.c_int), ("rtol", C.c_double), ("maxit", C.c_int64),
         ("restart", C.c_int), ("refactor_ratio", C.c_double), ("mem_space", C.c_int), ("stream", C.c_void_p),
-        ("graph_iters", C.c_int), ("tune", C.c_int),
+        ("graph_iters", C.c_int), ("tune", C.c_int), ("profile", C.c_int), ("apply_prec", C.c_int),
+        ("flexible", C.c_int), ("solve_kernel", C.c_int), ("spmv_form", C.c_int),
     ]
 
 
@@ -41,10 +42,16 @@ class sdsl_stats(C.Structure):
         ("nnz_system", C.c_int64), ("nnz_precond", C.c_int64), ("nnz_factor", C.c_int64),
         ("levels_lower", C.c_int64), ("levels_upper", C.c_int64), ("max_levels", C.c_int64),
         ("shifted_blocks", C.c_int64), ("builds", C.c_int64), ("bytes_per_iter", C.c_double),
+        ("kernel_ms", C.c_double * 4), ("kernel_launches", C.c_int64 * 4), ("kernel_bytes", C.c_double * 4),
+        ("spmv_lanes", C.c_int64), ("solve_lanes", C.c_int64), ("tuned_spmv_lanes", C.c_int64),
     ]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        d = {}
+        for k, _ in self._fields_:
+            v = getattr(self, k)
+            d[k] = list(v) if hasattr(v, "__len__") else v
+        return d
 
 
 class sdsl_info(C.Structure):
@@ -84,6 +91,8 @@ def load():
     L.sdsl_precond_apply.argtypes = [H, _VP, _VP]
     L.sdsl_status_str.argtypes = [C.c_int]
     L.sdsl_status_str.restype = C.c_char_p
+    L.sdsl_kernel_launches.argtypes = []
+    L.sdsl_kernel_launches.restype = C.c_int64
     L.sdsl_last_error.argtypes = []
     L.sdsl_last_error.restype = C.c_char_p
     for f in ("sdsl_setup", "sdsl_factor", "sdsl_solve", "sdsl_update_diag", "sdsl_free", "sdsl_get_stats",
@@ -210,6 +219,10 @@ def sdsl_export_levels(h, which):
     rows = np.zeros(max(info.n, 1), np.int32)
     _check(load().sdsl_export_levels(h, int(which), nlev.ctypes.data, lptr.ctypes.data, rows.ctypes.data))
     return nlev[: info.nblocks], lptr, rows
+
+
+def sdsl_kernel_launches() -> int:
+    return int(load().sdsl_kernel_launches())
 
 
 def sdsl_spmv(h, x, y):

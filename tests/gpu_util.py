@@ -18,8 +18,8 @@ def setup(prob, prec=64, graph_iters=16, device=False, **over):
     return h, (o, keep, arrs)
 
 
-def run_bj(prob, prec=64, graph_iters=16, b=None, x0=None):
-    h, keep = setup(prob, prec, graph_iters)
+def run_bj(prob, prec=64, graph_iters=16, b=None, x0=None, **over):
+    h, keep = setup(prob, prec, graph_iters, **over)
     try:
         sdsl.sdsl_factor(h)
         b = prob.b if b is None else b

@@ -70,5 +70,6 @@ def test_struct_layouts_match_header(lib):
             if not decl:
                 continue
             for part in decl.split(","):
+                part = re.sub(r"\[[^\]]*\]", "", part.strip())  # arrays: keep the name
                 names.append(re.findall(r"([A-Za-z_][A-Za-z_0-9]*)\s*$", part.strip())[0])
         assert names == [f for f, _ in cls._fields_], struct

@@ -86,6 +86,39 @@ def test_bj_parity_fp64(case):
     check_solution(prob, ref_state, ref, g)
 
 
+@pytest.mark.parametrize("kernel", [1, 2])
+@pytest.mark.parametrize("case", ["c1", "c2-5pct"])
+def test_both_solve_kernels_fp64(case, kernel):
+    """Level-synchronous and flag-synchronised block solves give the same
+    parity (FP64 factors, FP64 apply)."""
+    prob = CASES[case]()
+    ref_state, ref = oracle.bj_solve(prob)
+    g = run_bj(prob, 64, solve_kernel=kernel)
+    check_structures(prob, ref_state, g)
+    check_solution(prob, ref_state, ref, g)
+
+
+@pytest.mark.parametrize("form", [1, 2])
+def test_explicit_and_factored_products(form):
+    """The PCG product with the explicit CSR of S and in the factored form
+    A (theta o (A^T p)) + rho p are the same operator: both reach the oracle's
+    solution and iteration count."""
+    prob = CASES["c2-5pct"]()
+    ref_state, ref = oracle.bj_solve(prob)
+    g = run_bj(prob, 64, spmv_form=form)
+    check_solution(prob, ref_state, ref, g)
+
+
+def test_fp32_storage_fp64_apply():
+    """FP32-stored factors applied in FP64 arithmetic: a fixed linear
+    preconditioner, so the iteration count stays within 5 % of the oracle's."""
+    prob = CASES["c2-5pct"]()
+    ref_state, ref = oracle.bj_solve(prob)
+    g = run_bj(prob, 32, apply_prec=64)
+    check_solution(prob, ref_state, ref, g, iters_exact=False)
+    assert g["stats"]["iters"] <= 1.1 * ref.iters + 2
+
+
 @pytest.mark.parametrize("case", ["c1", "c2-5pct"])
 def test_bj_parity_fp32_factors(case):
     """FP32 factors under the FP64 loop: same structures, factor values within
