@@ -43,6 +43,9 @@ def parse():
     ap.add_argument("--scale", type=float, default=1.0, help="workload scale (1.0 = the benchmark size)")
     ap.add_argument("--quick", action="store_true", help="no CPU baseline, e2e, FP64 form or profile pass")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--solve-kernel", type=int, default=0, help="block solves: 0 auto, 1 level-sync, 2 flag-free, "
+                                                                 "3 TMA-staged")
+    ap.add_argument("--apply-prec", type=int, default=0, choices=[0, 32, 64])
     return ap.parse_args()
 
 
@@ -204,6 +207,8 @@ def run_ours(args, ws, rank, local):
     def one_solve(prec, profile=False, host_io=False, xbuf=None, bbuf=None, arrays=None):
         o, keep = sdsl.options_for(prob, factor_prec=prec, graph_iters=16, stream=stream.cuda_stream)
         o.profile = 1 if profile else 0
+        o.solve_kernel = args.solve_kernel
+        o.apply_prec = args.apply_prec if prec == 32 else 0
         arrs = arrays if arrays is not None else (d_rp, d_ci, d_v, d_th)
         h = sdsl.sdsl_setup(o, A.nrows, A.ncols, *arrs)
         try:

@@ -81,7 +81,8 @@ typedef struct {
                                     (robust to an FP32 apply); -1 = 1 iff the apply is FP32 */
   int solve_kernel;              /* block triangular solves: 0 auto, 1 level-synchronous (barrier per
                                     level), 2 flag-synchronised (rows in level order, per-row ready flags
-                                    in shared memory; needs the block to fit in shared memory) */
+                                    in shared memory; needs the block to fit in shared memory), 3 as 2
+                                    with level tiles staged into shared memory by TMA bulk copies */
   int spmv_form;                 /* PCG product S p (normal form): 0 auto (fewer HBM bytes), 1 explicit
                                     CSR of S, 2 factored A (theta o (A^T p)) + rho p */
 } sdsl_options;

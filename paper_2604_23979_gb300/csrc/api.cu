@@ -455,6 +455,129 @@ sdsl_status build_levels(sdsl_handle h, int dir, int32_t** off, int32_t** ptr, i
   return sync(h, "level lists");
 }
 
+// Variable-width tile streams of the TMA-staged sweeps (both directions).
+// Rows of one level are packed into 32-lane tiles, each row with V lanes
+// (the smallest power of two with 4V >= its entry count, at most 32), in
+// order of decreasing V so that groups sit at V-aligned lane offsets.
+// Returns SDSL_OK with *ok = false if the staging does not fit in shared
+// memory (the caller then uses another solve kernel).
+sdsl_status build_vtiles(sdsl_handle h, bool f32, int apply, bool* ok) {
+  TriSolve& M = h->M;
+  const int64_t nb = h->nblocks;
+  const int64_t nrows = h->h_bp[nb];
+  const int tsz = f32 ? 4 : 8;
+  const int tc = apply == 32 ? 4 : 8;
+  struct Plan {
+    std::vector<int32_t> trp{0}, rows;
+    std::vector<int8_t> logv;
+    std::vector<int64_t> toff{0}, tile_ptr;
+    int64_t max_bytes = 0;
+  } plan[2];
+  std::vector<int32_t> lptr, lrows;
+  std::vector<int64_t> lens(nrows);
+  int64_t* d_len;
+  Arena tmp;
+  tmp.st = h->st;
+  TRY(tmp.get(&d_len, nrows + 1));
+  for (int dir = 0; dir < 2; ++dir) {
+    const int64_t tot = dir == 0 ? h->tot_lo : h->tot_up;
+    const std::vector<int32_t>& nl = dir == 0 ? h->h_nlev_lo : h->h_nlev_up;
+    const int32_t* d_rows = dir == 0 ? h->lev_rows_lo : h->lev_rows_up;
+    lptr.resize(tot + 1);
+    lrows.resize(nrows);
+    TRY(to_host(h, lptr.data(), dir == 0 ? h->lev_ptr_lo : h->lev_ptr_up, tot + 1));
+    TRY(to_host(h, lrows.data(), d_rows, nrows));
+    TRY_CUDA(pack_count(dir, nrows, h->row_block, h->d_bp, h->p_rp, h->p_ci, h->p_diag, d_rows, d_len, h->st));
+    TRY(to_host(h, lens.data(), d_len, nrows));  // entry count of level position q
+    TRY(sync(h, "tile plan"));
+    Plan& P = plan[dir];
+    P.tile_ptr.assign(nb + 1, 0);
+    std::vector<std::pair<int, int32_t>> lev;  // (-logV, position)
+    int64_t L = 0, tiles = 0;
+    for (int64_t k = 0; k < nb; ++k) {
+      P.tile_ptr[k] = tiles;
+      for (int32_t l = 0; l < nl[k]; ++l, ++L) {
+        lev.clear();
+        for (int32_t q = lptr[L]; q < lptr[L + 1]; ++q) {
+          int lv = 0;
+          while (lv < 5 && (4 << lv) < lens[q]) ++lv;
+          lev.emplace_back(-lv, q);
+        }
+        std::stable_sort(lev.begin(), lev.end(),
+                         [](const std::pair<int, int32_t>& x, const std::pair<int, int32_t>& y) { return x.first < y.first; });
+        int used = 32, nr = 0;
+        int64_t ne = 0;
+        auto close = [&]() {
+          if (nr == 0) return;
+          const int64_t bytes = 16 + 256 + ((nr * tsz + 15) & ~15) + ((4 * ne + 15) & ~15) + ((ne * tsz + 15) & ~15);
+          P.toff.push_back(P.toff.back() + bytes);
+          P.trp.push_back((int32_t)P.rows.size());
+          P.max_bytes = std::max(P.max_bytes, bytes);
+          ++tiles;
+          nr = 0;
+          ne = 0;
+        };
+        for (const auto& e : lev) {
+          const int V = 1 << (-e.first);
+          if (used + V > 32) { close(); used = 0; }
+          P.rows.push_back(lrows[e.second]);
+          P.logv.push_back((int8_t)(-e.first));
+          used += V;
+          ++nr;
+          ne += lens[e.second];
+        }
+        close();
+        used = 32;
+      }
+    }
+    P.tile_ptr[nb] = tiles;
+  }
+  tmp.release();
+  // ring geometry within the shared-memory budget
+  int64_t mt = 0;
+  for (int64_t k = 0; k < nb; ++k)
+    mt = std::max<int64_t>(mt, (plan[0].tile_ptr[k + 1] - plan[0].tile_ptr[k]) +
+                                   (plan[1].tile_ptr[k + 1] - plan[1].tile_ptr[k]));
+  int64_t maxb = 0;
+  for (int64_t k = 0; k < nb; ++k) maxb = std::max(maxb, h->h_bp[k + 1] - h->h_bp[k]);
+  const size_t budget = (size_t)225 * 1024;
+  const size_t fixed = tma_smem_bytes(maxb, tc, 16, 0, 0) + (size_t)(mt + 2) * 8;
+  const int64_t big = std::max(plan[0].max_bytes, plan[1].max_bytes);
+  const int slots = 4;  // ring depth of the staged sweeps (copies of three tiles ahead in flight)
+  int slot = (int)std::min<int64_t>(((big + 255) / 256) * 256, 3072);
+  while (slot >= 512 && fixed + (size_t)16 * slots * ((size_t)slot + 8) > budget) slot -= 256;
+  if (slot < 512 || maxb > 65535) { *ok = false; return SDSL_OK; }
+  M.slot_bytes = slot;
+  M.slots = slots;
+  M.max_tiles = mt;
+  for (int dir = 0; dir < 2; ++dir) {
+    Plan& P = plan[dir];
+    const int64_t ntiles = (int64_t)P.trp.size() - 1;
+    int32_t *d_trp, *d_rows;
+    int8_t* d_logv;
+    int64_t *d_toff, *d_tile;
+    unsigned char* stream;
+    TRY(h->pc.get(&d_trp, ntiles + 1));
+    TRY(h->pc.get(&d_rows, P.rows.size()));
+    TRY(h->pc.get(&d_logv, P.logv.size()));
+    TRY(h->pc.get(&d_toff, ntiles + 1));
+    TRY(h->pc.get(&d_tile, nb + 1));
+    TRY(h->pc.get(&stream, P.toff.back()));
+    TRY(to_dev(h, d_trp, P.trp.data(), ntiles + 1));
+    TRY(to_dev(h, d_rows, P.rows.data(), P.rows.size()));
+    TRY(to_dev(h, d_logv, P.logv.data(), P.logv.size()));
+    TRY(to_dev(h, d_toff, P.toff.data(), ntiles + 1));
+    TRY(to_dev(h, d_tile, P.tile_ptr.data(), nb + 1));
+    TRY_CUDA(vt_fill(dir, ntiles, d_trp, d_rows, d_logv, h->row_block, h->d_bp, h->p_rp, h->p_ci, h->p_diag, h->F,
+                     h->dinv, f32 ? 32 : 64, d_toff, stream, h->st));
+    if (dir == 0) { M.fwd_stream = stream; M.fwd_toff = d_toff; M.fwd_tile = d_tile; }
+    else { M.bwd_stream = stream; M.bwd_toff = d_toff; M.bwd_tile = d_tile; }
+  }
+  TRY(sync(h, "tile streams"));
+  *ok = true;
+  return SDSL_OK;
+}
+
 sdsl_status factor_impl(sdsl_handle h) {
   cudaEventRecord(h->ev_a, h->st);
   h->pc.release();
@@ -621,12 +744,37 @@ sdsl_status factor_impl(sdsl_handle h) {
   M.flexible = h->opt.flexible < 0 ? (apply == 32 ? 1 : 0) : (h->opt.flexible ? 1 : 0);
   M.threads = 1024;
   const bool fits = sf_smem_bytes(maxb, apply == 32 ? 4 : 8) <= (size_t)200 * 1024;
-  if (h->opt.solve_kernel == 2 && !fits)
+  M.slot_bytes = apply == 32 ? 1536 : 1024;
+  const double avg_half2 = N > 0 ? (double)(h->p_nnz - N) / (2.0 * (double)N) : 1.0;
+  const int sweep_lanes = std::max(4, pow2_lanes(avg_half2, 4.0));
+  // bound of the staged tile offsets: every level padded to whole tiles of
+  // RW rows -> at most rows/RW + levels tiles per direction
+  {
+    const int64_t RWb = 32 / sweep_lanes;
+    int64_t mt = 0;
+    for (int64_t k = 0; k < nb; ++k) {
+      const int64_t rows = h->h_bp[k + 1] - h->h_bp[k];
+      mt = std::max<int64_t>(mt, 2 * (rows / RWb + 1) + h->h_nlev_lo[k] + h->h_nlev_up[k]);
+    }
+    M.max_tiles = mt;
+  }
+  const bool fits_tma = tma_smem_bytes(maxb, apply == 32 ? 4 : 8, 16, 1024, 2) +
+                        (size_t)(M.max_tiles + 2) * 8 <= (size_t)225 * 1024;
+  if ((h->opt.solve_kernel == 2 && !fits) || (h->opt.solve_kernel == 3 && !fits_tma))
     return fail(SDSL_ERR_ARG, "flag-synchronised solves need the largest block to fit in shared memory");
-  M.sync_free = (h->opt.solve_kernel == 2 || (h->opt.solve_kernel == 0 && fits)) ? 1 : 0;
+  M.tma = (h->opt.solve_kernel == 3 || (h->opt.solve_kernel == 0 && fits_tma)) ? 1 : 0;
+  if (M.tma) {
+    bool ok = false;
+    TRY(build_vtiles(h, f32, apply, &ok));
+    if (!ok) {
+      if (h->opt.solve_kernel == 3)
+        return fail(SDSL_ERR_ARG, "TMA-staged solves need the largest block to fit in shared memory");
+      M.tma = 0;
+    }
+  }
+  M.sync_free = (!M.tma && (h->opt.solve_kernel == 2 || (h->opt.solve_kernel == 0 && fits))) ? 1 : 0;
   if (M.sync_free) {
-    const double avg_half2 = N > 0 ? (double)(h->p_nnz - N) / (2.0 * (double)N) : 1.0;
-    M.lanes = std::max(4, pow2_lanes(avg_half2, 4.0));
+    M.lanes = sweep_lanes;
     const int RW = 32 / M.lanes;
     const int64_t nrows = h->h_bp[nb];
     const size_t vs = f32 ? 4 : 8;
@@ -859,7 +1007,7 @@ sdsl_status sdsl_setup(const sdsl_options* opt, int64_t m, int64_t n, const int6
   if (opt->form < SDSL_FORM_CSR || opt->form > SDSL_FORM_AUGMENTED) return fail(SDSL_ERR_ARG, "unknown form");
   if (opt->method != SDSL_BJ_PCG && opt->method != SDSL_BBD_GMRES) return fail(SDSL_ERR_ARG, "unknown method");
   if (opt->factor_prec != 64 && opt->factor_prec != 32) return fail(SDSL_ERR_ARG, "factor_prec must be 64 or 32");
-  if (opt->solve_kernel < 0 || opt->solve_kernel > 2) return fail(SDSL_ERR_ARG, "solve_kernel must be 0, 1 or 2");
+  if (opt->solve_kernel < 0 || opt->solve_kernel > 3) return fail(SDSL_ERR_ARG, "solve_kernel must be 0..3");
   if (opt->spmv_form < 0 || opt->spmv_form > 2) return fail(SDSL_ERR_ARG, "spmv_form must be 0, 1 or 2");
   if (opt->apply_prec != 0 && opt->apply_prec != 64 && opt->apply_prec != 32)
     return fail(SDSL_ERR_ARG, "apply_prec must be 0, 32 or 64");

@@ -72,6 +72,21 @@ cudaError_t ilu0_factor(int64_t nblocks, const int64_t* bp, const int64_t* prp, 
 cudaError_t ic0_finish(int64_t n, int64_t nnz, const int64_t* prp, const int64_t* pdiag, const int64_t* mir,
                        double* F, const double* dinv, float* Ff, float* dinvf, cudaStream_t st);
 cudaError_t to_float(int64_t n, const double* a, float* b, cudaStream_t st);
+// Tile streams of the TMA-staged solves (see TriSolve): bytes per tile, then fill.
+cudaError_t tile_count(int dir, int64_t ntiles, int RW, int tsz, const int32_t* sched, const int32_t* row_block,
+                       const int64_t* bp, const int64_t* prp, const int32_t* pci, const int64_t* pdiag,
+                       int64_t* tbytes, cudaStream_t st);
+cudaError_t tile_fill(int dir, int64_t ntiles, int RW, int prec, const int32_t* sched, const int32_t* row_block,
+                      const int64_t* bp, const int64_t* prp, const int32_t* pci, const int64_t* pdiag,
+                      const double* F, const double* dinv, const int64_t* toff, unsigned char* stream,
+                      cudaStream_t st);
+// Variable-width tiles (see precond.cu): fill the stream from a host-built plan.
+cudaError_t vt_fill(int dir, int64_t ntiles, const int32_t* tile_rows_ptr, const int32_t* plan_rows,
+                    const int8_t* plan_logv, const int32_t* row_block, const int64_t* bp, const int64_t* prp,
+                    const int32_t* pci, const int64_t* pdiag, const double* F, const double* dinv, int prec,
+                    const int64_t* toff, unsigned char* stream, cudaStream_t st);
+// Dynamic shared memory of the TMA-staged solve.
+size_t tma_smem_bytes(int64_t max_block, size_t tc_size, int warps, int slot_bytes, int slots);
 
 // ---- krylov.cu: SpMV, PCG iteration kernels, residuals
 struct PcgState {
@@ -129,6 +144,19 @@ struct TriSolve {  // block triangular factors on the layout of P
   const int32_t* bwd_row;
   const int64_t* fwd_pos;   // per block: first position of its padded schedule (nblocks+1)
   const int64_t* bwd_pos;
+  // TMA-staged tile streams (solve_kernel 3): tile t of a direction is the
+  // byte range [toff[t], toff[t+1]) of the stream; block b owns tiles
+  // tile_ptr[b] .. tile_ptr[b+1]-1.
+  const unsigned char* fwd_stream;
+  const int64_t* fwd_toff;
+  const int64_t* fwd_tile;
+  const unsigned char* bwd_stream;
+  const int64_t* bwd_toff;
+  const int64_t* bwd_tile;
+  int tma;              // 1: TMA-staged tiles (bulk copies into a per-warp shared-memory ring)
+  int slot_bytes;       // ring slot size; larger tiles are read from global memory directly
+  int64_t max_tiles;    // max over blocks of (forward tiles + backward tiles): staged tile offsets
+  int slots;            // ring slots per warp
   int sync_free;        // 1: packed flag-synchronised solves (block fits in shared memory)
   int apply_prec;       // arithmetic of the apply: 64 or 32
   int flexible;         // 1: beta = -alpha z_new^T q / rho (robust to an inexact FP32 apply)

@@ -86,11 +86,11 @@ def test_bj_parity_fp64(case):
     check_solution(prob, ref_state, ref, g)
 
 
-@pytest.mark.parametrize("kernel", [1, 2])
+@pytest.mark.parametrize("kernel", [1, 2, 3])
 @pytest.mark.parametrize("case", ["c1", "c2-5pct"])
 def test_both_solve_kernels_fp64(case, kernel):
-    """Level-synchronous and flag-synchronised block solves give the same
-    parity (FP64 factors, FP64 apply)."""
+    """Level-synchronous, flag-synchronised and TMA-staged block solves give
+    the same parity (FP64 factors, FP64 apply)."""
     prob = CASES[case]()
     ref_state, ref = oracle.bj_solve(prob)
     g = run_bj(prob, 64, solve_kernel=kernel)
