@@ -366,7 +366,7 @@ sdsl_status tune_spmv(sdsl_handle h) {
   int best_l = h->A.lanes;
   SpmvPlan P = h->A;
   TRY_CUDA(cudaMemsetAsync(h->p, 0, sizeof(double) * (size_t)h->N, h->st));
-  for (int l = 2; l <= 32; l <<= 1) {
+  for (int l = 1; l <= 32; l <<= 1) {
     P.lanes = l;
     float ms = 0.f;
     TRY_CUDA(time_spmv(P, h->p, h->q, 3, &ms, h->st));

@@ -27,8 +27,10 @@ __device__ __forceinline__ T warp_sum(T v) {
 // group ends with the group's sum.  Fixed butterfly order => deterministic.
 template <int G, typename T>
 __device__ __forceinline__ T group_sum(T v) {
+  if (G > 1) {
 #pragma unroll
-  for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  }
   return v;
 }
 

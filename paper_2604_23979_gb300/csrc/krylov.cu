@@ -618,6 +618,7 @@ __global__ void k_init_state(PcgState* s, double tol2, long long maxit) {
 template <typename F>
 cudaError_t by_lanes(int lanes, F&& f) {
   switch (lanes) {
+    case 1: return f(std::integral_constant<int, 1>{});
     case 2: return f(std::integral_constant<int, 2>{});
     case 4: return f(std::integral_constant<int, 4>{});
     case 8: return f(std::integral_constant<int, 8>{});
