@@ -85,6 +85,7 @@ typedef struct {
                                     with level tiles staged into shared memory by TMA bulk copies */
   int spmv_form;                 /* PCG product S p (normal form): 0 auto (fewer HBM bytes), 1 explicit
                                     CSR of S, 2 factored A (theta o (A^T p)) + rho p */
+  int orthog;                    /* GMRES orthogonalization: 0 modified Gram-Schmidt, 1 classical twice */
 } sdsl_options;
 
 typedef struct {
@@ -122,7 +123,8 @@ typedef struct {
 /* Fill *o with the defaults: BJ-PCG, normal form, tau 1e-3, delta 1e-12,
  * rho 1e-6, FP64 factors, rtol 1e-8, maxit 2000, restart 30, refactor_ratio
  * 1.5, device pointers, default stream, graph_iters 16, tune 0, profile 0,
- * apply_prec 0 (= factor_prec), flexible -1 (auto), solve_kernel 0 (auto), spmv_form 0 (auto). */
+ * apply_prec 0 (= factor_prec), flexible -1 (auto), solve_kernel 0 (auto), spmv_form 0 (auto),
+ * orthog 0 (modified Gram-Schmidt). */
 void sdsl_default_options(sdsl_options* o);
 
 /* Create a handle and form the system matrix on the device.

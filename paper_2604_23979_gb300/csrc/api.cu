@@ -139,6 +139,15 @@ struct sdsl_handle_s {
   cudaGraphExec_t graph = nullptr;
   int graph_iters = 0;
   cudaEvent_t prof_ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  // BBD: border, dense Schur complement (FP64), its FP32 LU and inverse,
+  // GMRES bases and apply scratch
+  int64_t b0 = 0, nbord = 0;
+  double* SB = nullptr;
+  float *LU32 = nullptr, *Sinv = nullptr;
+  int32_t* ipiv = nullptr;
+  double *V = nullptr, *Z = nullptr, *bt = nullptr, *bg = nullptr, *bz = nullptr, *bres = nullptr, *bcor = nullptr;
+  double *gpart = nullptr, *gh = nullptr;
+  std::vector<int32_t> h_lev_off_lo, h_lev_off_up;
   // reuse bookkeeping (Sec. 3.4)
   bool factored = false, need_rebuild = false;
   int64_t iters_post_build = -1;
@@ -455,6 +464,201 @@ sdsl_status build_levels(sdsl_handle h, int dir, int32_t** off, int32_t** ptr, i
   return sync(h, "level lists");
 }
 
+// BBD preconditioner (Sec. 2.4, third step): dense Schur complement of the
+// border, its FP32 LU with partial pivoting and the explicit inverse.
+sdsl_status build_bbd(sdsl_handle h) {
+  const int64_t nb = h->nblocks, N = h->N;
+  h->b0 = h->h_bp[nb];
+  h->nbord = N - h->b0;
+  const int64_t m = h->nbord;
+  h->h_lev_off_lo.assign(nb + 1, 0);
+  h->h_lev_off_up.assign(nb + 1, 0);
+  for (int64_t k = 0; k < nb; ++k) {
+    h->h_lev_off_lo[k + 1] = h->h_lev_off_lo[k] + h->h_nlev_lo[k];
+    h->h_lev_off_up[k + 1] = h->h_lev_off_up[k] + h->h_nlev_up[k];
+  }
+  TRY(h->pc.get(&h->bt, N));
+  TRY(h->pc.get(&h->bg, m + 1));
+  TRY(h->pc.get(&h->bz, m + 1));
+  TRY(h->pc.get(&h->bres, m + 1));
+  TRY(h->pc.get(&h->bcor, m + 1));
+  if (m == 0) return SDSL_OK;
+  TRY(h->pc.get(&h->SB, m * m));
+  TRY(h->pc.get(&h->LU32, m * m));
+  TRY(h->pc.get(&h->Sinv, m * m));
+  TRY(h->pc.get(&h->ipiv, m));
+  TRY_CUDA(schur_init(m, h->b0, h->p_rp, h->p_ci, h->p_v, h->SB, h->st));
+  int64_t maxb = 0;
+  for (int64_t k = 0; k < nb; ++k) maxb = std::max(maxb, h->h_bp[k + 1] - h->h_bp[k]);
+  Arena tmp;
+  tmp.st = h->st;
+  double* X;
+  float* work;
+  TRY(tmp.get(&X, (size_t)schur_tiles(m) * maxb * 32));
+  for (int64_t k = 0; k < nb; ++k)  // blocks in order: deterministic accumulation
+    TRY_CUDA(schur_block(h->h_bp[k], h->h_bp[k + 1], h->b0, m, h->p_rp, h->p_ci, h->p_v, h->F, h->dinv, h->p_diag,
+                         h->h_lev_off_lo[k], h->h_lev_off_lo[k + 1], h->lev_ptr_lo, h->lev_rows_lo,
+                         h->h_lev_off_up[k], h->h_lev_off_up[k + 1], h->lev_ptr_up, h->lev_rows_up, X, h->SB, h->st));
+  TRY_CUDA(cudaMemsetAsync(h->flag, 0, sizeof(int), h->st));
+  TRY_CUDA(dense_lu_f32(m, h->SB, h->LU32, h->ipiv, h->flag, h->st));
+  TRY(tmp.get(&work, (size_t)m * ((m + 31) / 32) * 32));
+  TRY_CUDA(dense_lu_inverse(m, h->LU32, h->ipiv, h->Sinv, work, h->st));
+  int bad = 0;
+  TRY(to_host(h, &bad, h->flag, 1));
+  TRY(sync(h, "schur lu"));
+  tmp.release();
+  if (bad) return fail(SDSL_ERR_BREAKDOWN, "zero pivot in the LU of the border Schur complement");
+  return SDSL_OK;
+}
+
+// z = M^{-1} r for the BBD preconditioner (Sec. 2.4, fourth step).  The
+// border solve uses the FP32 inverse of S_B with FP64 iterative refinement
+// against the FP64 S_B (at most 10 steps, until ||g - S_B z_B|| <= 1e-12 ||g||).
+sdsl_status bbd_apply(sdsl_handle h, const double* r, double* z) {
+  const int64_t b0 = h->b0, m = h->nbord, nb = h->nblocks;
+  TRY_CUDA(copy_vec(b0, r, h->bt, h->st));
+  TRY_CUDA(block_lu_solve(nb, h->d_bp, h->p_rp, h->p_ci, h->F, h->dinv, h->p_diag, h->lev_off_lo, h->lev_ptr_lo,
+                          h->lev_rows_lo, h->lev_off_up, h->lev_ptr_up, h->lev_rows_up, h->bt, h->st));
+  if (m > 0) {
+    TRY_CUDA(border_gather(m, b0, h->p_rp, h->p_ci, h->p_v, r, h->bt, h->bg, h->st));
+    TRY_CUDA(dense_mv(m, h->Sinv, nullptr, h->bg, nullptr, h->bz, 0, h->st));
+    double* nrm = h->scalars + 4;
+    TRY_CUDA(norm2_sq(m, h->bg, h->part, nrm + 1, reinterpret_cast<unsigned int*>(h->part + 152 * 32), h->st));
+    for (int it = 0; it < 10; ++it) {
+      TRY_CUDA(dense_mv(m, nullptr, h->SB, h->bz, h->bg, h->bres, 1, h->st));
+      TRY_CUDA(norm2_sq(m, h->bres, h->part, nrm, reinterpret_cast<unsigned int*>(h->part + 152 * 32), h->st));
+      double hn[2];
+      TRY(to_host(h, hn, nrm, 2));
+      TRY(sync(h, "refinement"));
+      if (!(hn[0] > 1e-24 * hn[1])) break;
+      TRY_CUDA(dense_mv(m, h->Sinv, nullptr, h->bres, nullptr, h->bcor, 0, h->st));
+      TRY_CUDA(axpy(m, 1.0, h->bcor, h->bz, h->st));
+    }
+  }
+  TRY_CUDA(border_scatter(b0, h->p_rp, h->p_ci, h->p_diag, h->p_v, r, h->bz, z, h->st));
+  TRY_CUDA(block_lu_solve(nb, h->d_bp, h->p_rp, h->p_ci, h->F, h->dinv, h->p_diag, h->lev_off_lo, h->lev_ptr_lo,
+                          h->lev_rows_lo, h->lev_off_up, h->lev_ptr_up, h->lev_rows_up, z, h->st));
+  if (m > 0) TRY_CUDA(copy_vec(m, h->bz, z + b0, h->st));
+  return SDSL_OK;
+}
+
+// Right-preconditioned restarted GMRES(m) (Sec. 2.2): K M^{-1} u = b,
+// x = M^{-1} u; classical Gram-Schmidt applied twice (CGS2) on the device,
+// Hessenberg least squares with Givens rotations on the host.  The count is
+// the number of Arnoldi steps (products K z).  Convergence on |g_{j+1}| <=
+// rtol ||b||, confirmed by the true residual at the end of every cycle.
+sdsl_status gmres_solve(sdsl_handle h) {
+  const int64_t N = h->N;
+  const int mres = std::max(1, h->opt.restart);
+  sdsl_stats& S = h->stats;
+  S.iters = 0;
+  S.restarts = 0;
+  double* bn2 = h->scalars;
+  TRY_CUDA(norm2_sq(N, h->b, h->part, bn2, reinterpret_cast<unsigned int*>(h->part + 152 * 32), h->st));
+  double bnorm2 = 0.0;
+  TRY(to_host(h, &bnorm2, bn2, 1));
+  TRY(sync(h, "gmres init"));
+  if (bnorm2 == 0.0) {
+    TRY_CUDA(cudaMemsetAsync(h->x, 0, sizeof(double) * (size_t)N, h->st));
+    S.rel_res_true = S.rel_res_rec = 0.0;
+    S.status = SDSL_OK;
+    return SDSL_OK;
+  }
+  const double bnorm = std::sqrt(bnorm2), tol = h->opt.rtol * bnorm;
+  std::vector<double> H((size_t)(mres + 1) * mres), cs(mres), sn(mres), g(mres + 1), y(mres), hv(mres + 2);
+  SpmvPlan A = h->A;
+  A.factored = 0;
+  double* hdev = h->gh;
+  int64_t it = 0;
+  double gres = 0.0, tnorm = 0.0;
+  sdsl_status result = SDSL_ERR_NOT_CONVERGED;
+  for (;;) {
+    TRY_CUDA(pcg_init_state(h->state, 0.0, 0, h->st));
+    TRY_CUDA(true_residual(A, h->b, h->x, h->r, h->part, h->state, 1, h->st));
+    TRY(to_host(h, h->h_state, h->state, 1));
+    TRY(sync(h, "gmres residual"));
+    tnorm = std::sqrt(h->h_state->tr);
+    gres = tnorm;
+    if (tnorm <= tol) { result = SDSL_OK; break; }
+    if (it >= h->opt.maxit) break;
+    S.restarts += 1;
+    double* nrm = h->scalars + 1;
+    {
+      const double tb = tnorm;
+      TRY(to_dev(h, nrm, &tb, 1));
+    }
+    TRY_CUDA(scale_to(N, nrm, 1, h->r, h->V, h->st));
+    std::fill(g.begin(), g.end(), 0.0);
+    g[0] = tnorm;
+    int jend = 0;
+    for (int j = 0; j < mres; ++j) {
+      double* vj = h->V + (int64_t)j * N;
+      double* zj = h->Z + (int64_t)j * N;
+      double* w = h->V + (int64_t)(j + 1) * N;
+      TRY(bbd_apply(h, vj, zj));
+      TRY_CUDA(spmv(A, zj, w, h->st));
+      ++it;
+      if (h->opt.orthog == 1) {
+        // CGS2: two passes of classical Gram-Schmidt against v_0 .. v_j
+        TRY_CUDA(multidot(N, j + 1, h->V, N, w, h->gpart, hdev, h->st));
+        TRY_CUDA(sub_multi(N, j + 1, h->V, N, hdev, w, h->st));
+        TRY_CUDA(multidot(N, j + 1, h->V, N, w, h->gpart, hdev + mres + 1, h->st));
+        TRY_CUDA(sub_multi(N, j + 1, h->V, N, hdev + mres + 1, w, h->st));
+        TRY_CUDA(norm2_sq(N, w, h->part, hdev + 2 * (mres + 1), reinterpret_cast<unsigned int*>(h->part + 152 * 32),
+                          h->st));
+      } else {
+        // modified Gram-Schmidt (the oracle's order): h_i = (w - sum_{l<i} h_l v_l)^T v_i
+        for (int i = 0; i <= j; ++i)
+          TRY_CUDA(mgs_step(N, w, i ? h->V + (int64_t)(i - 1) * N : nullptr, hdev + i - 1, h->V + (int64_t)i * N,
+                            h->gpart, hdev + i, h->st));
+        TRY_CUDA(mgs_step(N, w, h->V + (int64_t)j * N, hdev + j, nullptr, h->gpart, hdev + 2 * (mres + 1), h->st));
+        TRY_CUDA(cudaMemsetAsync(hdev + mres + 1, 0, sizeof(double) * (size_t)(mres + 1), h->st));
+      }
+      std::vector<double> hh(2 * (mres + 1) + 1);
+      TRY(to_host(h, hh.data(), hdev, 2 * (mres + 1) + 1));
+      TRY(sync(h, "arnoldi"));
+      const double hn = std::sqrt(hh[2 * (mres + 1)]);
+      for (int i = 0; i <= j; ++i) H[(size_t)i * mres + j] = hh[i] + hh[mres + 1 + i];
+      H[(size_t)(j + 1) * mres + j] = hn;
+      if (hn != 0.0) {
+        const double inv = hn;
+        TRY(to_dev(h, nrm, &inv, 1));
+        TRY_CUDA(scale_to(N, nrm, 1, w, w, h->st));
+      }
+      for (int i = 0; i < j; ++i) {
+        const double a = H[(size_t)i * mres + j], c = H[(size_t)(i + 1) * mres + j];
+        H[(size_t)i * mres + j] = cs[i] * a + sn[i] * c;
+        H[(size_t)(i + 1) * mres + j] = -sn[i] * a + cs[i] * c;
+      }
+      const double a = H[(size_t)j * mres + j], c = H[(size_t)(j + 1) * mres + j];
+      const double rr = std::hypot(a, c);
+      cs[j] = rr == 0.0 ? 1.0 : a / rr;
+      sn[j] = rr == 0.0 ? 0.0 : c / rr;
+      H[(size_t)j * mres + j] = rr;
+      H[(size_t)(j + 1) * mres + j] = 0.0;
+      g[j + 1] = -sn[j] * g[j];
+      g[j] = cs[j] * g[j];
+      gres = std::fabs(g[j + 1]);
+      jend = j + 1;
+      if (gres <= tol || it >= h->opt.maxit || hn == 0.0) break;
+    }
+    for (int i = jend - 1; i >= 0; --i) {
+      double acc = g[i];
+      for (int l = i + 1; l < jend; ++l) acc -= H[(size_t)i * mres + l] * y[l];
+      y[i] = acc / H[(size_t)i * mres + i];
+    }
+    TRY(to_dev(h, hdev, y.data(), jend));
+    TRY_CUDA(add_multi(N, jend, h->Z, N, hdev, h->x, h->st));
+  }
+  S.iters = it;
+  S.restarts = std::max<int64_t>(0, S.restarts - 1);
+  S.rel_res_true = tnorm / bnorm;
+  S.rel_res_rec = gres / bnorm;
+  S.status = result;
+  if (result == SDSL_OK) return SDSL_OK;
+  return fail(result, "GMRES reached maxit before the tolerance");
+}
+
 // Variable-width tile streams of the TMA-staged sweeps (both directions).
 // Rows of one level are packed into 32-lane tiles, each row with V lanes
 // (the smallest power of two with 4V >= its entry count, at most 32), in
@@ -708,6 +912,14 @@ sdsl_status factor_impl(sdsl_handle h) {
   } else {
     TRY_CUDA(ic0_finish(N, h->p_nnz, h->p_rp, h->p_diag, h->mir, h->F, h->dinv, h->Ff, h->dinvf, h->st));
   }
+  if (h->method == SDSL_BBD_GMRES) {
+    TRY(build_bbd(h));
+    const int mres = std::max(1, h->opt.restart);
+    TRY(h->pc.get(&h->V, (size_t)(mres + 1) * N));
+    TRY(h->pc.get(&h->Z, (size_t)mres * N));
+    TRY(h->pc.get(&h->gpart, (size_t)(mres + 1) * multidot_grid(N)));
+    TRY(h->pc.get(&h->gh, 2 * (mres + 1) + 2));
+  }
   // apply plan
   int64_t maxb = 0;
   for (int64_t k = 0; k < nb; ++k) maxb = std::max(maxb, h->h_bp[k + 1] - h->h_bp[k]);
@@ -762,7 +974,7 @@ sdsl_status factor_impl(sdsl_handle h) {
                         (size_t)(M.max_tiles + 2) * 8 <= (size_t)225 * 1024;
   if ((h->opt.solve_kernel == 2 && !fits) || (h->opt.solve_kernel == 3 && !fits_tma))
     return fail(SDSL_ERR_ARG, "flag-synchronised solves need the largest block to fit in shared memory");
-  M.tma = (h->opt.solve_kernel == 3 || (h->opt.solve_kernel == 0 && fits_tma)) ? 1 : 0;
+  M.tma = (h->method == SDSL_BJ_PCG && (h->opt.solve_kernel == 3 || (h->opt.solve_kernel == 0 && fits_tma))) ? 1 : 0;
   if (M.tma) {
     bool ok = false;
     TRY(build_vtiles(h, f32, apply, &ok));
@@ -772,7 +984,8 @@ sdsl_status factor_impl(sdsl_handle h) {
       M.tma = 0;
     }
   }
-  M.sync_free = (!M.tma && (h->opt.solve_kernel == 2 || (h->opt.solve_kernel == 0 && fits))) ? 1 : 0;
+  M.sync_free = (h->method == SDSL_BJ_PCG && !M.tma && (h->opt.solve_kernel == 2 || (h->opt.solve_kernel == 0 && fits)))
+                    ? 1 : 0;
   if (M.sync_free) {
     M.lanes = sweep_lanes;
     const int RW = 32 / M.lanes;
@@ -959,6 +1172,7 @@ void sdsl_default_options(sdsl_options* o) {
   o->graph_iters = 16;
   o->apply_prec = 0;
   o->flexible = -1;
+  o->orthog = 0;
 }
 
 const char* sdsl_status_str(sdsl_status s) {
@@ -1009,6 +1223,7 @@ sdsl_status sdsl_setup(const sdsl_options* opt, int64_t m, int64_t n, const int6
   if (opt->factor_prec != 64 && opt->factor_prec != 32) return fail(SDSL_ERR_ARG, "factor_prec must be 64 or 32");
   if (opt->solve_kernel < 0 || opt->solve_kernel > 3) return fail(SDSL_ERR_ARG, "solve_kernel must be 0..3");
   if (opt->spmv_form < 0 || opt->spmv_form > 2) return fail(SDSL_ERR_ARG, "spmv_form must be 0, 1 or 2");
+  if (opt->orthog < 0 || opt->orthog > 1) return fail(SDSL_ERR_ARG, "orthog must be 0 or 1");
   if (opt->apply_prec != 0 && opt->apply_prec != 64 && opt->apply_prec != 32)
     return fail(SDSL_ERR_ARG, "apply_prec must be 0, 32 or 64");
   if (opt->factor_prec == 64 && opt->apply_prec == 32)
@@ -1132,7 +1347,6 @@ sdsl_status sdsl_solve(sdsl_handle h, const double* b, double* x, int x0_zero, s
   if (!h) return fail(SDSL_ERR_ARG, "handle is NULL");
   if (!b || !x) return fail(SDSL_ERR_ARG, "b or x is NULL");
   if (!h->factored) return fail(SDSL_ERR_STATE, "sdsl_solve before sdsl_factor");
-  if (h->method != SDSL_BJ_PCG) return fail(SDSL_ERR_ARG, "BBD-GMRES solve not available in this build");
   Scope scope(h);
   int rebuilt = 0;
   if (h->need_rebuild) {
@@ -1143,7 +1357,7 @@ sdsl_status sdsl_solve(sdsl_handle h, const double* b, double* x, int x0_zero, s
   TRY(to_dev(h, h->b, b, h->N));
   if (x0_zero) TRY_CUDA(cudaMemsetAsync(h->x, 0, sizeof(double) * (size_t)h->N, h->st));
   else TRY(to_dev(h, h->x, (const double*)x, h->N));
-  sdsl_status s = pcg_solve(h, st);
+  sdsl_status s = h->method == SDSL_BBD_GMRES ? gmres_solve(h) : pcg_solve(h, st);
   TRY(to_host(h, x, h->x, h->N));
   cudaEventRecord(h->ev_b, h->st);
   TRY(sync(h, "solve end"));
@@ -1230,9 +1444,11 @@ sdsl_status sdsl_export_levels(sdsl_handle h, int which, int32_t* nlev, int64_t*
 }
 
 sdsl_status sdsl_export_schur(sdsl_handle h, double* sb) {
-  (void)sb;
-  if (!h) return fail(SDSL_ERR_ARG, "handle is NULL");
-  return fail(SDSL_ERR_STATE, "no Schur complement in this build");
+  if (!h || !sb) return fail(SDSL_ERR_ARG, "NULL argument");
+  if (h->method != SDSL_BBD_GMRES || !h->factored) return fail(SDSL_ERR_STATE, "no Schur complement (BBD, factored)");
+  Scope scope(h);
+  if (h->nbord > 0) TRY(to_host(h, sb, h->SB, h->nbord * h->nbord));
+  return sync(h, "export schur");
 }
 
 sdsl_status sdsl_spmv(sdsl_handle h, const double* x, double* y) {
@@ -1250,6 +1466,7 @@ sdsl_status sdsl_precond_apply(sdsl_handle h, const double* r, double* z) {
   if (!h || !r || !z) return fail(SDSL_ERR_ARG, "NULL argument");
   if (!h->factored) return fail(SDSL_ERR_STATE, "no preconditioner yet");
   Scope scope(h);
+  if (h->method == SDSL_BBD_GMRES) return bbd_apply(h, r, z);
   TRY_CUDA(precond_apply(h->M, r, z, nullptr, h->part_blk, h->state, 2, h->st));
   return SDSL_OK;
 }

@@ -220,4 +220,46 @@ cudaError_t true_residual(const SpmvPlan& A, const double* b, const double* x, d
 cudaError_t norm2_sq(int64_t n, const double* a, double* part, double* out, unsigned int* ticket, cudaStream_t st);
 cudaError_t pcg_init_state(PcgState* s, double tol2, long long maxit, cudaStream_t st);
 
+// ---- bbd.cu: BBD Schur complement, dense border LU, BBD apply, GMRES helpers
+cudaError_t schur_init(int64_t nb, int64_t b0, const int64_t* prp, const int32_t* pci, const double* pv, double* SB,
+                       cudaStream_t st);
+int64_t schur_tiles(int64_t nb);
+// S_B -= F_k (L_k U_k)^{-1} E_k for block [s, e); X: schur_tiles(nb) * (e-s) * 32 doubles.
+cudaError_t schur_block(int64_t s, int64_t e, int64_t b0, int64_t nb, const int64_t* prp, const int32_t* pci,
+                        const double* pv, const double* F, const double* dinv, const int64_t* pdiag, int32_t L0,
+                        int32_t L1, const int32_t* lev_ptr_lo, const int32_t* lev_rows_lo, int32_t U0, int32_t U1,
+                        const int32_t* lev_ptr_up, const int32_t* lev_rows_up, double* X, double* SB,
+                        cudaStream_t st);
+// FP32 LU with partial pivoting of the FP64 matrix SB (status = 1 on a zero pivot).
+cudaError_t dense_lu_f32(int64_t n, const double* SB, float* LU, int32_t* ipiv, int* status, cudaStream_t st);
+// Explicit inverse from the LU factors; work: n*n floats.
+cudaError_t dense_lu_inverse(int64_t n, const float* LU, const int32_t* ipiv, float* Xinv, float* work,
+                             cudaStream_t st);
+// y = U_k^{-1} L_k^{-1} y on every interior block (in place).
+cudaError_t block_lu_solve(int64_t nblocks, const int64_t* bp, const int64_t* prp, const int32_t* pci,
+                           const double* F, const double* dinv, const int64_t* pdiag, const int32_t* lev_off_lo,
+                           const int32_t* lev_ptr_lo, const int32_t* lev_rows_lo, const int32_t* lev_off_up,
+                           const int32_t* lev_ptr_up, const int32_t* lev_rows_up, double* y, cudaStream_t st);
+cudaError_t border_gather(int64_t nb, int64_t b0, const int64_t* prp, const int32_t* pci, const double* pv,
+                          const double* r, const double* t, double* g, cudaStream_t st);
+cudaError_t border_scatter(int64_t b0, const int64_t* prp, const int32_t* pci, const int64_t* pdiag,
+                           const double* pv, const double* r, const double* zB, double* w, cudaStream_t st);
+// y = A x (A FP32 if A32 != NULL else FP64); residual != 0: y = b - A x.
+cudaError_t dense_mv(int64_t n, const float* A32, const double* A64, const double* x, const double* b, double* y,
+                     int residual, cudaStream_t st);
+cudaError_t axpy(int64_t n, double a, const double* x, double* y, cudaStream_t st);
+cudaError_t copy_vec(int64_t n, const double* a, double* b, cudaStream_t st);
+int multidot_grid(int64_t n);
+// h[i] = V_i^T w (deterministic two-stage), part: nv * multidot_grid(n) doubles.
+cudaError_t multidot(int64_t n, int nv, const double* V, int64_t ldv, const double* w, double* part, double* h,
+                     cudaStream_t st);
+cudaError_t sub_multi(int64_t n, int nv, const double* V, int64_t ldv, const double* h, double* w, cudaStream_t st);
+// Modified Gram-Schmidt step: w -= (*hprev) vprev (if vprev), *hout = w^T vcur
+// (or w^T w if vcur is NULL); part: multidot_grid(n) doubles.
+cudaError_t mgs_step(int64_t n, double* w, const double* vprev, const double* hprev, const double* vcur, double* part,
+                     double* hout, cudaStream_t st);
+cudaError_t add_multi(int64_t n, int nv, const double* Z, int64_t ldz, const double* y, double* x, cudaStream_t st);
+// b = a * s (invert: a / s), s a device scalar.
+cudaError_t scale_to(int64_t n, const double* s, int invert, const double* a, double* b, cudaStream_t st);
+
 }  // namespace sdsl

@@ -30,7 +30,7 @@ class sdsl_options(C.Structure):
         ("rho", C.c_double), ("factor_prec", C.c_int), ("rtol", C.c_double), ("maxit", C.c_int64),
         ("restart", C.c_int), ("refactor_ratio", C.c_double), ("mem_space", C.c_int), ("stream", C.c_void_p),
         ("graph_iters", C.c_int), ("tune", C.c_int), ("profile", C.c_int), ("apply_prec", C.c_int),
-        ("flexible", C.c_int), ("solve_kernel", C.c_int), ("spmv_form", C.c_int),
+        ("flexible", C.c_int), ("solve_kernel", C.c_int), ("spmv_form", C.c_int), ("orthog", C.c_int),
     ]
 
 

@@ -1,0 +1,176 @@
+"""GPU parity of the bordered block-diagonal (BBD) path against the FP64 oracle:
+augmented matrix in BBD order, whole-matrix filter + correction, block level
+sets, per-block ILU(0), the border Schur complement, the preconditioner
+application and right-preconditioned GMRES(m)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2604_23979_gb300 import sdsl
+from paper_2604_23979_gb300 import workloads as W
+from tests.gpu_util import iters_close, rel, relres
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2604_23979_gb300 import build
+
+    build.build()
+    sdsl.load()
+
+
+def bits(a):
+    return np.ascontiguousarray(a, dtype=np.float64).view(np.int64)
+
+
+def kkt(seed=5, scale=0.002, nblocks=3, nlink=5, link_frac=0.3, mild=True):
+    p = W.config3(seed=seed, scale=scale, nblocks=nblocks, nlink=nlink, link_frac=link_frac)
+    if mild:  # well-conditioned variant: theta in [1e-2, 1e2], rho = 1e-2
+        rng = np.random.default_rng(0)
+        p.theta = np.exp(rng.uniform(np.log(1e-2), np.log(1e2), len(p.theta)))
+        p.rho = 1e-2
+    return p
+
+
+def oracle_bbd(p):
+    K, pos, kbp = oracle.augmented(p.A, p.theta, p.rho, p.row_block_ptr, p.col_block_ptr)
+    P = oracle.filter_correct(K, kbp, p.tau, p.delta, whole=True)
+    lo, up = oracle.levels(P, kbp)
+    F, alpha, st = oracle.ilu0(P, kbp)
+    SB = oracle.bbd_schur(P, F, kbp)
+    lu, ipiv, _ = oracle.dense_lu(SB)
+    return dict(K=K, kbp=kbp, P=P, lo=lo, up=up, F=F, alpha=alpha, SB=SB, lu=lu, ipiv=ipiv)
+
+
+def gpu_setup(p, **over):
+    o, keep = sdsl.options_for(p)
+    for k, v in over.items():
+        setattr(o, k, v)
+    h = sdsl.sdsl_setup(o, p.A.nrows, p.A.ncols, p.A.rowptr, p.A.col, p.A.val, p.theta)
+    return h, (o, keep)
+
+
+@pytest.mark.parametrize("seed,mild", [(5, True), (3, True), (7, False)])
+def test_bbd_structures_schur_apply(seed, mild):
+    p = kkt(seed=seed, mild=mild)
+    ref = oracle_bbd(p)
+    h, keep = gpu_setup(p)
+    try:
+        sdsl.sdsl_factor(h)
+        rp, ci, v = sdsl.sdsl_export_system(h)
+        assert np.array_equal(rp, ref["K"].rowptr) and np.array_equal(ci, ref["K"].col)
+        assert np.array_equal(bits(v), bits(ref["K"].val))
+        prp, pci, pv, fv, alpha = sdsl.sdsl_export_precond(h)
+        assert np.array_equal(prp, ref["P"].rowptr) and np.array_equal(pci, ref["P"].col)
+        assert np.array_equal(bits(pv), bits(ref["P"].val))
+        assert np.array_equal(alpha, ref["alpha"])
+        for which, lev in ((0, ref["lo"]), (1, ref["up"])):
+            nlev, lptr, rows = sdsl.sdsl_export_levels(h, which)
+            rn, rptr, rr = oracle.level_lists(ref["kbp"], lev)
+            assert np.array_equal(nlev, rn) and np.array_equal(lptr, rptr)
+            assert np.array_equal(rows[: len(rr)], rr)
+        # factor values on the in-block positions
+        row = np.repeat(np.arange(len(prp) - 1), np.diff(prp))
+        kbp = ref["kbp"]
+        blk = np.searchsorted(kbp, np.arange(len(prp) - 1), side="right") - 1
+        inb = (row < kbp[-1]) & (pci < kbp[-1]) & (blk[row] == blk[np.minimum(pci, kbp[-1] - 1)])
+        assert rel(fv[inb], ref["F"][inb]) <= 1e-11
+        nb = len(prp) - 1 - kbp[-1]
+        SB = np.zeros(nb * nb)
+        load = sdsl.load()
+        assert load.sdsl_export_schur(h, SB.ctypes.data) == 0
+        SB = SB.reshape(nb, nb)
+        assert rel(SB, ref["SB"]) <= 1e-10
+        # preconditioner application against the oracle's exact block-LU apply
+        r = np.random.default_rng(seed).standard_normal(len(prp) - 1)
+        z = np.zeros_like(r)
+        import torch
+        rd, zd = torch.from_numpy(r).cuda(), torch.zeros(len(r), dtype=torch.float64, device="cuda")
+        sdsl.sdsl_precond_apply(h, rd, zd)
+        torch.cuda.synchronize()
+        z = zd.cpu().numpy()
+        zr = oracle.bbd_apply(ref["P"], ref["F"], kbp, ref["lu"], ref["ipiv"], r)
+        assert rel(z, zr) <= 1e-8
+    finally:
+        sdsl.sdsl_free(h)
+
+
+@pytest.mark.parametrize("seed", [5, 3])
+def test_bbd_gmres_matches_oracle(seed):
+    p = kkt(seed=seed)
+    ref = oracle_bbd(p)
+    res = oracle.gmres(ref["K"], p.b, oracle.PRE_BBD, ref["P"], ref["F"], ref["kbp"], ref["lu"], ref["ipiv"],
+                       rtol=p.rtol, maxit=p.maxit, restart=p.restart)
+    assert res.status == 0
+    h, keep = gpu_setup(p)
+    try:
+        sdsl.sdsl_factor(h)
+        x = np.zeros(len(p.b))
+        st = sdsl.sdsl_solve(h, p.b, x)
+    finally:
+        sdsl.sdsl_free(h)
+    assert st.status == 0
+    assert relres(ref["K"], x, p.b) <= p.rtol
+    assert rel(x, res.x) <= 1e-6
+    # Restarted GMRES that needs dozens of cycles is chaotic: the oracle's own
+    # count moves by several per cent when b is perturbed at 1e-14.  The GPU
+    # count must lie within that spread (widened by 5 %).
+    counts = [res.iters]
+    for k in range(1, 5):
+        bk = p.b * (1 + 1e-14 * np.random.default_rng(k).standard_normal(len(p.b)))
+        counts.append(oracle.gmres(ref["K"], bk, oracle.PRE_BBD, ref["P"], ref["F"], ref["kbp"], ref["lu"],
+                                   ref["ipiv"], rtol=p.rtol, maxit=p.maxit, restart=p.restart).iters)
+    assert 0.95 * min(counts) <= st.iters <= 1.05 * max(counts), (st.iters, counts)
+
+
+def test_bbd_gmres_unrestarted_counts():
+    """Without restarts (restart >= iterations) GMRES is not chaotic: the GPU
+    count is within max(1, 5 %) of the oracle's."""
+    p = kkt(seed=5, scale=0.001, nblocks=2, nlink=3)
+    p.restart = 400
+    ref = oracle_bbd(p)
+    res = oracle.gmres(ref["K"], p.b, oracle.PRE_BBD, ref["P"], ref["F"], ref["kbp"], ref["lu"], ref["ipiv"],
+                       rtol=p.rtol, maxit=p.maxit, restart=p.restart)
+    assert res.status == 0 and res.iters < p.restart
+    h, keep = gpu_setup(p)
+    try:
+        sdsl.sdsl_factor(h)
+        x = np.zeros(len(p.b))
+        st = sdsl.sdsl_solve(h, p.b, x)
+    finally:
+        sdsl.sdsl_free(h)
+    assert st.status == 0 and relres(ref["K"], x, p.b) <= p.rtol
+    assert iters_close(st.iters, res.iters), (st.iters, res.iters)
+
+
+def test_bbd_exact_blocks_one_iteration():
+    """KKT blocks with a single nonzero per column of A_k are closed under
+    ILU(0) elimination; with tau = 0, delta = 0 the BBD preconditioner is
+    exact and GMRES stops after one Arnoldi step (as the oracle pin shows)."""
+    p = kkt(seed=11)
+    # one in-block nonzero per column: keep the first in-block entry of every column
+    A = p.A
+    rows = np.repeat(np.arange(A.nrows), np.diff(A.rowptr))
+    nint = p.row_block_ptr[-1]
+    keep = np.ones(A.nnz, bool)
+    seen = set()
+    for q in range(A.nnz):
+        if rows[q] < nint:
+            c = A.col[q]
+            if c in seen:
+                keep[q] = False
+            seen.add(c)
+    A.col, A.val = A.col[keep], A.val[keep]
+    A.rowptr = np.zeros(A.nrows + 1, np.int64)
+    np.cumsum(np.bincount(rows[keep], minlength=A.nrows), out=A.rowptr[1:])
+    p.tau, p.delta = 0.0, 0.0
+    h, keep2 = gpu_setup(p)
+    try:
+        sdsl.sdsl_factor(h)
+        x = np.zeros(len(p.b))
+        st = sdsl.sdsl_solve(h, p.b, x)
+    finally:
+        sdsl.sdsl_free(h)
+    assert st.status == 0 and st.iters == 1
