@@ -202,6 +202,42 @@ sdsl_status sdsl_spmv(sdsl_handle h, const double* x, double* y);
 /* z = M^{-1} r with the current preconditioner (device pointers, FP64). */
 sdsl_status sdsl_precond_apply(sdsl_handle h, const double* r, double* z);
 
+/* Largest n accepted by sdsl_normal_spmv_noalloc: its static scratch holds
+ * this many doubles (4 MiB) on every GPU where the library is loaded. */
+#define SDSL_NOALLOC_MAX_COLS (1 << 19)
+
+/* y = A (theta o (A^T x)) + rho x, the normal-equation product of
+ * sdsl_spmv without forming S and without allocating.  The paper has no
+ * counterpart: this entry point exists for callers that cannot call
+ * cudaMalloc -- a host program whose memory manager has reserved nearly all
+ * of HBM for its own pool, or a latency-bound serving loop where an
+ * allocation would synchronise the device -- and therefore cannot create a
+ * handle.
+ *   m, n       A is m x n; 0 <= n <= SDSL_NOALLOC_MAX_COLS, else SDSL_ERR_ARG
+ *              with nothing launched.
+ *   nnz        nonzeros of A (chooses lanes per row; must fit int32).
+ *   a_*        A in CSR: rowptr[m+1] (int64), col/val[nnz]; at_* A^T in CSR
+ *              (rowptr[n+1]).  Valid CSR with columns in range is the
+ *              caller's responsibility: it is not checked here.
+ *   theta[n], x[m], y[m]: device memory of the current device (or managed),
+ *              owned by the caller; y is overwritten, x and y may not alias.
+ *   stream     cudaStream_t (NULL: the legacy default stream); the call only
+ *              enqueues work and returns without synchronising.
+ * The intermediate theta o (A^T x) lives in a file-scope __device__ array
+ * of SDSL_NOALLOC_MAX_COLS doubles.  The first call on a device looks up that
+ * array's address with the device current (the library's module is loaded
+ * then if it was not yet), so make the first call on each device before any
+ * stream capture begins.  All calls share the array: calls whose kernels
+ * overlap on the GPU (different streams without ordering between them) race
+ * on it.  Each call writes every scratch entry it reads, so nothing carries
+ * over between calls.  Errors: SDSL_ERR_ARG for bad sizes, NULL pointers or
+ * pointers that are not device memory of the current device; SDSL_ERR_CUDA
+ * for a failed lookup or launch (sdsl_last_error() has the text). */
+sdsl_status sdsl_normal_spmv_noalloc(int64_t m, int64_t n, int64_t nnz, const int64_t* a_rowptr,
+                                     const int32_t* a_col, const double* a_val, const int64_t* at_rowptr,
+                                     const int32_t* at_col, const double* at_val, const double* theta, double rho,
+                                     const double* x, double* y, void* stream);
+
 /* Number of kernels this library has launched in the process so far (every
  * launch, including those inside CUDA graphs, counted once). */
 int64_t sdsl_kernel_launches(void);

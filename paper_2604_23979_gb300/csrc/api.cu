@@ -19,6 +19,7 @@ namespace sdsl {
 static std::atomic<long long> g_launches{0};
 void count_launch(long long k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 long long launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
+sdsl_status report_error(sdsl_status s, const std::string& msg);
 }  // namespace sdsl
 
 using namespace sdsl;
@@ -26,6 +27,16 @@ using namespace sdsl;
 namespace {
 
 thread_local std::string g_err;
+
+}  // namespace
+
+// Error reporting for entry points defined in other translation units.
+sdsl_status sdsl::report_error(sdsl_status s, const std::string& msg) {
+  g_err = msg;
+  return s;
+}
+
+namespace {
 
 sdsl_status fail(sdsl_status s, const std::string& msg) {
   g_err = msg;

@@ -200,6 +200,10 @@ struct SpmvPlan {
 cudaError_t spmv(const SpmvPlan& A, const double* x, double* y, cudaStream_t st);
 cudaError_t time_spmv(const SpmvPlan& A, const double* x, double* y, int reps, float* ms, cudaStream_t st);
 // q = A p, partial p^T q; last CTA: alpha = rho/pq, iters++.
+// q = A (theta o (A^T p)) + rho p through the scratch A.u (n entries); with
+// pcg = 1 also the partial p^T q and, in the last CTA, alpha = rho/pq, iters++.
+cudaError_t factored_product(const SpmvPlan& A, const double* p, double* q, double* part, PcgState* s, int pcg,
+                             cudaStream_t st);
 cudaError_t pcg_spmv(const SpmvPlan& A, const double* p, double* q, double* part, PcgState* s, cudaStream_t st);
 // x += alpha p, r -= alpha q, z = M^{-1} r per block; last CTA: convergence, beta.
 // part: 3 sections of nblocks partial sums [||r||^2 | r^T z | z^T q].

@@ -89,6 +89,8 @@ def load():
     L.sdsl_export_schur.argtypes = [H, _VP]
     L.sdsl_spmv.argtypes = [H, _VP, _VP]
     L.sdsl_precond_apply.argtypes = [H, _VP, _VP]
+    L.sdsl_normal_spmv_noalloc.argtypes = [_I64, _I64, _I64, _VP, _VP, _VP, _VP, _VP, _VP, _VP, C.c_double,
+                                           _VP, _VP, _VP]
     L.sdsl_status_str.argtypes = [C.c_int]
     L.sdsl_status_str.restype = C.c_char_p
     L.sdsl_kernel_launches.argtypes = []
@@ -97,7 +99,7 @@ def load():
     L.sdsl_last_error.restype = C.c_char_p
     for f in ("sdsl_setup", "sdsl_factor", "sdsl_solve", "sdsl_update_diag", "sdsl_free", "sdsl_get_stats",
               "sdsl_get_info", "sdsl_export_system", "sdsl_export_precond", "sdsl_export_levels",
-              "sdsl_export_schur", "sdsl_spmv", "sdsl_precond_apply"):
+              "sdsl_export_schur", "sdsl_spmv", "sdsl_precond_apply", "sdsl_normal_spmv_noalloc"):
         getattr(L, f).restype = C.c_int
     _lib = L
     return L
@@ -231,6 +233,18 @@ def sdsl_spmv(h, x, y):
 
 def sdsl_precond_apply(h, r, z):
     return _check(load().sdsl_precond_apply(h, _ptr(r)[0], _ptr(z)[0]))
+
+
+NOALLOC_MAX_COLS = 1 << 19
+
+
+def sdsl_normal_spmv_noalloc(m, n, nnz, a_rowptr, a_col, a_val, at_rowptr, at_col, at_val, theta, rho, x, y,
+                             stream=0):
+    """y = A (theta o (A^T x)) + rho x without any device allocation (all
+    arrays are device tensors of the current device; stream is a raw
+    cudaStream_t handle, 0 for the legacy default stream)."""
+    ptrs = [_ptr(a)[0] for a in (a_rowptr, a_col, a_val, at_rowptr, at_col, at_val, theta, x, y)]
+    return _check(load().sdsl_normal_spmv_noalloc(m, n, nnz, *ptrs[:7], float(rho), ptrs[7], ptrs[8], stream or None))
 
 
 def options_for(prob, method=BJ_PCG, factor_prec=64, graph_iters=16, stream=None):
