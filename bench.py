@@ -46,6 +46,10 @@ def parse():
     ap.add_argument("--solve-kernel", type=int, default=0, help="block solves: 0 auto, 1 level-sync, 2 flag-free, "
                                                                  "3 TMA-staged")
     ap.add_argument("--apply-prec", type=int, default=0, choices=[0, 32, 64])
+    ap.add_argument("--sweep-warps", type=int, default=0, help="warps per block in the staged sweeps (0 auto)")
+    ap.add_argument("--backoff-ns", type=int, default=-1, help="poll backoff of the staged sweeps (-1 auto)")
+    ap.add_argument("--lane-entries", type=int, default=0, help="entries per lane of the sweep tiles (0 auto)")
+    ap.add_argument("--tune", type=int, default=0, help="1: autotune the product kernels' lane widths at factor time")
     return ap.parse_args()
 
 
@@ -209,6 +213,10 @@ def run_ours(args, ws, rank, local):
         o.profile = 1 if profile else 0
         o.solve_kernel = args.solve_kernel
         o.apply_prec = args.apply_prec if prec == 32 else 0
+        o.sweep_warps = args.sweep_warps
+        o.sweep_backoff_ns = args.backoff_ns
+        o.sweep_lane_entries = args.lane_entries
+        o.tune = args.tune
         arrs = arrays if arrays is not None else (d_rp, d_ci, d_v, d_th)
         h = sdsl.sdsl_setup(o, A.nrows, A.ncols, *arrs)
         try:
@@ -283,6 +291,7 @@ def run_ours(args, ws, rank, local):
                       "solve": round(last.ms_solve, 3)},
         "shifted_blocks": int(last.shifted_blocks),
         "levels_max": int(last.max_levels),
+        "product_lanes": [int(last_setup.product_lanes[0]), int(last_setup.product_lanes[1])],
         "krylov_iter_bytes": last.bytes_per_iter,
         "krylov_iter_gbs": round(last.bytes_per_iter * last.iters / (last.ms_solve * 1e-3) / 1e9, 1),
         "gpu_launches": int(launches),

@@ -86,6 +86,10 @@ typedef struct {
   int spmv_form;                 /* PCG product S p (normal form): 0 auto (fewer HBM bytes), 1 explicit
                                     CSR of S, 2 factored A (theta o (A^T p)) + rho p */
   int orthog;                    /* GMRES orthogonalization: 0 modified Gram-Schmidt, 1 classical twice */
+  int sweep_warps;               /* warps per block that run the staged triangular sweeps: 0 auto, 1..16 */
+  int sweep_backoff_ns;          /* sleep between unsuccessful readiness polls in those sweeps: -1 auto, 0..1000 */
+  int sweep_lane_entries;        /* tile shape of those sweeps: a row gets the fewest lanes (a power of two)
+                                    that leave at most this many of its entries per lane; 0 auto, 1..64 */
 } sdsl_options;
 
 typedef struct {
@@ -111,7 +115,9 @@ typedef struct {
   double kernel_bytes[4]; /* algorithmic HBM bytes per launch of the kernels above (model) */
   int64_t spmv_lanes;     /* lanes per row of the SpMV in use */
   int64_t solve_lanes;    /* lanes per row of the block triangular solves in use */
-  int64_t tuned_spmv_lanes; /* choice of the autotuner (0 if it did not run) */
+  int64_t tuned_spmv_lanes; /* explicit-S SpMV lanes chosen by the autotuner (0 if it did not run) */
+  int64_t product_lanes[2]; /* factored normal-equation product: lanes per row of A^T p and of A u
+                               (0 when the explicit S is used) */
 } sdsl_stats;
 
 typedef struct {

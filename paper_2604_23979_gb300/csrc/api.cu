@@ -346,6 +346,24 @@ int lanes_for(double avg) {  // about 12+ nonzeros per lane (FP64 instruction ec
   return lanes;
 }
 
+// Grids of the product kernels: at least 64 rows per CTA, at most one full
+// wave (resident CTAs per SM x SMs, capped at 8 per SM -- the partial-sum
+// arrays hold that many), so no CTA waits for a second wave.
+int one_wave(int64_t rows, int sms, int per_sm) {
+  const int64_t g = std::min<int64_t>((rows + 63) / 64, (int64_t)sms * std::min(per_sm, 8));
+  return (int)std::max<int64_t>(1, g);
+}
+
+void set_product_grids(sdsl_handle h) {
+  SpmvPlan& A = h->A;
+  if (A.factored) {
+    A.at_grid = one_wave(h->n, h->sms, product_occupancy(2, A.at_lanes));
+    A.grid = one_wave(h->N, h->sms, product_occupancy(3, A.a_lanes));
+  } else {
+    A.grid = one_wave(h->N, h->sms, product_occupancy(1, A.lanes));
+  }
+}
+
 void choose_spmv_plan(sdsl_handle h) {
   const double avg = h->N > 0 ? (double)h->s_nnz / (double)h->N : 1.0;
   // Normal equations: the PCG product S p can use the factored form
@@ -365,34 +383,49 @@ void choose_spmv_plan(sdsl_handle h) {
     h->A.u = h->u;
     h->A.a_lanes = lanes_for(h->m > 0 ? (double)h->a_nnz / (double)h->m : 1.0);
     h->A.at_lanes = lanes_for(h->n > 0 ? (double)h->a_nnz / (double)h->n : 1.0);
-    int64_t g2 = (h->n + 63) / 64;
-    h->A.at_grid = (int)std::max<int64_t>(1, std::min<int64_t>(g2, (int64_t)h->sms * 8));
   }
   h->A.n = h->N;
   h->A.rp = h->s_rp;
   h->A.ci = h->s_ci;
   h->A.v = h->s_v;
   h->A.lanes = lanes_for(avg);
-  const int64_t rows_per_cta_min = 64;
-  int64_t g = (h->N + rows_per_cta_min - 1) / rows_per_cta_min;
-  g = std::max<int64_t>(1, std::min<int64_t>(g, (int64_t)h->sms * 8));
-  h->A.grid = (int)g;
+  set_product_grids(h);
 }
 
 // Autotuner: time the SpMV at every lane width on the handle's own matrix
 // and keep the fastest (ties keep the smaller width).
 sdsl_status tune_spmv(sdsl_handle h) {
+  TRY_CUDA(cudaMemsetAsync(h->p, 0, sizeof(double) * (size_t)h->N, h->st));
+  if (h->A.factored) {
+    // the two halves of the factored product are independent choices
+    float best_at = 1e30f, best_a = 1e30f;
+    int l_at = h->A.at_lanes, l_a = h->A.a_lanes;
+    for (int l = 1; l <= 32; l <<= 1) {
+      h->A.at_lanes = l;
+      h->A.a_lanes = l;
+      set_product_grids(h);
+      float ms_at = 0.f, ms_a = 0.f;
+      TRY_CUDA(time_factored(h->A, h->p, h->q, 3, &ms_at, &ms_a, h->st));
+      if (ms_at < best_at * 0.98f) { best_at = ms_at; l_at = l; }
+      if (ms_a < best_a * 0.98f) { best_a = ms_a; l_a = l; }
+    }
+    h->A.at_lanes = l_at;
+    h->A.a_lanes = l_a;
+    set_product_grids(h);
+    return SDSL_OK;
+  }
   float best = 1e30f;
   int best_l = h->A.lanes;
   SpmvPlan P = h->A;
-  TRY_CUDA(cudaMemsetAsync(h->p, 0, sizeof(double) * (size_t)h->N, h->st));
   for (int l = 1; l <= 32; l <<= 1) {
     P.lanes = l;
+    P.grid = one_wave(h->N, h->sms, product_occupancy(0, l));
     float ms = 0.f;
     TRY_CUDA(time_spmv(P, h->p, h->q, 3, &ms, h->st));
     if (ms < best * 0.98f) { best = ms; best_l = l; }
   }
   h->A.lanes = best_l;
+  set_product_grids(h);
   h->stats.tuned_spmv_lanes = best_l;
   return SDSL_OK;
 }
@@ -670,10 +703,13 @@ sdsl_status gmres_solve(sdsl_handle h) {
   return fail(result, "GMRES reached maxit before the tolerance");
 }
 
-// Variable-width tile streams of the TMA-staged sweeps (both directions).
+// Variable-width tile streams of the staged sweeps (both directions).
 // Rows of one level are packed into 32-lane tiles, each row with V lanes
-// (the smallest power of two with 4V >= its entry count, at most 32), in
-// order of decreasing V so that groups sit at V-aligned lane offsets.
+// (the smallest power of two with E*V >= its entry count, at most 32, E the
+// entries-per-lane target), in order of decreasing V so that groups sit at
+// V-aligned lane offsets.  A tile is closed early when it would outgrow the
+// ring slot.  The ring depth (4, 3 or 2 slots per warp) is the deepest whose
+// slots hold the largest tile within the shared-memory budget.
 // Returns SDSL_OK with *ok = false if the staging does not fit in shared
 // memory (the caller then uses another solve kernel).
 sdsl_status build_vtiles(sdsl_handle h, bool f32, int apply, bool* ok) {
@@ -682,89 +718,125 @@ sdsl_status build_vtiles(sdsl_handle h, bool f32, int apply, bool* ok) {
   const int64_t nrows = h->h_bp[nb];
   const int tsz = f32 ? 4 : 8;
   const int tc = apply == 32 ? 4 : 8;
+  const int E = h->opt.sweep_lane_entries > 0 ? h->opt.sweep_lane_entries : 16;
+  const int kWarps = 16;
+  *ok = false;
+  int64_t maxb = 0;
+  for (int64_t k = 0; k < nb; ++k) maxb = std::max(maxb, h->h_bp[k + 1] - h->h_bp[k]);
+  if (maxb > 65535) return SDSL_OK;  // block-local rows and columns are 16-bit
   struct Plan {
     std::vector<int32_t> trp{0}, rows;
     std::vector<int8_t> logv;
     std::vector<int64_t> toff{0}, tile_ptr;
     int64_t max_bytes = 0;
   } plan[2];
-  std::vector<int32_t> lptr, lrows;
-  std::vector<int64_t> lens(nrows);
+  std::vector<int32_t> lptr[2], lrows[2];
+  std::vector<int64_t> lens[2];
   int64_t* d_len;
   Arena tmp;
   tmp.st = h->st;
+  struct Release {
+    Arena& a;
+    ~Release() { a.release(); }
+  } release_tmp{tmp};
   TRY(tmp.get(&d_len, nrows + 1));
   for (int dir = 0; dir < 2; ++dir) {
     const int64_t tot = dir == 0 ? h->tot_lo : h->tot_up;
-    const std::vector<int32_t>& nl = dir == 0 ? h->h_nlev_lo : h->h_nlev_up;
     const int32_t* d_rows = dir == 0 ? h->lev_rows_lo : h->lev_rows_up;
-    lptr.resize(tot + 1);
-    lrows.resize(nrows);
-    TRY(to_host(h, lptr.data(), dir == 0 ? h->lev_ptr_lo : h->lev_ptr_up, tot + 1));
-    TRY(to_host(h, lrows.data(), d_rows, nrows));
+    lptr[dir].resize(tot + 1);
+    lrows[dir].resize(nrows);
+    lens[dir].resize(nrows);
+    TRY(to_host(h, lptr[dir].data(), dir == 0 ? h->lev_ptr_lo : h->lev_ptr_up, tot + 1));
+    TRY(to_host(h, lrows[dir].data(), d_rows, nrows));
     TRY_CUDA(pack_count(dir, nrows, h->row_block, h->d_bp, h->p_rp, h->p_ci, h->p_diag, d_rows, d_len, h->st));
-    TRY(to_host(h, lens.data(), d_len, nrows));  // entry count of level position q
+    TRY(to_host(h, lens[dir].data(), d_len, nrows));  // entry count of level position q
     TRY(sync(h, "tile plan"));
-    Plan& P = plan[dir];
-    P.tile_ptr.assign(nb + 1, 0);
-    std::vector<std::pair<int, int32_t>> lev;  // (-logV, position)
-    int64_t L = 0, tiles = 0;
-    for (int64_t k = 0; k < nb; ++k) {
-      P.tile_ptr[k] = tiles;
-      for (int32_t l = 0; l < nl[k]; ++l, ++L) {
-        lev.clear();
-        for (int32_t q = lptr[L]; q < lptr[L + 1]; ++q) {
-          int lv = 0;
-          while (lv < 5 && (4 << lv) < lens[q]) ++lv;
-          lev.emplace_back(-lv, q);
-        }
-        std::stable_sort(lev.begin(), lev.end(),
-                         [](const std::pair<int, int32_t>& x, const std::pair<int, int32_t>& y) { return x.first < y.first; });
-        int used = 32, nr = 0;
-        int64_t ne = 0;
-        auto close = [&]() {
-          if (nr == 0) return;
-          const int64_t bytes = 16 + 256 + ((nr * tsz + 15) & ~15) + ((4 * ne + 15) & ~15) + ((ne * tsz + 15) & ~15);
-          P.toff.push_back(P.toff.back() + bytes);
-          P.trp.push_back((int32_t)P.rows.size());
-          P.max_bytes = std::max(P.max_bytes, bytes);
-          ++tiles;
-          nr = 0;
-          ne = 0;
-        };
-        for (const auto& e : lev) {
-          const int V = 1 << (-e.first);
-          if (used + V > 32) { close(); used = 0; }
-          P.rows.push_back(lrows[e.second]);
-          P.logv.push_back((int8_t)(-e.first));
-          used += V;
-          ++nr;
-          ne += lens[e.second];
-        }
-        close();
-        used = 32;
-      }
-    }
-    P.tile_ptr[nb] = tiles;
+    for (int64_t q = 0; q < nrows; ++q)
+      if (lens[dir][q] > 255 * 32) return SDSL_OK;  // a lane's entry count is 8-bit
   }
-  tmp.release();
-  // ring geometry within the shared-memory budget
-  int64_t mt = 0;
-  for (int64_t k = 0; k < nb; ++k)
-    mt = std::max<int64_t>(mt, (plan[0].tile_ptr[k + 1] - plan[0].tile_ptr[k]) +
-                                   (plan[1].tile_ptr[k + 1] - plan[1].tile_ptr[k]));
-  int64_t maxb = 0;
-  for (int64_t k = 0; k < nb; ++k) maxb = std::max(maxb, h->h_bp[k + 1] - h->h_bp[k]);
+  auto tile_bytes = [&](int64_t nr, int64_t ne) {
+    return 16 + 256 + ((nr * tsz + 15) & ~15) + ((2 * ne + 15) & ~15) + ((ne * tsz + 15) & ~15);
+  };
+  // Pack every level of every block into tiles no larger than cap bytes
+  // (a single row larger than cap gets a tile of its own).
+  auto make_plan = [&](int64_t cap) {
+    for (int dir = 0; dir < 2; ++dir) {
+      const std::vector<int32_t>& nl = dir == 0 ? h->h_nlev_lo : h->h_nlev_up;
+      Plan& P = plan[dir];
+      P = Plan{};
+      P.tile_ptr.assign(nb + 1, 0);
+      std::vector<std::pair<int, int32_t>> lev;  // (-logV, position)
+      int64_t L = 0, tiles = 0;
+      for (int64_t k = 0; k < nb; ++k) {
+        P.tile_ptr[k] = tiles;
+        for (int32_t l = 0; l < nl[k]; ++l, ++L) {
+          lev.clear();
+          for (int32_t q = lptr[dir][L]; q < lptr[dir][L + 1]; ++q) {
+            int lv = 0;
+            while (lv < 5 && ((int64_t)E << lv) < lens[dir][q]) ++lv;
+            lev.emplace_back(-lv, q);
+          }
+          std::stable_sort(lev.begin(), lev.end(), [](const std::pair<int, int32_t>& x,
+                                                      const std::pair<int, int32_t>& y) { return x.first < y.first; });
+          int used = 0, nr = 0;
+          int64_t ne = 0;
+          auto close = [&]() {
+            if (nr == 0) return;
+            const int64_t bytes = tile_bytes(nr, ne);
+            P.toff.push_back(P.toff.back() + bytes);
+            P.trp.push_back((int32_t)P.rows.size());
+            P.max_bytes = std::max(P.max_bytes, bytes);
+            ++tiles;
+            nr = 0;
+            ne = 0;
+            used = 0;
+          };
+          for (const auto& e : lev) {
+            const int V = 1 << (-e.first);
+            const int64_t len = lens[dir][e.second];
+            if (used + V > 32 || (nr > 0 && tile_bytes(nr + 1, ne + len) > cap)) close();
+            P.rows.push_back(lrows[dir][e.second]);
+            P.logv.push_back((int8_t)(-e.first));
+            used += V;
+            ++nr;
+            ne += len;
+          }
+          close();
+        }
+      }
+      P.tile_ptr[nb] = tiles;
+    }
+  };
+  auto max_tiles = [&]() {
+    int64_t mt = 0;
+    for (int64_t k = 0; k < nb; ++k)
+      mt = std::max<int64_t>(mt, (plan[0].tile_ptr[k + 1] - plan[0].tile_ptr[k]) +
+                                     (plan[1].tile_ptr[k + 1] - plan[1].tile_ptr[k]));
+    return mt;
+  };
   const size_t budget = (size_t)225 * 1024;
-  const size_t fixed = tma_smem_bytes(maxb, tc, 16, 0, 0) + (size_t)(mt + 2) * 8;
-  const int64_t big = std::max(plan[0].max_bytes, plan[1].max_bytes);
-  const int slots = 4;  // ring depth of the staged sweeps (copies of three tiles ahead in flight)
-  int slot = (int)std::min<int64_t>(((big + 255) / 256) * 256, 3072);
-  while (slot >= 512 && fixed + (size_t)16 * slots * ((size_t)slot + 8) > budget) slot -= 256;
-  if (slot < 512 || maxb > 65535) { *ok = false; return SDSL_OK; }
+  make_plan(INT64_MAX);
+  int64_t mt = max_tiles();
+  const int64_t big = ((std::max(plan[0].max_bytes, plan[1].max_bytes) + 255) / 256) * 256;
+  int slots = 0, slot = 0;
+  for (int sl = 4; sl >= 2 && slots == 0; --sl)
+    if (staged_smem_bytes(maxb, tc, kWarps, (int)big, sl, mt) <= budget) { slots = sl; slot = (int)big; }
+  if (slots == 0) {
+    // the largest tiles do not fit two slots: cap the tiles at the largest
+    // slot that does (the cap raises the tile count, so re-check)
+    slots = 2;
+    const size_t fixed = staged_smem_bytes(maxb, tc, kWarps, 0, 0, 2 * mt);
+    if (fixed >= budget) return SDSL_OK;
+    slot = (int)std::min<int64_t>(((budget - fixed) / ((size_t)kWarps * slots)) & ~(size_t)255, 16384);
+    if (slot < 1024) return SDSL_OK;
+    make_plan(slot);
+    mt = max_tiles();
+    if (staged_smem_bytes(maxb, tc, kWarps, slot, slots, mt) > budget) return SDSL_OK;
+  }
   M.slot_bytes = slot;
   M.slots = slots;
   M.max_tiles = mt;
+  M.kreg = E <= 8 ? 8 : 16;
   for (int dir = 0; dir < 2; ++dir) {
     Plan& P = plan[dir];
     const int64_t ntiles = (int64_t)P.trp.size() - 1;
@@ -981,11 +1053,12 @@ sdsl_status factor_impl(sdsl_handle h) {
     }
     M.max_tiles = mt;
   }
-  const bool fits_tma = tma_smem_bytes(maxb, apply == 32 ? 4 : 8, 16, 1024, 2) +
-                        (size_t)(M.max_tiles + 2) * 8 <= (size_t)225 * 1024;
+  const bool fits_tma = staged_smem_bytes(maxb, apply == 32 ? 4 : 8, 16, 1024, 2, M.max_tiles) <= (size_t)225 * 1024;
   if ((h->opt.solve_kernel == 2 && !fits) || (h->opt.solve_kernel == 3 && !fits_tma))
     return fail(SDSL_ERR_ARG, "flag-synchronised solves need the largest block to fit in shared memory");
   M.tma = (h->method == SDSL_BJ_PCG && (h->opt.solve_kernel == 3 || (h->opt.solve_kernel == 0 && fits_tma))) ? 1 : 0;
+  M.sweep_warps = h->opt.sweep_warps > 0 ? h->opt.sweep_warps : 12;
+  M.backoff_ns = h->opt.sweep_backoff_ns >= 0 ? h->opt.sweep_backoff_ns : 20;
   if (M.tma) {
     bool ok = false;
     TRY(build_vtiles(h, f32, apply, &ok));
@@ -1057,6 +1130,8 @@ sdsl_status factor_impl(sdsl_handle h) {
   h->stats.nnz_precond = h->p_nnz;
   h->stats.nnz_factor = h->method == SDSL_BBD_GMRES ? h->p_nnz : (h->p_nnz + N) / 2;
   h->stats.spmv_lanes = h->A.lanes;
+  h->stats.product_lanes[0] = h->A.factored ? h->A.at_lanes : 0;
+  h->stats.product_lanes[1] = h->A.factored ? h->A.a_lanes : 0;
   h->stats.solve_lanes = h->M.lanes;
   h->stats.levels_lower = h->tot_lo;
   h->stats.levels_upper = h->tot_up;
@@ -1184,6 +1259,9 @@ void sdsl_default_options(sdsl_options* o) {
   o->apply_prec = 0;
   o->flexible = -1;
   o->orthog = 0;
+  o->sweep_warps = 0;
+  o->sweep_backoff_ns = -1;
+  o->sweep_lane_entries = 0;
 }
 
 const char* sdsl_status_str(sdsl_status s) {
@@ -1235,6 +1313,11 @@ sdsl_status sdsl_setup(const sdsl_options* opt, int64_t m, int64_t n, const int6
   if (opt->solve_kernel < 0 || opt->solve_kernel > 3) return fail(SDSL_ERR_ARG, "solve_kernel must be 0..3");
   if (opt->spmv_form < 0 || opt->spmv_form > 2) return fail(SDSL_ERR_ARG, "spmv_form must be 0, 1 or 2");
   if (opt->orthog < 0 || opt->orthog > 1) return fail(SDSL_ERR_ARG, "orthog must be 0 or 1");
+  if (opt->sweep_warps < 0 || opt->sweep_warps > 16) return fail(SDSL_ERR_ARG, "sweep_warps must be in 0..16");
+  if (opt->sweep_backoff_ns < -1 || opt->sweep_backoff_ns > 1000)
+    return fail(SDSL_ERR_ARG, "sweep_backoff_ns must be in -1..1000");
+  if (opt->sweep_lane_entries < 0 || opt->sweep_lane_entries > 64)
+    return fail(SDSL_ERR_ARG, "sweep_lane_entries must be in 0..64");
   if (opt->apply_prec != 0 && opt->apply_prec != 64 && opt->apply_prec != 32)
     return fail(SDSL_ERR_ARG, "apply_prec must be 0, 32 or 64");
   if (opt->factor_prec == 64 && opt->apply_prec == 32)

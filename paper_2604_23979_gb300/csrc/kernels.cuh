@@ -86,7 +86,10 @@ cudaError_t vt_fill(int dir, int64_t ntiles, const int32_t* tile_rows_ptr, const
                     const int32_t* pci, const int64_t* pdiag, const double* F, const double* dinv, int prec,
                     const int64_t* toff, unsigned char* stream, cudaStream_t st);
 // Dynamic shared memory of the TMA-staged solve.
-size_t tma_smem_bytes(int64_t max_block, size_t tc_size, int warps, int slot_bytes, int slots);
+// Dynamic shared memory of the staged solve kernel (sweep.cu): y in both
+// directions, the warps' tile rings and the block's staged tile offsets.
+size_t staged_smem_bytes(int64_t max_block, size_t tc_size, int warps, int slot_bytes, int slots, int64_t max_tiles);
+
 
 // ---- krylov.cu: SpMV, PCG iteration kernels, residuals
 struct PcgState {
@@ -153,14 +156,17 @@ struct TriSolve {  // block triangular factors on the layout of P
   const unsigned char* bwd_stream;
   const int64_t* bwd_toff;
   const int64_t* bwd_tile;
-  int tma;              // 1: TMA-staged tiles (bulk copies into a per-warp shared-memory ring)
+  int tma;              // 1: staged level tiles (cp.async copies into a per-warp shared-memory ring)
   int slot_bytes;       // ring slot size; larger tiles are read from global memory directly
+  int kreg;             // entries per lane and gather round of the staged solves (8 or 16)
   int64_t max_tiles;    // max over blocks of (forward tiles + backward tiles): staged tile offsets
   int slots;            // ring slots per warp
   int sync_free;        // 1: packed flag-synchronised solves (block fits in shared memory)
   int apply_prec;       // arithmetic of the apply: 64 or 32
   int flexible;         // 1: beta = -alpha z_new^T q / rho (robust to an inexact FP32 apply)
   int threads;          // CTA size of the solve kernel
+  int sweep_warps;      // warps of the staged solve that take tiles (the rest only stage and reduce)
+  int backoff_ns;       // sleep between unsuccessful readiness polls
 };
 
 // Packed level-ordered triangle of one direction (dir 0 = strict lower in
@@ -204,11 +210,17 @@ cudaError_t time_spmv(const SpmvPlan& A, const double* x, double* y, int reps, f
 // pcg = 1 also the partial p^T q and, in the last CTA, alpha = rho/pq, iters++.
 cudaError_t factored_product(const SpmvPlan& A, const double* p, double* q, double* part, PcgState* s, int pcg,
                              cudaStream_t st);
+int product_occupancy(int kind, int lanes);
+cudaError_t time_factored(const SpmvPlan& A, const double* p, double* q, int reps, float* ms_at, float* ms_a,
+                          cudaStream_t st);
 cudaError_t pcg_spmv(const SpmvPlan& A, const double* p, double* q, double* part, PcgState* s, cudaStream_t st);
 // x += alpha p, r -= alpha q, z = M^{-1} r per block; last CTA: convergence, beta.
 // part: 3 sections of nblocks partial sums [||r||^2 | r^T z | z^T q].
 cudaError_t pcg_update_precond(const TriSolve& M, const double* p, const double* q, double* x, double* r, double* z,
                                double* part, PcgState* s, cudaStream_t st);
+// PCG update + staged Block-Jacobi apply (solve_kernel 3); modes as pcg_update_precond.
+cudaError_t update_staged(const TriSolve& M, const double* p, const double* q, double* x, double* r, double* z,
+                          double* pp, double* part, PcgState* s, int mode, cudaStream_t st);
 // Dynamic shared memory of the flag-synchronised solve for a block size.
 size_t sf_smem_bytes(int64_t max_block, size_t tc_size);
 // p = z + beta p

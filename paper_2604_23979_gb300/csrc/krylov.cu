@@ -14,6 +14,7 @@
 // on-device reduction; the ghost exchange disappears (x is resident).
 #include "common.cuh"
 #include "kernels.cuh"
+#include "pcg_common.cuh"
 
 namespace sdsl {
 
@@ -21,23 +22,6 @@ namespace {
 
 constexpr int kThreads = 256;
 
-// Deterministic sum of a[0, n) by one warp (lane-strided, then butterfly).
-__device__ __forceinline__ double warp_fixed_sum(const double* a, int n) {
-  double t = 0.0;
-  for (int i = lane_id(); i < n; i += 32) t += a[i];
-  return warp_sum(t);
-}
-
-// Returns true in every thread of the last CTA to arrive.
-__device__ __forceinline__ bool last_block(unsigned int* ticket) {
-  __shared__ int amlast;
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) amlast = atomicAdd(ticket, 1u) == gridDim.x - 1;
-  __syncthreads();
-  if (amlast) __threadfence();
-  return amlast;
-}
 
 // Row i of A times x by the V lanes of a group.  Every lane of the warp must
 // call it (the group shuffle uses the full mask); lanes of a group without a
@@ -292,46 +276,6 @@ __device__ __forceinline__ void block_solve(const TriSolve& M, const T* __restri
   }
 }
 
-// Shared epilogue of the update kernels: z, the block partials of
-// ||r||^2, r^T z and z^T q, and (last CTA) the scalars of the next launch.
-// part holds three sections of nblocks entries: [rr | rz | zq].
-__device__ __forceinline__ void update_epilogue(const TriSolve& M, double rrb, double rzb, double zqb,
-                                                double* __restrict__ part, PcgState* __restrict__ s, int mode,
-                                                bool timed_out) {
-  const int b = blockIdx.x;
-  const int nb = (int)M.nblocks;
-  if (threadIdx.x == 0) {
-    part[b] = rrb;
-    part[nb + b] = rzb;
-    part[2 * nb + b] = zqb;
-    if (timed_out) s->err = 1;
-  }
-  if (mode == 2) return;
-  if (last_block(&s->ticket[2])) {
-    if (threadIdx.x < 32) {
-      const double rrt = warp_fixed_sum(part, nb);
-      const double rzt = warp_fixed_sum(part + nb, nb);
-      const double zqt = warp_fixed_sum(part + 2 * nb, nb);
-      if (threadIdx.x == 0) {
-        s->rr = rrt;
-        s->rz_new = rzt;
-        s->zq = zqt;
-        if (mode == 0) {
-          if (rrt <= s->tol2) s->done = 1;
-          else if (s->iters >= s->maxit) s->done = 2;
-          else if (!isfinite(rzt) || !isfinite(rrt)) s->done = 3;
-          // standard beta = rho_new / rho; flexible (Polak-Ribiere) beta =
-          // z_new^T (r_new - r_old) / rho = -alpha z_new^T q / rho
-          s->beta = M.flexible ? -s->alpha * zqt / s->rho : rzt / s->rho;
-          s->rho = rzt;
-        } else {
-          s->rho = rzt;
-        }
-        s->ticket[2] = 0;
-      }
-    }
-  }
-}
 
 // Level-synchronous variant (any block size): y staged in shared memory if
 // the largest block fits, else in a global scratch vector.
@@ -400,11 +344,6 @@ __device__ __forceinline__ T group_sum_own(T v) {
   return v;
 }
 
-constexpr int kSpinLimit = 1 << 26;
-#ifndef SDSL_BACKOFF_NS
-#define SDSL_BACKOFF_NS 20
-#endif
-constexpr unsigned kBackoffNs = SDSL_BACKOFF_NS;  // ~1 s of polling: a wait that long is a bug, reported as TIMEOUT
 constexpr int kPre = 4;              // entries per lane prefetched one position ahead
 
 template <typename TS, typename TC>
@@ -467,15 +406,6 @@ __device__ __forceinline__ void load_pos(RowPre<TS, TC>& R, const int64_t* __res
   }
 }
 
-// "Not yet computed" marker of the flag-free sweeps: a signalling-NaN bit
-// pattern.  Arithmetic never produces a signalling NaN (results are finite
-// or the canonical quiet NaN), so a solved value can never look unsolved,
-// and an aligned 32/64-bit shared-memory store publishes value and readiness
-// at once -- no separate flag and no memory fence on the critical path.
-__device__ __forceinline__ float sentinel(float) { return __uint_as_float(0x7FA5A5A5u); }
-__device__ __forceinline__ double sentinel(double) { return __longlong_as_double(0x7FF4A5A5A5A5A5A5ll); }
-__device__ __forceinline__ bool is_sentinel(float v) { return __float_as_uint(v) == 0x7FA5A5A5u; }
-__device__ __forceinline__ bool is_sentinel(double v) { return __double_as_longlong(v) == 0x7FF4A5A5A5A5A5A5ll; }
 
 // Read y[j] once it has been solved (bounded wait).
 // The wait backs off with a short sleep between polls: dozens of warps
@@ -634,255 +564,6 @@ inline unsigned grid_for(int64_t work, int per_block, int cap = 152 * 16) {
   return (unsigned)g;
 }
 
-// ---------------------------------------------------------------- TMA-staged solves
-
-constexpr int kTmaWarps = 16;
-__device__ __forceinline__ unsigned smem_u32(const void* p) {
-  return static_cast<unsigned>(__cvta_generic_to_shared(p));
-}
-constexpr int kSlotsCp = 4;   // ring slots per warp: cp.async copies of the next 3 tiles in flight
-
-__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
-  unsigned ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// 1-D bulk copy global -> shared (TMA engine), completion counted on `bar`.
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
-      "l"(src), "r"(bytes), "r"(smem_u32(bar))
-      : "memory");
-}
-
-__host__ __device__ inline size_t align128(size_t x) { return (x + 127) & ~(size_t)127; }
-
-// One sweep of a block from its tile stream.  Warp w takes the block's
-// tiles w, w+W, ... in order; lane 0 keeps the bulk copies of the next two
-// tiles in flight into the warp's ring while the warp solves the current
-// one (tiles larger than a slot are read from global memory in place).  The
-// rows of a tile share one level; a tile waits (warp-uniformly, bounded)
-// until every column it reads is final, as in the packed sweep.
-// Sum within aligned lane groups of size V (a power of two, per lane): every
-// lane takes part in every shuffle; a lane adds only partners of its group.
-template <typename T>
-__device__ __forceinline__ T segmented_sum(T v, int V) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const T w = __shfl_xor_sync(0xffffffffu, v, o);
-    if (o < V) v += w;
-  }
-  return v;
-}
-
-// One sweep of a block from its stream of variable-width tiles.  Warp w
-// takes the block's tiles w, w+W, ... in order; its lanes keep asynchronous
-// 16-byte copies (cp.async) of the next three tiles in flight into the
-// warp's shared-memory ring while the warp solves the current one (a tile
-// larger than a slot is read in place).  Small per-tile copies are spread
-// over the load/store units instead of one bulk-copy engine per SM.
-// Tile offsets are staged in shared memory, so the loop issues no global
-// load.  The rows of a tile share one level; each lane waits for the values
-// its entries read (bounded), the lanes of a row reduce, its first lane
-// writes the value.
-template <typename TS, typename TC>
-__device__ void sweep_tma(const unsigned char* __restrict__ stream, const int64_t* toff_s, int64_t ntile,
-                          unsigned char* ring, uint64_t* bars, int slot_bytes, int slots, unsigned& phase,
-                          volatile TC* in, volatile TC* out, bool unit, int* timeout) {
-  const int lane = lane_id(), w = threadIdx.x >> 5, W = blockDim.x >> 5;
-  const int64_t nk = ntile > w ? (ntile - w + W - 1) / W : 0;  // tiles of this warp
-  if (nk == 0) return;
-  // every lane copies 16-byte chunks of the tile; one commit group per tile
-  // (empty groups keep the count uniform), so wait_group<kSlotsCp-1> means
-  // "tile k has landed" for this lane; __syncwarp then publishes all lanes'
-  // chunks to the warp.
-  auto issue = [&](int64_t k) {
-    if (k < nk) {
-      const int64_t t = w + k * W;
-      const int64_t a = toff_s[t], b = toff_s[t + 1];
-      if (b - a <= slot_bytes) {
-        unsigned char* dst = ring + (size_t)(k % kSlotsCp) * slot_bytes;
-        for (int64_t c = lane; c < (b - a) / 16; c += 32) cp_async16(dst + 16 * c, stream + a + 16 * c);
-      }
-    }
-    cp_async_commit();
-  };
-  for (int d = 0; d < kSlotsCp - 1; ++d) issue(d);
-  for (int64_t k = 0; k < nk; ++k) {
-    issue(k + kSlotsCp - 1);
-    const int64_t t = w + k * W;
-    const int64_t a = toff_s[t], bytes = toff_s[t + 1] - a;
-    const unsigned char* base;
-    cp_async_wait<kSlotsCp - 1>();
-    __syncwarp();
-    if (bytes <= slot_bytes) {
-      base = ring + (size_t)(k % kSlotsCp) * slot_bytes;
-    } else {
-      base = stream + a;
-    }
-    const int nr = reinterpret_cast<const int32_t*>(base)[0];
-    const int ne = reinterpret_cast<const int32_t*>(base)[1];
-    const uint2 rec = reinterpret_cast<const uint2*>(base + 16)[lane];  // this lane's role, one load
-    const int row = (rec.x & 0xFFFFu) == 0xFFFFu ? -1 : (int)(rec.x & 0xFFFFu);
-    const int first = (int)(rec.x >> 16);
-    const int cnt = (int)(rec.y & 0xFFu);
-    const int V = 1 << ((rec.y >> 8) & 0xFFu);
-    const int r = (int)((rec.y >> 16) & 0xFFu);
-    const bool leader = ((rec.y >> 24) & 1u) != 0;
-    const TS* dv = reinterpret_cast<const TS*>(base + 16 + 256);
-    const int32_t* cols = reinterpret_cast<const int32_t*>(base + 16 + 256 + ((nr * (int)sizeof(TS) + 15) & ~15));
-    const TS* vals = reinterpret_cast<const TS*>(reinterpret_cast<const unsigned char*>(cols) + ((4 * ne + 15) & ~15));
-    // Gather this lane's entries (at most kReg per round; longer rows take
-    // more warp-uniform rounds), then wait warp-uniformly until every value
-    // the tile reads is solved: per-lane spin loops would leave the warp
-    // diverged, and its serialized paths would delay the row reduction.  An
-    // unsuccessful poll sleeps briefly to leave issue slots to working warps.
-    constexpr int kReg = 8;
-    TC acc = TC(0);
-    const int rounds = __reduce_max_sync(0xffffffffu, (cnt + kReg - 1) / kReg);
-    for (int c = 0; c < rounds; ++c) {
-      int jj[kReg];
-      TC vv[kReg];
-#pragma unroll
-      for (int k = 0; k < kReg; ++k) {
-        const int idx = c * kReg + k;
-        const bool ok = idx < cnt;
-        const int e = first + idx * V;
-        jj[k] = ok ? cols[e] : -1;
-        vv[k] = ok ? (TC)vals[e] : TC(0);
-      }
-      int spins = 0;
-      bool ready = true;
-#pragma unroll
-      for (int k = 0; k < kReg; ++k)
-        if (jj[k] >= 0 && is_sentinel((TC)out[jj[k]])) ready = false;
-      while (!__all_sync(0xffffffffu, ready)) {
-        __nanosleep(kBackoffNs);
-        ready = true;
-#pragma unroll
-        for (int k = 0; k < kReg; ++k)
-          if (jj[k] >= 0 && is_sentinel((TC)out[jj[k]])) ready = false;
-        if (++spins > kSpinLimit / 8) { *timeout = 1; ready = true; }
-      }
-#pragma unroll
-      for (int k = 0; k < kReg; ++k)
-        if (jj[k] >= 0) acc = fma(vv[k], (TC)out[jj[k]], acc);
-    }
-    acc = segmented_sum(acc, V);
-    if (leader) {
-      TC yi = in[row] - acc;
-      if (!unit) yi *= (TC)dv[r];
-      out[row] = yi;
-    }
-    __syncwarp();  // the slot is free for the copy issued at the next step
-  }
-  cp_async_wait<0>();
-}
-
-template <typename TS, typename TC, int V>
-__global__ void __launch_bounds__(kTmaWarps * 32) k_pcg_update_tma(TriSolve M, const double* __restrict__ p,
-                                                                   const double* __restrict__ q,
-                                                                   double* __restrict__ x, double* __restrict__ r,
-                                                                   double* __restrict__ z, double* __restrict__ pp,
-                                                                   double* __restrict__ part,
-                                                                   PcgState* __restrict__ s, int mode) {
-  if (mode == 0 && s->done) return;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ double sh[32];
-  __shared__ int timeout;
-  const int b = blockIdx.x;
-  const int64_t s0 = M.bp[b], e0 = M.bp[b + 1];
-  const size_t ybytes = align128((size_t)M.max_block * sizeof(TC));
-  const size_t fbytes = ybytes;
-  volatile TC* yb = reinterpret_cast<volatile TC*>(smem_raw);
-  volatile TC* yf = reinterpret_cast<volatile TC*>(smem_raw + ybytes);
-  const TC S = sentinel(TC(0));
-  const int w = threadIdx.x >> 5;
-  const int slots = M.slots;
-  unsigned char* ring = smem_raw + ybytes + fbytes + (size_t)w * slots * M.slot_bytes;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + ybytes + fbytes +
-                                               (size_t)(blockDim.x >> 5) * slots * M.slot_bytes) + w * slots;
-  // this block's tile offsets of both directions, staged once
-  int64_t* toff_f = reinterpret_cast<int64_t*>(bars + (blockDim.x >> 5) * slots - w * slots);
-  const int64_t tf0 = M.fwd_tile[b], ntf = M.fwd_tile[b + 1] - tf0;
-  const int64_t tb0 = M.bwd_tile[b], ntb = M.bwd_tile[b + 1] - tb0;
-  int64_t* toff_b = toff_f + ntf + 1;
-  for (int64_t t = threadIdx.x; t <= ntf; t += blockDim.x) toff_f[t] = M.fwd_toff[tf0 + t];
-  for (int64_t t = threadIdx.x; t <= ntb; t += blockDim.x) toff_b[t] = M.bwd_toff[tb0 + t];
-  if (threadIdx.x == 0) timeout = 0;
-  if (lane_id() == 0)
-    for (int k = 0; k < slots; ++k) mbar_init(bars + k, 1);
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  double rr = 0.0;
-  if (mode == 0) {
-    const double a = s->alpha;
-    for (int64_t i = s0 + threadIdx.x; i < e0; i += blockDim.x) {
-      const double ri = __fma_rn(-a, q[i], r[i]);
-      x[i] = __fma_rn(a, p[i], x[i]);
-      r[i] = ri;
-      rr = __fma_rn(ri, ri, rr);
-      yb[i - s0] = (TC)ri;
-      yf[i - s0] = S;
-    }
-  } else {
-    for (int64_t i = s0 + threadIdx.x; i < e0; i += blockDim.x) {
-      const double ri = r[i];
-      rr = __fma_rn(ri, ri, rr);
-      yb[i - s0] = (TC)ri;
-      yf[i - s0] = S;
-    }
-  }
-  const double rrb = block_sum(rr, sh);
-  __syncthreads();
-  unsigned phase = 0;
-  sweep_tma<TS, TC>(M.fwd_stream, toff_f, ntf, ring, bars, M.slot_bytes, slots, phase, yb, yf, M.unit_lower != 0,
-                    &timeout);
-  __syncthreads();
-  for (int64_t i = threadIdx.x; i < e0 - s0; i += blockDim.x) yb[i] = S;
-  __syncthreads();
-  sweep_tma<TS, TC>(M.bwd_stream, toff_b, ntb, ring, bars, M.slot_bytes, slots, phase, yf, yb, false, &timeout);
-  __syncthreads();
-  double rz = 0.0, zq = 0.0;
-  for (int64_t i = s0 + threadIdx.x; i < e0; i += blockDim.x) {
-    const double zi = (double)yb[i - s0];
-    z[i] = zi;
-    if (mode == 1) pp[i] = zi;
-    rz = __fma_rn(r[i], zi, rz);
-    if (mode == 0) zq = __fma_rn(zi, q[i], zq);
-  }
-  const double rzb = block_sum(rz, sh);
-  const double zqb = block_sum(zq, sh);
-  update_epilogue(M, rrb, rzb, zqb, part, s, mode, timeout != 0);
-}
-
-template <typename TS, typename TC, int V>
-cudaError_t launch_update_tma(const TriSolve& M, const double* p, const double* q, double* x, double* r, double* z,
-                              double* pp, double* part, PcgState* s, int mode, cudaStream_t st) {
-  const size_t need = tma_smem_bytes(M.max_block, sizeof(TC), kTmaWarps, M.slot_bytes, M.slots) +
-                      (size_t)(M.max_tiles + 2) * sizeof(int64_t);
-  auto kern = k_pcg_update_tma<TS, TC, V>;
-  SDSL_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need));
-  kern<<<(unsigned)M.nblocks, kTmaWarps * 32, need, st>>>(M, p, q, x, r, z, pp, part, s, mode); count_launch();
-  return cudaGetLastError();
-}
 
 template <typename T, int V>
 cudaError_t launch_update(const TriSolve& M, const double* p, const double* q, double* x, double* r, double* z,
@@ -912,11 +593,7 @@ cudaError_t update_any(const TriSolve& M, const double* p, const double* q, doub
                        double* pp, double* part, PcgState* s, int mode, cudaStream_t st) {
   return by_lanes(M.lanes, [&](auto V) -> cudaError_t {
     constexpr int kV = decltype(V)::value;
-    if (M.tma) {
-      if (M.prec == 64) return launch_update_tma<double, double, kV>(M, p, q, x, r, z, pp, part, s, mode, st);
-      if (M.apply_prec == 64) return launch_update_tma<float, double, kV>(M, p, q, x, r, z, pp, part, s, mode, st);
-      return launch_update_tma<float, float, kV>(M, p, q, x, r, z, pp, part, s, mode, st);
-    }
+    if (M.tma) return update_staged(M, p, q, x, r, z, pp, part, s, mode, st);
     if (M.sync_free) {
       if (M.prec == 64) return launch_update_sf<double, double, kV>(M, p, q, x, r, z, pp, part, s, mode, st);
       if (M.apply_prec == 64) return launch_update_sf<float, double, kV>(M, p, q, x, r, z, pp, part, s, mode, st);
@@ -968,6 +645,57 @@ cudaError_t factored_product(const SpmvPlan& A, const double* p, double* q, doub
   });
 }
 
+// Resident CTAs per SM of a product kernel at a lane width (kind 0: k_spmv,
+// 1: k_pcg_spmv, 2: k_at_theta, 3: k_a_u_dot), for one-wave grids.
+int product_occupancy(int kind, int lanes) {
+  int n = 0;
+  by_lanes(lanes, [&](auto V) -> cudaError_t {
+    constexpr int kV = decltype(V)::value;
+    switch (kind) {
+      case 0: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_spmv<kV>, kThreads, 0);
+      case 1: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_pcg_spmv<kV>, kThreads, 0);
+      case 2: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_at_theta<kV>, kThreads, 0);
+      default: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_a_u_dot<kV>, kThreads, 0);
+    }
+  });
+  return n > 0 ? n : 1;
+}
+
+// Mean device time of each half of the factored product over `reps` launches
+// (the autotuner's probe; p and q are scratch vectors).
+cudaError_t time_factored(const SpmvPlan& A, const double* p, double* q, int reps, float* ms_at, float* ms_a,
+                          cudaStream_t st) {
+  cudaEvent_t ev[3];
+  for (auto& e : ev) SDSL_CUDA_TRY(cudaEventCreate(&e));
+  SDSL_CUDA_TRY(factored_product(A, p, q, nullptr, nullptr, 0, st));  // warm
+  float t_at = 0.f, t_a = 0.f;
+  for (int i = 0; i < reps; ++i) {
+    SDSL_CUDA_TRY(cudaEventRecord(ev[0], st));
+    SDSL_CUDA_TRY(by_lanes(A.at_lanes, [&](auto V) -> cudaError_t {
+      k_at_theta<decltype(V)::value><<<A.at_grid, kThreads, 0, st>>>(A.ncols, A.at_rp, A.at_ci, A.at_v, A.theta, p,
+                                                                     A.u, nullptr); count_launch();
+      return cudaGetLastError();
+    }));
+    SDSL_CUDA_TRY(cudaEventRecord(ev[1], st));
+    SDSL_CUDA_TRY(by_lanes(A.a_lanes, [&](auto V) -> cudaError_t {
+      k_a_u_dot<decltype(V)::value><<<A.grid, kThreads, 0, st>>>(A.n, A.a_rp, A.a_ci, A.a_v, A.u, A.rho, p, q,
+                                                                 nullptr, nullptr, 0); count_launch();
+      return cudaGetLastError();
+    }));
+    SDSL_CUDA_TRY(cudaEventRecord(ev[2], st));
+    SDSL_CUDA_TRY(cudaEventSynchronize(ev[2]));
+    float a = 0.f, b = 0.f;
+    SDSL_CUDA_TRY(cudaEventElapsedTime(&a, ev[0], ev[1]));
+    SDSL_CUDA_TRY(cudaEventElapsedTime(&b, ev[1], ev[2]));
+    t_at += a;
+    t_a += b;
+  }
+  for (auto& e : ev) cudaEventDestroy(e);
+  *ms_at = t_at / (float)reps;
+  *ms_a = t_a / (float)reps;
+  return cudaSuccess;
+}
+
 cudaError_t pcg_spmv(const SpmvPlan& A, const double* p, double* q, double* part, PcgState* s, cudaStream_t st) {
   if (A.factored) return factored_product(A, p, q, part, s, 1, st);
   return by_lanes(A.lanes, [&](auto V) -> cudaError_t {
@@ -981,10 +709,6 @@ cudaError_t pcg_update_precond(const TriSolve& M, const double* p, const double*
   return update_any(M, p, q, x, r, z, nullptr, part, s, 0, st);
 }
 
-size_t tma_smem_bytes(int64_t max_block, size_t tc_size, int warps, int slot_bytes, int slots) {
-  return 2 * align128((size_t)max_block * tc_size) + (size_t)warps * slots * (size_t)slot_bytes +
-         (size_t)warps * slots * sizeof(uint64_t);
-}
 
 size_t sf_smem_bytes(int64_t max_block, size_t tc_size) {
   return 2 * (((size_t)max_block * tc_size + 15) & ~(size_t)15);

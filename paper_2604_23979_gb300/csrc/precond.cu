@@ -533,13 +533,13 @@ __global__ void k_tile_fill(int dir, int64_t ntiles, int RW, const int32_t* __re
 }
 
 // Variable-width tiles.  A tile holds rows of one level; row r of the tile
-// gets V_r lanes (a power of two, about four entries per lane), groups packed
-// at V-aligned lane offsets.  Layout (16-byte aligned parts):
+// gets V_r lanes (a power of two, a planned number of entries per lane),
+// groups packed at V-aligned lane offsets.  Layout (16-byte aligned parts):
 //   int32 nr, ne, 0, 0
 //   lane record x 32 (8 bytes each): uint16 row (block-local; 0xFFFF = idle),
 //     uint16 first (index of the lane's first entry in the tile), uint8 count
 //     (entries of the lane, strided by V), uint8 log2 V, uint8 r, uint8 0
-//   TS dinv[nr] | int32 col[ne] (block-local) | TS val[ne]
+//   TS dinv[nr] | uint16 col[ne] (block-local) | TS val[ne]
 // A lane reads its whole role with one 8-byte load.  The plan (rows of every
 // tile in packing order and their V) is built on the host; one tile per thread.
 template <typename TS>
@@ -584,8 +584,8 @@ __global__ void k_vt_fill(int dir, int64_t ntiles, const int32_t* __restrict__ t
     hdr[1] = ne;
     hdr[2] = 0;
     hdr[3] = 0;
-    int32_t* col = reinterpret_cast<int32_t*>(base + 16 + 256 + r16((int64_t)nr * sizeof(TS)));
-    TS* val = reinterpret_cast<TS*>(reinterpret_cast<unsigned char*>(col) + r16(4 * (int64_t)ne));
+    uint16_t* col = reinterpret_cast<uint16_t*>(base + 16 + 256 + r16((int64_t)nr * sizeof(TS)));
+    TS* val = reinterpret_cast<TS*>(reinterpret_cast<unsigned char*>(col) + r16(2 * (int64_t)ne));
     int at = 0;
     for (int r = 0; r < nr; ++r) {
       const int64_t i = plan_rows[r0 + r];
@@ -596,7 +596,7 @@ __global__ void k_vt_fill(int dir, int64_t ntiles, const int32_t* __restrict__ t
       for (int64_t q = t0; q < t1; ++q) {
         const int32_t j = pci[q];
         if (j < s || j >= e) continue;
-        col[at] = (int32_t)(j - s);
+        col[at] = (uint16_t)(j - s);
         val[at] = (TS)F[q];
         ++at;
       }

@@ -1,0 +1,278 @@
+// sweep.cu -- staged block triangular solves of the Block-Jacobi apply
+// (Sec. 2.3: z = M^{-1} r with M = blockdiag(L_b L_b^T) or blockdiag(L_b U_b)).
+//
+// One CTA per diagonal block (all blocks are independent work of one launch).
+// The block's rows are grouped by level (Sec. 2.2, level scheduling); the
+// rows of one level are packed into 32-lane tiles, a row taking V lanes.
+// Each tile is a contiguous byte record in HBM:
+//   [16 B header: nr, ne][32 lane records, 8 B each][inverse diagonals, nr]
+//   [block-local columns, ne x u16][values, ne]            (16-byte aligned parts)
+// A lane record is {row (0xFFFF: idle), first entry, entry count | log2 V << 8,
+// row-in-tile | first-lane-of-row << 8}.
+// Warp w of the CTA takes the block's tiles w, w+W, ... in order; its lanes
+// keep cp.async copies of the next SLOTS-1 tiles in flight into the warp's
+// shared-memory ring while the warp solves the current tile.  y lives in
+// shared memory, initialised to a signalling-NaN sentinel; a tile waits
+// (warp-uniformly, bounded) until every value it reads is no longer the
+// sentinel, so no barrier separates the levels.
+#include "pcg_common.cuh"
+
+namespace sdsl {
+
+namespace {
+
+constexpr int kSweepWarps = 16;
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+__host__ __device__ inline size_t align128(size_t x) { return (x + 127) & ~(size_t)127; }
+
+// Sum within aligned lane groups of size V (a power of two, per lane): every
+// lane takes part in every shuffle; a lane adds only partners of its group.
+// Vmax is the warp's largest group (warp-uniform): wider offsets are skipped.
+template <typename T>
+__device__ __forceinline__ T segmented_sum(T v, int V, int Vmax) {
+  for (int o = Vmax >> 1; o > 0; o >>= 1) {
+    const T w = __shfl_xor_sync(0xffffffffu, v, o);
+    if (o < V) v += w;
+  }
+  return v;
+}
+
+// One sweep of a block.  `in` holds the right-hand side, `out` the solution
+// (sentinel until solved).  Only warps w < W take tiles.
+template <typename TS, typename TC, int SLOTS, int KREG>
+__device__ __forceinline__ void sweep_staged(const unsigned char* __restrict__ stream, const int64_t* toff_s,
+                                             int ntile, unsigned char* ring, int slot_bytes, volatile TC* in,
+                                             volatile TC* out, bool unit, int* timeout, int W, unsigned backoff) {
+  const int lane = lane_id(), w = threadIdx.x >> 5;
+  if (w >= W) return;
+  const int nk = ntile > w ? (ntile - w + W - 1) / W : 0;  // tiles of this warp
+  if (nk == 0) return;
+  // Every lane copies 16-byte chunks of a tile; one commit group per tile
+  // (empty groups keep the count uniform).  Tiles 0..SLOTS-2 are issued up
+  // front and tile k+SLOTS-1 right after tile k is solved, so at tile k
+  // wait_group<SLOTS-2> means "tile k has landed" for this lane; __syncwarp
+  // then publishes all lanes' chunks to the warp.
+  auto issue = [&](int k) {
+    if (k < nk) {
+      const int t = w + k * W;
+      const int64_t a = toff_s[t];
+      const int n16 = (int)((toff_s[t + 1] - a) >> 4);
+      if (n16 * 16 <= slot_bytes) {
+        unsigned char* dst = ring + (k % SLOTS) * slot_bytes;
+        const unsigned char* src = stream + a;
+        for (int c = lane; c < n16; c += 32) cp_async16(dst + 16 * c, src + 16 * c);
+      }
+    }
+    cp_async_commit();
+  };
+#pragma unroll
+  for (int d = 0; d < SLOTS - 1; ++d) issue(d);
+  for (int k = 0; k < nk; ++k) {
+    const int t = w + k * W;
+    const int64_t a = toff_s[t];
+    const int bytes = (int)(toff_s[t + 1] - a);
+    cp_async_wait<SLOTS - 2>();
+    __syncwarp();
+    // A tile larger than a slot (one very long row) is read in place.
+    const unsigned char* base = bytes <= slot_bytes ? ring + (k % SLOTS) * slot_bytes : stream + a;
+    const int nr = reinterpret_cast<const int32_t*>(base)[0];
+    const int ne = reinterpret_cast<const int32_t*>(base)[1];
+    const uint2 rec = reinterpret_cast<const uint2*>(base + 16)[lane];  // this lane's role, one load
+    const int row = (int)(rec.x & 0xFFFFu);
+    const int first = (int)(rec.x >> 16);
+    const int cnt = (int)(rec.y & 0xFFu);
+    const int V = 1 << ((rec.y >> 8) & 0xFFu);
+    const int r = (int)((rec.y >> 16) & 0xFFu);
+    const bool leader = ((rec.y >> 24) & 1u) != 0;
+    const int Vmax = (int)__reduce_max_sync(0xffffffffu, (unsigned)V);
+    const TS* dv = reinterpret_cast<const TS*>(base + 16 + 256);
+    const uint16_t* cols = reinterpret_cast<const uint16_t*>(base + 16 + 256 + ((nr * (int)sizeof(TS) + 15) & ~15));
+    const TS* vals = reinterpret_cast<const TS*>(reinterpret_cast<const unsigned char*>(cols) + ((2 * ne + 15) & ~15));
+    // The right-hand side and the inverse diagonal are final before the
+    // sweep starts: read them before waiting, off the critical path.
+    const TC inr = leader ? (TC)in[row] : TC(0);
+    const TC dvr = leader && !unit ? (TC)dv[r] : TC(1);
+    // Gather this lane's entries (KREG per round; longer rows take more
+    // warp-uniform rounds), then wait warp-uniformly until every value the
+    // round reads is solved: per-lane spin loops would leave the warp
+    // diverged.  The values read by the poll are the ones used: a value that
+    // is no longer the sentinel is final (written once per sweep).  Two
+    // accumulators halve the dependent FMA chain after the wait.
+    TC acc = TC(0), acc2 = TC(0);
+    const int rounds = __reduce_max_sync(0xffffffffu, (unsigned)((cnt + KREG - 1) / KREG));
+    for (int c = 0; c < rounds; ++c) {
+      int jj[KREG];
+      TC vv[KREG], xv[KREG];
+#pragma unroll
+      for (int k2 = 0; k2 < KREG; ++k2) {
+        const int idx = c * KREG + k2;
+        const bool ok = idx < cnt;
+        const int e = first + idx * V;
+        jj[k2] = ok ? (int)cols[e] : -1;
+        vv[k2] = ok ? (TC)vals[e] : TC(0);
+      }
+      bool ready = true;
+#pragma unroll
+      for (int k2 = 0; k2 < KREG; ++k2) {
+        xv[k2] = jj[k2] >= 0 ? (TC)out[jj[k2]] : TC(0);
+        if (is_sentinel(xv[k2])) ready = false;
+      }
+      int spins = 0;
+      while (!__all_sync(0xffffffffu, ready)) {
+        if (backoff) __nanosleep(backoff);
+        ready = true;
+#pragma unroll
+        for (int k2 = 0; k2 < KREG; ++k2) {
+          if (jj[k2] >= 0 && is_sentinel(xv[k2])) xv[k2] = (TC)out[jj[k2]];
+          if (is_sentinel(xv[k2])) ready = false;
+        }
+        if (++spins > kSpinLimit / 8) {
+          *timeout = 1;
+          ready = true;
+#pragma unroll
+          for (int k2 = 0; k2 < KREG; ++k2)
+            if (is_sentinel(xv[k2])) xv[k2] = TC(0);
+        }
+      }
+#pragma unroll
+      for (int k2 = 0; k2 < KREG; k2 += 2) {
+        acc = fma(vv[k2], xv[k2], acc);
+        acc2 = fma(vv[k2 + 1], xv[k2 + 1], acc2);
+      }
+    }
+    acc = segmented_sum(acc + acc2, V, Vmax);
+    if (leader) out[row] = (inr - acc) * dvr;
+    __syncwarp();  // the slot of tile k-1 is free: refill it with tile k+SLOTS-1
+    issue(k + SLOTS - 1);
+  }
+  cp_async_wait<0>();
+}
+
+// mode 0: x += alpha p, r -= alpha q, ||r||^2, z = M^{-1} r, r^T z, z^T q;
+// mode 1: z = M^{-1} r only, then rho = r^T z and p = z (start or restart);
+// mode 2: z = M^{-1} r only.
+template <typename TS, typename TC, int SLOTS, int KREG>
+__global__ void __launch_bounds__(kSweepWarps * 32) k_pcg_update_staged(TriSolve M, const double* __restrict__ p,
+                                                                        const double* __restrict__ q,
+                                                                        double* __restrict__ x, double* __restrict__ r,
+                                                                        double* __restrict__ z, double* __restrict__ pp,
+                                                                        double* __restrict__ part,
+                                                                        PcgState* __restrict__ s, int mode) {
+  if (mode == 0 && s->done) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double sh[32];
+  __shared__ int timeout;
+  const int b = blockIdx.x;
+  const int64_t s0 = M.bp[b], e0 = M.bp[b + 1];
+  const size_t ybytes = align128((size_t)M.max_block * sizeof(TC));
+  volatile TC* yb = reinterpret_cast<volatile TC*>(smem_raw);
+  volatile TC* yf = reinterpret_cast<volatile TC*>(smem_raw + ybytes);
+  const TC S = sentinel(TC(0));
+  const int w = threadIdx.x >> 5;
+  const int W = blockDim.x >> 5;
+  unsigned char* rings = smem_raw + 2 * ybytes;
+  unsigned char* ring = rings + (size_t)w * SLOTS * M.slot_bytes;
+  // this block's tile offsets of both directions, staged once
+  int64_t* toff_f = reinterpret_cast<int64_t*>(rings + (size_t)W * SLOTS * M.slot_bytes);
+  const int64_t tf0 = M.fwd_tile[b];
+  const int ntf = (int)(M.fwd_tile[b + 1] - tf0);
+  const int64_t tb0 = M.bwd_tile[b];
+  const int ntb = (int)(M.bwd_tile[b + 1] - tb0);
+  int64_t* toff_b = toff_f + ntf + 1;
+  for (int t = threadIdx.x; t <= ntf; t += blockDim.x) toff_f[t] = M.fwd_toff[tf0 + t];
+  for (int t = threadIdx.x; t <= ntb; t += blockDim.x) toff_b[t] = M.bwd_toff[tb0 + t];
+  if (threadIdx.x == 0) timeout = 0;
+  double rr = 0.0;
+  if (mode == 0) {
+    const double a = s->alpha;
+    for (int64_t i = s0 + threadIdx.x; i < e0; i += blockDim.x) {
+      const double ri = __fma_rn(-a, q[i], r[i]);
+      x[i] = __fma_rn(a, p[i], x[i]);
+      r[i] = ri;
+      rr = __fma_rn(ri, ri, rr);
+      yb[i - s0] = (TC)ri;
+      yf[i - s0] = S;
+    }
+  } else {
+    for (int64_t i = s0 + threadIdx.x; i < e0; i += blockDim.x) {
+      const double ri = r[i];
+      rr = __fma_rn(ri, ri, rr);
+      yb[i - s0] = (TC)ri;
+      yf[i - s0] = S;
+    }
+  }
+  const double rrb = block_sum(rr, sh);
+  __syncthreads();
+  sweep_staged<TS, TC, SLOTS, KREG>(M.fwd_stream, toff_f, ntf, ring, M.slot_bytes, yb, yf, M.unit_lower != 0,
+                                    &timeout, M.sweep_warps, (unsigned)M.backoff_ns);
+  __syncthreads();
+  for (int64_t i = threadIdx.x; i < e0 - s0; i += blockDim.x) yb[i] = S;
+  __syncthreads();
+  sweep_staged<TS, TC, SLOTS, KREG>(M.bwd_stream, toff_b, ntb, ring, M.slot_bytes, yf, yb, false, &timeout,
+                                    M.sweep_warps, (unsigned)M.backoff_ns);
+  __syncthreads();
+  double rz = 0.0, zq = 0.0;
+  for (int64_t i = s0 + threadIdx.x; i < e0; i += blockDim.x) {
+    const double zi = (double)yb[i - s0];
+    z[i] = zi;
+    if (mode == 1) pp[i] = zi;
+    rz = __fma_rn(r[i], zi, rz);
+    if (mode == 0) zq = __fma_rn(zi, q[i], zq);
+  }
+  const double rzb = block_sum(rz, sh);
+  const double zqb = block_sum(zq, sh);
+  update_epilogue(M, rrb, rzb, zqb, part, s, mode, timeout != 0);
+}
+
+template <typename TS, typename TC, int SLOTS, int KREG>
+cudaError_t launch_staged(const TriSolve& M, const double* p, const double* q, double* x, double* r, double* z,
+                          double* pp, double* part, PcgState* s, int mode, cudaStream_t st) {
+  const size_t need = staged_smem_bytes(M.max_block, sizeof(TC), kSweepWarps, M.slot_bytes, M.slots, M.max_tiles);
+  auto kern = k_pcg_update_staged<TS, TC, SLOTS, KREG>;
+  SDSL_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need));
+  kern<<<(unsigned)M.nblocks, kSweepWarps * 32, need, st>>>(M, p, q, x, r, z, pp, part, s, mode); count_launch();
+  return cudaGetLastError();
+}
+
+template <typename TS, typename TC>
+cudaError_t launch_shape(const TriSolve& M, const double* p, const double* q, double* x, double* r, double* z,
+                         double* pp, double* part, PcgState* s, int mode, cudaStream_t st) {
+  const bool wide = M.kreg > 8;
+  switch (M.slots) {
+    case 2:
+      return wide ? launch_staged<TS, TC, 2, 16>(M, p, q, x, r, z, pp, part, s, mode, st)
+                  : launch_staged<TS, TC, 2, 8>(M, p, q, x, r, z, pp, part, s, mode, st);
+    case 3:
+      return wide ? launch_staged<TS, TC, 3, 16>(M, p, q, x, r, z, pp, part, s, mode, st)
+                  : launch_staged<TS, TC, 3, 8>(M, p, q, x, r, z, pp, part, s, mode, st);
+    default:
+      return wide ? launch_staged<TS, TC, 4, 16>(M, p, q, x, r, z, pp, part, s, mode, st)
+                  : launch_staged<TS, TC, 4, 8>(M, p, q, x, r, z, pp, part, s, mode, st);
+  }
+}
+
+}  // namespace
+
+size_t staged_smem_bytes(int64_t max_block, size_t tc_size, int warps, int slot_bytes, int slots, int64_t max_tiles) {
+  return 2 * align128((size_t)max_block * tc_size) + (size_t)warps * slots * (size_t)slot_bytes +
+         (size_t)(max_tiles + 2) * sizeof(int64_t);
+}
+
+cudaError_t update_staged(const TriSolve& M, const double* p, const double* q, double* x, double* r, double* z,
+                          double* pp, double* part, PcgState* s, int mode, cudaStream_t st) {
+  if (M.prec == 64) return launch_shape<double, double>(M, p, q, x, r, z, pp, part, s, mode, st);
+  if (M.apply_prec == 64) return launch_shape<float, double>(M, p, q, x, r, z, pp, part, s, mode, st);
+  return launch_shape<float, float>(M, p, q, x, r, z, pp, part, s, mode, st);
+}
+
+}  // namespace sdsl

@@ -31,6 +31,7 @@ class sdsl_options(C.Structure):
         ("restart", C.c_int), ("refactor_ratio", C.c_double), ("mem_space", C.c_int), ("stream", C.c_void_p),
         ("graph_iters", C.c_int), ("tune", C.c_int), ("profile", C.c_int), ("apply_prec", C.c_int),
         ("flexible", C.c_int), ("solve_kernel", C.c_int), ("spmv_form", C.c_int), ("orthog", C.c_int),
+        ("sweep_warps", C.c_int), ("sweep_backoff_ns", C.c_int), ("sweep_lane_entries", C.c_int),
     ]
 
 
@@ -44,6 +45,7 @@ class sdsl_stats(C.Structure):
         ("shifted_blocks", C.c_int64), ("builds", C.c_int64), ("bytes_per_iter", C.c_double),
         ("kernel_ms", C.c_double * 4), ("kernel_launches", C.c_int64 * 4), ("kernel_bytes", C.c_double * 4),
         ("spmv_lanes", C.c_int64), ("solve_lanes", C.c_int64), ("tuned_spmv_lanes", C.c_int64),
+        ("product_lanes", C.c_int64 * 2),
     ]
 
     def as_dict(self):
