@@ -118,6 +118,8 @@ typedef struct {
   int64_t tuned_spmv_lanes; /* explicit-S SpMV lanes chosen by the autotuner (0 if it did not run) */
   int64_t product_lanes[2]; /* factored normal-equation product: lanes per row of A^T p and of A u
                                (0 when the explicit S is used) */
+  double ms_schur;        /* BBD: device time of the border Schur complement assembly (part of ms_factor) */
+  double ms_dense_lu;     /* BBD: device time of its dense LU and FP32 inverse (part of ms_factor) */
 } sdsl_stats;
 
 typedef struct {

@@ -107,6 +107,13 @@ struct sdsl_handle_s {
   cudaStream_t user = nullptr;     // caller's stream, joined at entry/exit
   cudaEvent_t ev_a = nullptr, ev_b = nullptr, ev_join = nullptr;
   int dev = 0, sms = 152;
+  long long graph_kernels = 0;     // kernels in one launch of the iteration graph
+  // rows of the system matrix longer than long_thr (summed by one CTA each)
+  bool long_planned = false;
+  int long_thr = 0;
+  int64_t n_long = 0;
+  int32_t* long_rows = nullptr;
+  double* long_ax = nullptr;
   int form = 0, method = 0;
   int64_t m = 0, n = 0, N = 0;  // input rows/cols, system dimension
   Arena sys, pc;
@@ -389,6 +396,10 @@ void choose_spmv_plan(sdsl_handle h) {
   h->A.ci = h->s_ci;
   h->A.v = h->s_v;
   h->A.lanes = lanes_for(avg);
+  h->A.long_thr = h->long_thr;
+  h->A.n_long = h->n_long;
+  h->A.long_rows = h->long_rows;
+  h->A.long_ax = h->long_ax;
   set_product_grids(h);
 }
 
@@ -467,6 +478,31 @@ sdsl_status profiled_iteration(sdsl_handle h) {
   return SDSL_OK;
 }
 
+// Rows of the system matrix with more than max(1024, 16 x average) entries
+// (the border rows of a BBD system span every block) get one CTA each in the
+// products; the list depends only on the pattern, so it is built once.
+sdsl_status plan_long_rows(sdsl_handle h) {
+  if (h->long_planned) return SDSL_OK;
+  const int64_t N = h->N;
+  std::vector<int64_t> rp(N + 1);
+  TRY(to_host(h, rp.data(), h->s_rp, N + 1));
+  TRY(sync(h, "long rows"));
+  const double avg = N > 0 ? (double)rp[N] / (double)N : 0.0;
+  const int64_t thr = std::max<int64_t>(1024, (int64_t)(16.0 * avg));
+  std::vector<int32_t> rows;
+  for (int64_t i = 0; i < N; ++i)
+    if (rp[i + 1] - rp[i] > thr) rows.push_back((int32_t)i);
+  h->long_thr = (int)std::min<int64_t>(thr, INT32_MAX);
+  h->n_long = (int64_t)rows.size();
+  if (h->n_long > 0) {
+    TRY(h->sys.get(&h->long_rows, h->n_long));
+    TRY(h->sys.get(&h->long_ax, h->n_long));
+    TRY(to_dev(h, h->long_rows, rows.data(), h->n_long));
+  }
+  h->long_planned = true;
+  return SDSL_OK;
+}
+
 sdsl_status build_graph(sdsl_handle h) {
   destroy_graph(h);
   const int G = h->opt.graph_iters;
@@ -477,7 +513,8 @@ sdsl_status build_graph(sdsl_handle h) {
   sdsl_status s = SDSL_OK;
   for (int i = 0; i < G && s == SDSL_OK; ++i) s = enqueue_pcg_iteration(h);
   cudaError_t e = cudaStreamEndCapture(h->st, &g);
-  count_launch(before - launches_so_far());  // captured, not executed: counted per graph launch
+  h->graph_kernels = launches_so_far() - before;
+  count_launch(-h->graph_kernels);  // captured, not executed: counted per graph launch
   if (s != SDSL_OK) { if (g) cudaGraphDestroy(g); return s; }
   if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
   e = cudaGraphInstantiate(&h->graph, g, 0);
@@ -539,17 +576,28 @@ sdsl_status build_bbd(sdsl_handle h) {
   double* X;
   float* work;
   TRY(tmp.get(&X, (size_t)schur_tiles(m) * maxb * 32));
+  cudaEvent_t ev[3];
+  for (auto& e : ev) TRY_CUDA(cudaEventCreate(&e));
+  TRY_CUDA(cudaEventRecord(ev[0], h->st));
   for (int64_t k = 0; k < nb; ++k)  // blocks in order: deterministic accumulation
     TRY_CUDA(schur_block(h->h_bp[k], h->h_bp[k + 1], h->b0, m, h->p_rp, h->p_ci, h->p_v, h->F, h->dinv, h->p_diag,
                          h->h_lev_off_lo[k], h->h_lev_off_lo[k + 1], h->lev_ptr_lo, h->lev_rows_lo,
                          h->h_lev_off_up[k], h->h_lev_off_up[k + 1], h->lev_ptr_up, h->lev_rows_up, X, h->SB, h->st));
+  TRY_CUDA(cudaEventRecord(ev[1], h->st));
   TRY_CUDA(cudaMemsetAsync(h->flag, 0, sizeof(int), h->st));
   TRY_CUDA(dense_lu_f32(m, h->SB, h->LU32, h->ipiv, h->flag, h->st));
   TRY(tmp.get(&work, (size_t)m * ((m + 31) / 32) * 32));
   TRY_CUDA(dense_lu_inverse(m, h->LU32, h->ipiv, h->Sinv, work, h->st));
+  TRY_CUDA(cudaEventRecord(ev[2], h->st));
   int bad = 0;
   TRY(to_host(h, &bad, h->flag, 1));
   TRY(sync(h, "schur lu"));
+  float t0 = 0.f, t1 = 0.f;
+  cudaEventElapsedTime(&t0, ev[0], ev[1]);
+  cudaEventElapsedTime(&t1, ev[1], ev[2]);
+  h->stats.ms_schur = t0;
+  h->stats.ms_dense_lu = t1;
+  for (auto& e : ev) cudaEventDestroy(e);
   tmp.release();
   if (bad) return fail(SDSL_ERR_BREAKDOWN, "zero pivot in the LU of the border Schur complement");
   return SDSL_OK;
@@ -1118,6 +1166,7 @@ sdsl_status factor_impl(sdsl_handle h) {
       else { M.bwd_off = off; M.bwd_col = col; M.bwd_val = val; M.bwd_dinv = pdv; M.bwd_row = prow; M.bwd_pos = d_pos; }
     }
   }
+  TRY(plan_long_rows(h));
   choose_spmv_plan(h);
   if (h->opt.tune) TRY(tune_spmv(h));
   if (h->method == SDSL_BJ_PCG && !h->opt.profile) TRY(build_graph(h));
@@ -1197,7 +1246,7 @@ sdsl_status pcg_solve(sdsl_handle h, sdsl_stats* st_out) {
       TRY(profiled_iteration(h));
     } else if (h->graph) {
       TRY_CUDA(cudaGraphLaunch(h->graph, h->st));
-      count_launch(3LL * h->graph_iters);
+      count_launch(h->graph_kernels);
     } else {
       for (int i = 0; i < 8; ++i) TRY(enqueue_pcg_iteration(h));
     }

@@ -90,12 +90,16 @@ __global__ void k_schur_tile(int64_t s, int64_t e, int64_t b0, int64_t nb, const
     }
     __syncthreads();
   }
-  // S_B[:, tile] -= F_k X   (border rows, block-k columns)
+  // S_B[:, tile] -= F_k X   (border rows, block-k columns).  A border row
+  // spans every block; its columns are sorted, so only the block's range is
+  // visited (first in-block entry by binary search).
   for (int64_t r = w; r < nb; r += nw) {
     double acc = 0.0;
-    for (int64_t t = prp[b0 + r]; t < prp[b0 + r + 1]; ++t) {
+    const int64_t t1 = prp[b0 + r + 1];
+    for (int64_t t = lower_bound_i32(pci, prp[b0 + r], t1, (int32_t)s); t < t1; ++t) {
       const int64_t j = pci[t];
-      if (j >= s && j < e) acc = __fma_rn(pv[t], X[(j - s) * kR + lane], acc);
+      if (j >= e) break;
+      acc = __fma_rn(pv[t], X[(j - s) * kR + lane], acc);
     }
     if (c < nb) SB[r * nb + c] -= acc;
   }
@@ -199,8 +203,11 @@ __global__ void k_lu_inverse(int64_t n, const float* __restrict__ LU, const int3
 
 // ---------------------------------------------------------------- BBD apply
 
-// Interior blocks: level-scheduled unit-lower then upper sweep on a global
-// vector, one CTA per block (in place: y = L^{-1} y, then y = U^{-1} y).
+// Block LU solves y_k = U_k^{-1} L_k^{-1} y_k for every interior block (one
+// CTA per block), level by level.  A row is summed by a group of kLuV lanes
+// (rows here have tens of entries); the loop over a level's rows is
+// warp-uniform so the group shuffles see every lane.
+constexpr int kLuV = 4;
 __global__ void k_block_lu_solve(const int64_t* __restrict__ bp, const int64_t* __restrict__ prp,
                                  const int32_t* __restrict__ pci, const double* __restrict__ F,
                                  const double* __restrict__ dinv, const int64_t* __restrict__ pdiag,
@@ -211,29 +218,40 @@ __global__ void k_block_lu_solve(const int64_t* __restrict__ bp, const int64_t* 
   const int b = blockIdx.x;
   const int64_t s = bp[b], e = bp[b + 1];
   const int lane = lane_id(), w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int g = lane / kLuV, sub = lane % kLuV;
+  constexpr int kRows = 32 / kLuV;  // rows per warp step
   for (int32_t L = lev_off_lo[b]; L < lev_off_lo[b + 1]; ++L) {
-    for (int32_t q = lev_ptr_lo[L] + w; q < lev_ptr_lo[L + 1]; q += nw) {
-      const int64_t i = lev_rows_lo[q];
+    const int32_t q0 = lev_ptr_lo[L], q1 = lev_ptr_lo[L + 1];
+    for (int32_t base = q0 + w * kRows; base < q1; base += nw * kRows) {
+      const int32_t q = base + g;
+      const bool valid = q < q1;
+      const int64_t i = valid ? lev_rows_lo[q] : 0;
       double acc = 0.0;
-      for (int64_t t = prp[i] + lane; t < pdiag[i]; t += 32) {
-        const int64_t j = pci[t];
-        if (j >= s) acc = __fma_rn(F[t], y[j], acc);
-      }
-      acc = warp_sum(acc);
-      if (lane == 0) y[i] -= acc;
+      if (valid)
+        for (int64_t t = prp[i] + sub; t < pdiag[i]; t += kLuV) {
+          const int64_t j = pci[t];
+          if (j >= s) acc = __fma_rn(F[t], y[j], acc);
+        }
+      acc = group_sum<kLuV>(acc);
+      if (valid && sub == 0) y[i] -= acc;
     }
     __syncthreads();
   }
   for (int32_t L = lev_off_up[b]; L < lev_off_up[b + 1]; ++L) {
-    for (int32_t q = lev_ptr_up[L] + w; q < lev_ptr_up[L + 1]; q += nw) {
-      const int64_t i = lev_rows_up[q];
+    const int32_t q0 = lev_ptr_up[L], q1 = lev_ptr_up[L + 1];
+    for (int32_t base = q0 + w * kRows; base < q1; base += nw * kRows) {
+      const int32_t q = base + g;
+      const bool valid = q < q1;
+      const int64_t i = valid ? lev_rows_up[q] : 0;
       double acc = 0.0;
-      for (int64_t t = pdiag[i] + 1 + lane; t < prp[i + 1]; t += 32) {
-        const int64_t j = pci[t];
-        if (j < e) acc = __fma_rn(F[t], y[j], acc);
-      }
-      acc = warp_sum(acc);
-      if (lane == 0) y[i] = (y[i] - acc) * dinv[i];
+      if (valid)
+        for (int64_t t = pdiag[i] + 1 + sub; t < prp[i + 1]; t += kLuV) {
+          const int64_t j = pci[t];
+          if (j >= e) break;  // columns are sorted: the rest lie beyond the block
+          acc = __fma_rn(F[t], y[j], acc);
+        }
+      acc = group_sum<kLuV>(acc);
+      if (valid && sub == 0) y[i] = (y[i] - acc) * dinv[i];
     }
     __syncthreads();
   }

@@ -81,6 +81,16 @@ __device__ __forceinline__ int64_t bsearch_i32(const int32_t* __restrict__ a, in
   return -1;
 }
 
+// First index in sorted a[lo, hi) with a[index] >= key (hi if none).
+__device__ __forceinline__ int64_t lower_bound_i32(const int32_t* __restrict__ a, int64_t lo, int64_t hi,
+                                                   int32_t key) {
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (a[mid] < key) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
 // Process-wide count of kernel launches made by this library (every
 // `<<<...>>>` launch site calls count_launch once per launch).
 void count_launch(long long k = 1);

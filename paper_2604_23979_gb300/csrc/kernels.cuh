@@ -201,6 +201,13 @@ struct SpmvPlan {
   double* u;      // scratch, n entries
   int at_lanes, a_lanes;
   int at_grid;
+  // rows longer than long_thr entries (e.g. the border rows of a BBD system,
+  // which span every block) are summed by one CTA each before the row kernel
+  // runs; the row kernel takes their values from long_ax.
+  int long_thr;             // 0: no long rows
+  int64_t n_long;
+  const int32_t* long_rows; // ascending
+  double* long_ax;          // n_long values of the last product
 };
 
 cudaError_t spmv(const SpmvPlan& A, const double* x, double* y, cudaStream_t st);

@@ -12,6 +12,8 @@
 // order and writes the scalars for the next launch into PcgState.  The
 // paper's MPI_Allreduce of the inner products (Sec. 2.3) becomes this
 // on-device reduction; the ghost exchange disappears (x is resident).
+#include <algorithm>
+
 #include "common.cuh"
 #include "kernels.cuh"
 #include "pcg_common.cuh"
@@ -58,6 +60,59 @@ __device__ __forceinline__ double row_dot(const int64_t* __restrict__ rp, const 
   return group_sum<V>(acc);
 }
 
+// Long rows (more than thr entries): their product values were computed by
+// k_long_dot into ax[k] (k = position of the row in the ascending list).
+struct LongRows {
+  int thr;
+  int64_t n;
+  const int32_t* rows;
+  const double* ax;
+};
+
+__device__ __forceinline__ double long_value(const LongRows& L, int64_t i) {
+  int64_t lo = 0, hi = L.n - 1;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (L.rows[mid] < i) lo = mid + 1; else hi = mid;
+  }
+  return L.ax[lo];
+}
+
+// Row i of A times x (every lane of the warp calls it), long rows excepted.
+template <int V>
+__device__ __forceinline__ double row_value(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                            const double* __restrict__ v, const double* __restrict__ x, int64_t i,
+                                            int sub, bool valid, const LongRows& L) {
+  const bool lng = valid && L.thr > 0 && rp[i + 1] - rp[i] > L.thr;
+  const double acc = row_dot<V>(rp, ci, v, x, i, sub, valid && !lng);
+  return lng ? long_value(L, i) : acc;
+}
+
+// One CTA per long row: a[k] = row long_rows[k] of A times x, summed by the
+// whole CTA in a fixed order (deterministic).
+__global__ void __launch_bounds__(kThreads) k_long_dot(int64_t n_long, const int32_t* __restrict__ rows,
+                                                       const int64_t* __restrict__ rp,
+                                                       const int32_t* __restrict__ ci, const double* __restrict__ v,
+                                                       const double* __restrict__ x, double* __restrict__ ax,
+                                                       const PcgState* __restrict__ s) {
+  if (s && s->done) return;
+  __shared__ double sh[kThreads / 32];
+  for (int64_t k = blockIdx.x; k < n_long; k += gridDim.x) {
+    const int64_t i = rows[k];
+    double a0 = 0.0, a1 = 0.0;
+    const int64_t e = rp[i + 1];
+    int64_t t = rp[i] + threadIdx.x;
+    for (; t + kThreads < e; t += 2 * kThreads) {
+      a0 = __fma_rn(__ldcs(v + t), __ldg(x + __ldcs(ci + t)), a0);
+      a1 = __fma_rn(__ldcs(v + t + kThreads), __ldg(x + __ldcs(ci + t + kThreads)), a1);
+    }
+    if (t < e) a0 = __fma_rn(__ldcs(v + t), __ldg(x + __ldcs(ci + t)), a0);
+    const double tot = block_sum(a0 + a1, sh);
+    if (threadIdx.x == 0) ax[k] = tot;
+    __syncthreads();
+  }
+}
+
 // Row range of CTA c: rows split evenly (deterministic for a fixed grid).
 __device__ __forceinline__ void cta_rows(int64_t n, int64_t& r0, int64_t& r1) {
   const int64_t per = (n + gridDim.x - 1) / gridDim.x;
@@ -68,14 +123,15 @@ __device__ __forceinline__ void cta_rows(int64_t n, int64_t& r0, int64_t& r1) {
 template <int V>
 __global__ void __launch_bounds__(kThreads) k_spmv(int64_t n, const int64_t* __restrict__ rp,
                                                    const int32_t* __restrict__ ci, const double* __restrict__ v,
-                                                   const double* __restrict__ x, double* __restrict__ y) {
+                                                   const double* __restrict__ x, double* __restrict__ y,
+                                                   LongRows L) {
   int64_t r0, r1;
   cta_rows(n, r0, r1);
   const int g = threadIdx.x / V, sub = threadIdx.x % V, ng = kThreads / V;
   for (int64_t base = r0; base < r1; base += ng) {
     const int64_t i = base + g;
     const bool valid = i < r1;
-    const double acc = row_dot<V>(rp, ci, v, x, i, sub, valid);
+    const double acc = row_value<V>(rp, ci, v, x, i, sub, valid, L);
     if (valid && sub == 0) y[i] = acc;
   }
 }
@@ -84,7 +140,8 @@ template <int V>
 __global__ void __launch_bounds__(kThreads) k_pcg_spmv(int64_t n, const int64_t* __restrict__ rp,
                                                        const int32_t* __restrict__ ci, const double* __restrict__ v,
                                                        const double* __restrict__ p, double* __restrict__ q,
-                                                       double* __restrict__ part, PcgState* __restrict__ s) {
+                                                       double* __restrict__ part, PcgState* __restrict__ s,
+                                                       LongRows L) {
   if (s->done) return;
   __shared__ double sh[kThreads / 32];
   int64_t r0, r1;
@@ -94,7 +151,7 @@ __global__ void __launch_bounds__(kThreads) k_pcg_spmv(int64_t n, const int64_t*
   for (int64_t base = r0; base < r1; base += ng) {
     const int64_t i = base + g;
     const bool valid = i < r1;
-    const double acc = row_dot<V>(rp, ci, v, p, i, sub, valid);
+    const double acc = row_value<V>(rp, ci, v, p, i, sub, valid, L);
     if (valid && sub == 0) {
       q[i] = acc;
       loc = __fma_rn(p[i], acc, loc);
@@ -183,7 +240,7 @@ __global__ void __launch_bounds__(kThreads) k_residual(int64_t n, const int64_t*
                                                        const int32_t* __restrict__ ci, const double* __restrict__ v,
                                                        const double* __restrict__ b, const double* __restrict__ x,
                                                        double* __restrict__ r, double* __restrict__ part,
-                                                       PcgState* __restrict__ s, int write_r) {
+                                                       PcgState* __restrict__ s, int write_r, LongRows L) {
   __shared__ double sh[kThreads / 32];
   int64_t r0, r1;
   cta_rows(n, r0, r1);
@@ -192,7 +249,7 @@ __global__ void __launch_bounds__(kThreads) k_residual(int64_t n, const int64_t*
   for (int64_t base = r0; base < r1; base += ng) {
     const int64_t i = base + g;
     const bool valid = i < r1;
-    const double ax = row_dot<V>(rp, ci, v, x, i, sub, valid);
+    const double ax = row_value<V>(rp, ci, v, x, i, sub, valid, L);
     if (valid && sub == 0) {
       const double t = b[i] - ax;
       if (write_r) r[i] = t;
@@ -604,11 +661,29 @@ cudaError_t update_any(const TriSolve& M, const double* p, const double* q, doub
   });
 }
 
+LongRows long_of(const SpmvPlan& A) {
+  LongRows L;
+  L.thr = A.n_long > 0 ? A.long_thr : 0;
+  L.n = A.n_long;
+  L.rows = A.long_rows;
+  L.ax = A.long_ax;
+  return L;
+}
+
+// Long rows of the plan (if any), one CTA each, before the row kernel.
+cudaError_t long_rows(const SpmvPlan& A, const double* x, const PcgState* s, cudaStream_t st) {
+  if (A.n_long <= 0) return cudaSuccess;
+  const unsigned grid = (unsigned)std::min<int64_t>(A.n_long, 152 * 8);
+  k_long_dot<<<grid, kThreads, 0, st>>>(A.n_long, A.long_rows, A.rp, A.ci, A.v, x, A.long_ax, s); count_launch();
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 cudaError_t spmv(const SpmvPlan& A, const double* x, double* y, cudaStream_t st) {
   return by_lanes(A.lanes, [&](auto V) -> cudaError_t {
-    k_spmv<decltype(V)::value><<<A.grid, kThreads, 0, st>>>(A.n, A.rp, A.ci, A.v, x, y); count_launch();
+    SDSL_CUDA_TRY(long_rows(A, x, nullptr, st));
+    k_spmv<decltype(V)::value><<<A.grid, kThreads, 0, st>>>(A.n, A.rp, A.ci, A.v, x, y, long_of(A)); count_launch();
     return cudaGetLastError();
   });
 }
@@ -699,7 +774,8 @@ cudaError_t time_factored(const SpmvPlan& A, const double* p, double* q, int rep
 cudaError_t pcg_spmv(const SpmvPlan& A, const double* p, double* q, double* part, PcgState* s, cudaStream_t st) {
   if (A.factored) return factored_product(A, p, q, part, s, 1, st);
   return by_lanes(A.lanes, [&](auto V) -> cudaError_t {
-    k_pcg_spmv<decltype(V)::value><<<A.grid, kThreads, 0, st>>>(A.n, A.rp, A.ci, A.v, p, q, part, s); count_launch();
+    SDSL_CUDA_TRY(long_rows(A, p, s, st));
+    k_pcg_spmv<decltype(V)::value><<<A.grid, kThreads, 0, st>>>(A.n, A.rp, A.ci, A.v, p, q, part, s, long_of(A)); count_launch();
     return cudaGetLastError();
   });
 }
@@ -727,7 +803,9 @@ cudaError_t pcg_direction(int64_t n, const double* z, double* p, PcgState* s, cu
 cudaError_t true_residual(const SpmvPlan& A, const double* b, const double* x, double* r, double* part,
                           PcgState* s, int write_r, cudaStream_t st) {
   return by_lanes(A.lanes, [&](auto V) -> cudaError_t {
-    k_residual<decltype(V)::value><<<A.grid, kThreads, 0, st>>>(A.n, A.rp, A.ci, A.v, b, x, r, part, s, write_r); count_launch();
+    SDSL_CUDA_TRY(long_rows(A, x, nullptr, st));
+    k_residual<decltype(V)::value><<<A.grid, kThreads, 0, st>>>(A.n, A.rp, A.ci, A.v, b, x, r, part, s, write_r,
+                                                                long_of(A)); count_launch();
     return cudaGetLastError();
   });
 }

@@ -45,7 +45,7 @@ class sdsl_stats(C.Structure):
         ("shifted_blocks", C.c_int64), ("builds", C.c_int64), ("bytes_per_iter", C.c_double),
         ("kernel_ms", C.c_double * 4), ("kernel_launches", C.c_int64 * 4), ("kernel_bytes", C.c_double * 4),
         ("spmv_lanes", C.c_int64), ("solve_lanes", C.c_int64), ("tuned_spmv_lanes", C.c_int64),
-        ("product_lanes", C.c_int64 * 2),
+        ("product_lanes", C.c_int64 * 2), ("ms_schur", C.c_double), ("ms_dense_lu", C.c_double),
     ]
 
     def as_dict(self):

@@ -118,11 +118,36 @@ def test_bbd_gmres_matches_oracle(seed):
     # count moves by several per cent when b is perturbed at 1e-14.  The GPU
     # count must lie within that spread (widened by 5 %).
     counts = [res.iters]
-    for k in range(1, 5):
+    for k in range(1, 10):
         bk = p.b * (1 + 1e-14 * np.random.default_rng(k).standard_normal(len(p.b)))
         counts.append(oracle.gmres(ref["K"], bk, oracle.PRE_BBD, ref["P"], ref["F"], ref["kbp"], ref["lu"],
                                    ref["ipiv"], rtol=p.rtol, maxit=p.maxit, restart=p.restart).iters)
     assert 0.95 * min(counts) <= st.iters <= 1.05 * max(counts), (st.iters, counts)
+
+
+@pytest.mark.parametrize("seed", [5, 3])
+def test_bbd_gmres_few_restarts(seed):
+    """theta in [0.1, 10], rho = 1: GMRES(30) converges in two or three
+    cycles, where the count is stable under rounding, so the GPU count is
+    within max(1, 5 %) of the oracle's."""
+    p = kkt(seed=seed)
+    rng = np.random.default_rng(0)
+    p.theta = np.exp(rng.uniform(np.log(0.1), np.log(10.0), len(p.theta)))
+    p.rho = 1.0
+    ref = oracle_bbd(p)
+    res = oracle.gmres(ref["K"], p.b, oracle.PRE_BBD, ref["P"], ref["F"], ref["kbp"], ref["lu"], ref["ipiv"],
+                       rtol=p.rtol, maxit=p.maxit, restart=p.restart)
+    assert res.status == 0 and p.restart < res.iters <= 4 * p.restart
+    h, keep = gpu_setup(p)
+    try:
+        sdsl.sdsl_factor(h)
+        x = np.zeros(len(p.b))
+        st = sdsl.sdsl_solve(h, p.b, x)
+    finally:
+        sdsl.sdsl_free(h)
+    assert st.status == 0 and relres(ref["K"], x, p.b) <= p.rtol
+    assert rel(x, res.x) <= 1e-6
+    assert iters_close(st.iters, res.iters), (st.iters, res.iters)
 
 
 def test_bbd_gmres_unrestarted_counts():
