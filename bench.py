@@ -50,6 +50,14 @@ def parse():
     ap.add_argument("--backoff-ns", type=int, default=-1, help="poll backoff of the staged sweeps (-1 auto)")
     ap.add_argument("--lane-entries", type=int, default=0, help="entries per lane of the sweep tiles (0 auto)")
     ap.add_argument("--tune", type=int, default=0, help="1: autotune the product kernels' lane widths at factor time")
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5"],
+                    help="c2: the headline Block-Jacobi solve (default); c3: BBD GMRES(30) on the block-angular "
+                         "KKT system; c4: 30-step IPM sequence with preconditioner reuse; c5: served stream")
+    ap.add_argument("--maxit", type=int, default=0, help="c3: cap on GMRES iterations (0: the workload's)")
+    ap.add_argument("--count", type=int, default=200, help="c5: requests in the stream")
+    ap.add_argument("--rates", default="200", help="c5: comma-separated Poisson rates (requests/s) to sweep")
+    ap.add_argument("--slots", type=int, default=8, help="c5: concurrent requests at most")
+    ap.add_argument("--m-hi", type=int, default=500000, help="c5: largest request size m")
     return ap.parse_args()
 
 
@@ -349,6 +357,164 @@ def run_ours(args, ws, rank, local):
     return out
 
 
+# --------------------------------------------------------------------------- secondary workloads
+
+def _device_arrays(prob, dev):
+    import numpy as np
+    import torch
+
+    A = prob.A
+    return [torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in (A.rowptr, A.col, A.val, prob.theta)]
+
+
+def run_c3(args, local):
+    """BBD + GMRES(30) on the augmented block-angular KKT system: setup, the
+    factor split (block ILU(0) + filter, Schur assembly, dense LU), and
+    GMRES until 1e-8 or the iteration cap (the status is reported)."""
+    import torch
+
+    from paper_2604_23979_gb300 import build as pbuild
+    from paper_2604_23979_gb300 import sdsl
+    from paper_2604_23979_gb300 import workloads as W
+
+    pbuild.build()
+    sdsl.load()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    prob = W.config3(scale=args.scale)
+    arrs = _device_arrays(prob, dev)
+    b = torch.from_numpy(prob.b).to(dev)
+    x = torch.zeros_like(b)
+    runs = []
+    for k in range(args.warmup + args.steps):
+        o, keep = sdsl.options_for(prob, factor_prec=args.prec, stream=torch.cuda.current_stream(dev).cuda_stream)
+        if args.maxit:
+            o.maxit = args.maxit
+        h = sdsl.sdsl_setup(o, prob.A.nrows, prob.A.ncols, *arrs)
+        try:
+            sdsl.sdsl_factor(h)
+            fs = sdsl.sdsl_get_stats(h)
+            st = sdsl.sdsl_solve(h, b, x)
+            info = sdsl.sdsl_get_info(h)
+        finally:
+            sdsl.sdsl_free(h)
+        if k >= args.warmup:
+            runs.append((fs, st, info))
+    fs, st, info = runs[-1]
+    ms = [r[0].ms_setup + r[0].ms_factor + r[1].ms_solve for r in runs]
+    return {"workload": "c3", "metric": "time-to-1e-8 rel. residual (or status at the iteration cap)",
+            "unit": "ms", "value": round(statistics.median(ms), 1), "higher_is_better": False,
+            "config": {"workload": f"block-angular KKT, 128 blocks, 2048 linking rows, BBD + GMRES(30)"
+                                   + (f" scaled x{args.scale}" if args.scale != 1.0 else ""),
+                       "n": int(info.n), "nnz_K": int(info.nnz_system), "border": int(info.border),
+                       "factor_prec": args.prec, "maxit": args.maxit or prob.maxit},
+            "status": sdsl.sdsl_status_str_py(st.status), "iters": int(st.iters), "rel_res_true": st.rel_res_true,
+            "ms": {"setup": round(fs.ms_setup, 1), "factor": round(fs.ms_factor, 1),
+                   "schur_assembly": round(fs.ms_schur, 1), "dense_lu": round(fs.ms_dense_lu, 1),
+                   "solve": round(st.ms_solve, 1), "per_gmres_iter": round(st.ms_solve / max(1, st.iters), 3)},
+            "steps": args.steps, "warmup": args.warmup}
+
+
+def run_c4(args, local):
+    """30 consecutive IPM systems from one A with drifting theta: update the
+    system values on the device, solve with the kept preconditioner, rebuild
+    when a solve needs more than 1.5x the first post-build count.  Amortized
+    device ms per IPM step (update + rebuilds + solve), FP64 and FP32 factors."""
+    import torch
+
+    from paper_2604_23979_gb300 import build as pbuild
+    from paper_2604_23979_gb300 import sdsl
+    from paper_2604_23979_gb300 import workloads as W
+
+    pbuild.build()
+    sdsl.load()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    prob, thetas = W.config4(scale=args.scale)
+    A = prob.A
+    arrs = _device_arrays(prob, dev)
+    d_thetas = [torch.from_numpy(t).to(dev) for t in thetas]
+    b = torch.from_numpy(prob.b).to(dev)
+    out = {"workload": "c4", "metric": "amortized ms per IPM step (update + rebuilds + solve)", "unit": "ms",
+           "higher_is_better": False,
+           "config": {"workload": f"staircase {A.nrows}x{A.ncols} 6/col, 256 blocks, 30 IPM steps, reuse ratio 1.5",
+                      "nnz_A": int(A.nnz)}, "forms": {}}
+    for prec in (64, 32):
+        o, keep = sdsl.options_for(prob, factor_prec=prec, stream=torch.cuda.current_stream(dev).cuda_stream)
+        h = sdsl.sdsl_setup(o, A.nrows, A.ncols, *arrs)
+        steps = []
+        try:
+            t0 = time.perf_counter()
+            sdsl.sdsl_factor(h)
+            fs = sdsl.sdsl_get_stats(h)
+            first = fs.ms_setup + fs.ms_factor
+            for k, th in enumerate(d_thetas):
+                upd = 0.0
+                if k > 0:
+                    sdsl.sdsl_update_diag(h, th)
+                    upd = sdsl.sdsl_get_stats(h).ms_update
+                x = torch.zeros_like(b)
+                st = sdsl.sdsl_solve(h, b, x)
+                steps.append(dict(k=k, iters=int(st.iters), status=int(st.status), rebuilt=int(st.rebuilt),
+                                  ms_update=upd, ms_factor=st.ms_factor if st.rebuilt else 0.0, ms_solve=st.ms_solve,
+                                  relres=st.rel_res_true))
+            wall = time.perf_counter() - t0
+        finally:
+            sdsl.sdsl_free(h)
+        total = first + sum(s["ms_update"] + s["ms_factor"] + s["ms_solve"] for s in steps)
+        out["forms"][f"f{prec}"] = {
+            "ms_per_ipm_step": round(total / len(steps), 2), "rebuilds": sum(s["rebuilt"] for s in steps),
+            "setup_factor_ms": round(first, 1), "wall_s": round(wall, 2),
+            "iters": [s["iters"] for s in steps], "unconverged": sum(1 for s in steps if s["status"] != 0),
+            "max_relres": max(s["relres"] for s in steps),
+            "solve_ms_total": round(sum(s["ms_solve"] for s in steps), 1),
+            "update_ms_mean": round(statistics.mean(s["ms_update"] for s in steps[1:]), 3)}
+    out["value"] = out["forms"]["f32"]["ms_per_ipm_step"]
+    return out
+
+
+def run_c5(args, local):
+    """Served stream: Poisson arrivals of independent normal-equations solves
+    (m log-uniform up to --m-hi, 1-10 follow-up diagonal updates each),
+    admitted by free HBM into --slots concurrent streams (FP32 factors), next
+    to a sequential plain-FP64 loop over the same stream."""
+    import numpy as np
+    import torch
+
+    from paper_2604_23979_gb300 import build as pbuild
+    from paper_2604_23979_gb300 import sdsl
+    from paper_2604_23979_gb300 import serve
+    from paper_2604_23979_gb300 import workloads as W
+
+    pbuild.build()
+    sdsl.load()
+    torch.cuda.set_device(local)
+    t0 = time.perf_counter()
+    rng = np.random.default_rng(6)
+    reqs = [W.serving_request(rng, 0.0, 1000, args.m_hi) for _ in range(args.count)]
+    gen_s = time.perf_counter() - t0
+    # warm-up (module load, memory pools) on a few small requests
+    wrng = np.random.default_rng(99)
+    warm = [W.serving_request(wrng, 0.0, 1000, 5000) for _ in range(max(3, args.warmup))]
+    serve.GpuServer(slots=2, factor_prec=32).serve(warm)
+    out = {"workload": "c5", "metric": "served solves/s + p99 latency", "unit": "solves/s",
+           "higher_is_better": True,
+           "config": {"workload": f"Poisson stream of {args.count} normal-equations requests, m log-uniform "
+                                  f"[1k, {args.m_hi}], n = 2.5 m, 5-8/col, blocks ceil(m/4000), 1-10 follow-ups",
+                      "slots": args.slots, "factor_prec": 32, "generation_s": round(gen_s, 1)},
+           "rates": {}}
+    for rate in [float(r) for r in args.rates.split(",")]:
+        arrivals = list(np.cumsum(np.random.default_rng(5).exponential(1.0 / rate, args.count)))
+        _, summ = serve.GpuServer(slots=args.slots, factor_prec=32).serve(reqs, arrivals=arrivals)
+        _, base = serve.serve_sequential(reqs, factor_prec=64, arrivals=arrivals)
+        out["rates"][str(rate)] = {"served": summ, "sequential_fp64": base,
+                                   "speedup_solves_per_s": round(summ["solves_per_s"] / base["solves_per_s"], 2)}
+    first = out["rates"][next(iter(out["rates"]))]
+    out["value"] = first["served"]["solves_per_s"]
+    out["p99_s"] = first["served"]["latency_p99_s"]
+    return out
+
+
 # --------------------------------------------------------------------------- the oracle
 
 def oracle_sample(prob, n_iter=30):
@@ -415,6 +581,12 @@ def main():
     ws, rank, local = dist_init(args)
     if args.impl == "reference":
         out = run_reference(args, ws, rank)
+    elif args.workload == "c3":
+        out = run_c3(args, local) if rank == 0 else None
+    elif args.workload == "c4":
+        out = run_c4(args, local) if rank == 0 else None
+    elif args.workload == "c5":
+        out = run_c5(args, local) if rank == 0 else None
     else:
         out = run_ours(args, ws, rank, local)
     if rank == 0 and out is not None:

@@ -81,6 +81,35 @@ __device__ __forceinline__ int64_t bsearch_i32(const int32_t* __restrict__ a, in
   return -1;
 }
 
+// Allow a kernel the device's whole opt-in dynamic shared memory.  The limit
+// is a property of the function, shared by every handle in the process: it is
+// raised once per device and never lowered, so a launch captured in one
+// handle's CUDA graph stays valid while other handles launch the same kernel
+// with less.  (Occupancy follows the size each launch requests.)
+inline cudaError_t set_max_dynamic_smem(const void* kern) {
+  int dev = 0, optin = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return e;
+  cudaFuncAttributes fa{};
+  e = cudaFuncGetAttributes(&fa, kern);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+}
+
+template <auto Kern>
+cudaError_t allow_max_dynamic_smem() {
+  static int done[64] = {};  // per device; a racing second set is idempotent
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev >= 0 && dev < 64 && done[dev]) return cudaSuccess;
+  e = set_max_dynamic_smem(reinterpret_cast<const void*>(Kern));
+  if (e == cudaSuccess && dev >= 0 && dev < 64) done[dev] = 1;
+  return e;
+}
+
 // First index in sorted a[lo, hi) with a[index] >= key (hi if none).
 __device__ __forceinline__ int64_t lower_bound_i32(const int32_t* __restrict__ a, int64_t lo, int64_t hi,
                                                    int32_t key) {

@@ -628,7 +628,7 @@ cudaError_t launch_update(const TriSolve& M, const double* p, const double* q, d
   const size_t need = (size_t)M.max_block * sizeof(T);
   if (need <= (size_t)200 * 1024) {
     auto kern = k_pcg_update<T, V, true>;
-    SDSL_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need));
+    SDSL_CUDA_TRY((allow_max_dynamic_smem<k_pcg_update<T, V, true>>()));
     kern<<<(unsigned)M.nblocks, kThreads, need, st>>>(M, p, q, x, r, z, pp, part, s, mode); count_launch();
   } else {
     k_pcg_update<T, V, false><<<(unsigned)M.nblocks, kThreads, 0, st>>>(M, p, q, x, r, z, pp, part, s, mode); count_launch();
@@ -641,7 +641,7 @@ cudaError_t launch_update_sf(const TriSolve& M, const double* p, const double* q
                              double* pp, double* part, PcgState* s, int mode, cudaStream_t st) {
   const size_t need = sf_smem_bytes(M.max_block, sizeof(TC));
   auto kern = k_pcg_update_sf<TS, TC, V>;
-  SDSL_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need));
+  SDSL_CUDA_TRY((allow_max_dynamic_smem<k_pcg_update_sf<TS, TC, V>>()));
   kern<<<(unsigned)M.nblocks, M.threads, need, st>>>(M, p, q, x, r, z, pp, part, s, mode); count_launch();
   return cudaGetLastError();
 }

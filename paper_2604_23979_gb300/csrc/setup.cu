@@ -374,10 +374,10 @@ cudaError_t normal_symbolic_long(bool fill, int nlong, const int32_t* long_rows,
   if (nlong == 0) return cudaSuccess;
   const size_t smem = sizeof(int32_t) * kLongCap;
   if (fill) {
-    SDSL_CUDA_TRY(cudaFuncSetAttribute(k_sym_long<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    SDSL_CUDA_TRY((allow_max_dynamic_smem<k_sym_long<true>>()));
     k_sym_long<true><<<nlong, 1024, smem, st>>>(long_rows, rp, ci, trp, tci, srp, sci, err); count_launch();
   } else {
-    SDSL_CUDA_TRY(cudaFuncSetAttribute(k_sym_long<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    SDSL_CUDA_TRY((allow_max_dynamic_smem<k_sym_long<false>>()));
     k_sym_long<false><<<nlong, 1024, smem, st>>>(long_rows, rp, ci, trp, tci, srp, sci, err); count_launch();
   }
   return cudaGetLastError();

@@ -239,7 +239,7 @@ cudaError_t launch_staged(const TriSolve& M, const double* p, const double* q, d
                           double* pp, double* part, PcgState* s, int mode, cudaStream_t st) {
   const size_t need = staged_smem_bytes(M.max_block, sizeof(TC), kSweepWarps, M.slot_bytes, M.slots, M.max_tiles);
   auto kern = k_pcg_update_staged<TS, TC, SLOTS, KREG>;
-  SDSL_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need));
+  SDSL_CUDA_TRY((allow_max_dynamic_smem<k_pcg_update_staged<TS, TC, SLOTS, KREG>>()));
   kern<<<(unsigned)M.nblocks, kSweepWarps * 32, need, st>>>(M, p, q, x, r, z, pp, part, s, mode); count_launch();
   return cudaGetLastError();
 }

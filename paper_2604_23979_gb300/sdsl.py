@@ -237,6 +237,11 @@ def sdsl_precond_apply(h, r, z):
     return _check(load().sdsl_precond_apply(h, _ptr(r)[0], _ptr(z)[0]))
 
 
+def sdsl_status_str_py(status) -> str:
+    """Name of a status code."""
+    return load().sdsl_status_str(int(status)).decode()
+
+
 NOALLOC_MAX_COLS = 1 << 19
 
 
