@@ -90,6 +90,9 @@ typedef struct {
   int sweep_backoff_ns;          /* sleep between unsuccessful readiness polls in those sweeps: -1 auto, 0..1000 */
   int sweep_lane_entries;        /* tile shape of those sweeps: a row gets the fewest lanes (a power of two)
                                     that leave at most this many of its entries per lane; 0 auto, 1..64 */
+  int sweep_wait;                /* readiness in those sweeps: 0 auto, 1 per value (a tile waits until every
+                                    value it reads is solved), 2 per level (a tile waits until the previous
+                                    level of its block is complete, one shared counter per level) */
 } sdsl_options;
 
 typedef struct {

@@ -776,6 +776,7 @@ sdsl_status build_vtiles(sdsl_handle h, bool f32, int apply, bool* ok) {
     std::vector<int32_t> trp{0}, rows;
     std::vector<int8_t> logv;
     std::vector<int64_t> toff{0}, tile_ptr;
+    std::vector<int32_t> meta;  // per tile: level within the block, tiles of the previous level
     int64_t max_bytes = 0;
   } plan[2];
   std::vector<int32_t> lptr[2], lrows[2];
@@ -817,7 +818,9 @@ sdsl_status build_vtiles(sdsl_handle h, bool f32, int apply, bool* ok) {
       int64_t L = 0, tiles = 0;
       for (int64_t k = 0; k < nb; ++k) {
         P.tile_ptr[k] = tiles;
+        int32_t prev_tiles = 0;
         for (int32_t l = 0; l < nl[k]; ++l, ++L) {
+          const int64_t level_first = tiles;
           lev.clear();
           for (int32_t q = lptr[dir][L]; q < lptr[dir][L + 1]; ++q) {
             int lv = 0;
@@ -834,6 +837,8 @@ sdsl_status build_vtiles(sdsl_handle h, bool f32, int apply, bool* ok) {
             P.toff.push_back(P.toff.back() + bytes);
             P.trp.push_back((int32_t)P.rows.size());
             P.max_bytes = std::max(P.max_bytes, bytes);
+            P.meta.push_back(l);
+            P.meta.push_back(prev_tiles);
             ++tiles;
             nr = 0;
             ne = 0;
@@ -850,6 +855,7 @@ sdsl_status build_vtiles(sdsl_handle h, bool f32, int apply, bool* ok) {
             ne += len;
           }
           close();
+          prev_tiles = (int32_t)(tiles - level_first);
         }
       }
       P.tile_ptr[nb] = tiles;
@@ -863,48 +869,55 @@ sdsl_status build_vtiles(sdsl_handle h, bool f32, int apply, bool* ok) {
     return mt;
   };
   const size_t budget = (size_t)225 * 1024;
+  int64_t maxlev = 0;
+  for (int64_t k = 0; k < nb; ++k) maxlev = std::max<int64_t>(maxlev, std::max(h->h_nlev_lo[k], h->h_nlev_up[k]));
   make_plan(INT64_MAX);
   int64_t mt = max_tiles();
   const int64_t big = ((std::max(plan[0].max_bytes, plan[1].max_bytes) + 255) / 256) * 256;
   int slots = 0, slot = 0;
   for (int sl = 4; sl >= 2 && slots == 0; --sl)
-    if (staged_smem_bytes(maxb, tc, kWarps, (int)big, sl, mt) <= budget) { slots = sl; slot = (int)big; }
+    if (staged_smem_bytes(maxb, tc, kWarps, (int)big, sl, mt, maxlev) <= budget) { slots = sl; slot = (int)big; }
   if (slots == 0) {
     // the largest tiles do not fit two slots: cap the tiles at the largest
     // slot that does (the cap raises the tile count, so re-check)
     slots = 2;
-    const size_t fixed = staged_smem_bytes(maxb, tc, kWarps, 0, 0, 2 * mt);
+    const size_t fixed = staged_smem_bytes(maxb, tc, kWarps, 0, 0, 2 * mt, maxlev);
     if (fixed >= budget) return SDSL_OK;
     slot = (int)std::min<int64_t>(((budget - fixed) / ((size_t)kWarps * slots)) & ~(size_t)255, 16384);
     if (slot < 1024) return SDSL_OK;
     make_plan(slot);
     mt = max_tiles();
-    if (staged_smem_bytes(maxb, tc, kWarps, slot, slots, mt) > budget) return SDSL_OK;
+    if (staged_smem_bytes(maxb, tc, kWarps, slot, slots, mt, maxlev) > budget) return SDSL_OK;
   }
   M.slot_bytes = slot;
   M.slots = slots;
   M.max_tiles = mt;
   M.kreg = E <= 8 ? 8 : 16;
+  M.max_levels = (int)maxlev;
+  M.level_wait = h->opt.sweep_wait == 1 ? 0 : 1;  // auto: per-level counters
   for (int dir = 0; dir < 2; ++dir) {
     Plan& P = plan[dir];
     const int64_t ntiles = (int64_t)P.trp.size() - 1;
     int32_t *d_trp, *d_rows;
     int8_t* d_logv;
     int64_t *d_toff, *d_tile;
+    int32_t* d_meta;
     unsigned char* stream;
     TRY(h->pc.get(&d_trp, ntiles + 1));
     TRY(h->pc.get(&d_rows, P.rows.size()));
     TRY(h->pc.get(&d_logv, P.logv.size()));
     TRY(h->pc.get(&d_toff, ntiles + 1));
     TRY(h->pc.get(&d_tile, nb + 1));
+    TRY(tmp.get(&d_meta, P.meta.size()));
     TRY(h->pc.get(&stream, P.toff.back()));
     TRY(to_dev(h, d_trp, P.trp.data(), ntiles + 1));
     TRY(to_dev(h, d_rows, P.rows.data(), P.rows.size()));
     TRY(to_dev(h, d_logv, P.logv.data(), P.logv.size()));
     TRY(to_dev(h, d_toff, P.toff.data(), ntiles + 1));
     TRY(to_dev(h, d_tile, P.tile_ptr.data(), nb + 1));
+    TRY(to_dev(h, d_meta, P.meta.data(), P.meta.size()));
     TRY_CUDA(vt_fill(dir, ntiles, d_trp, d_rows, d_logv, h->row_block, h->d_bp, h->p_rp, h->p_ci, h->p_diag, h->F,
-                     h->dinv, f32 ? 32 : 64, d_toff, stream, h->st));
+                     h->dinv, f32 ? 32 : 64, d_toff, d_meta, stream, h->st));
     if (dir == 0) { M.fwd_stream = stream; M.fwd_toff = d_toff; M.fwd_tile = d_tile; }
     else { M.bwd_stream = stream; M.bwd_toff = d_toff; M.bwd_tile = d_tile; }
   }
@@ -1101,11 +1114,11 @@ sdsl_status factor_impl(sdsl_handle h) {
     }
     M.max_tiles = mt;
   }
-  const bool fits_tma = staged_smem_bytes(maxb, apply == 32 ? 4 : 8, 16, 1024, 2, M.max_tiles) <= (size_t)225 * 1024;
+  const bool fits_tma = staged_smem_bytes(maxb, apply == 32 ? 4 : 8, 16, 1024, 2, M.max_tiles, 0) <= (size_t)225 * 1024;
   if ((h->opt.solve_kernel == 2 && !fits) || (h->opt.solve_kernel == 3 && !fits_tma))
     return fail(SDSL_ERR_ARG, "flag-synchronised solves need the largest block to fit in shared memory");
   M.tma = (h->method == SDSL_BJ_PCG && (h->opt.solve_kernel == 3 || (h->opt.solve_kernel == 0 && fits_tma))) ? 1 : 0;
-  M.sweep_warps = h->opt.sweep_warps > 0 ? h->opt.sweep_warps : 12;
+  M.sweep_warps = h->opt.sweep_warps > 0 ? h->opt.sweep_warps : 16;
   M.backoff_ns = h->opt.sweep_backoff_ns >= 0 ? h->opt.sweep_backoff_ns : 20;
   if (M.tma) {
     bool ok = false;
@@ -1311,6 +1324,7 @@ void sdsl_default_options(sdsl_options* o) {
   o->sweep_warps = 0;
   o->sweep_backoff_ns = -1;
   o->sweep_lane_entries = 0;
+  o->sweep_wait = 0;
 }
 
 const char* sdsl_status_str(sdsl_status s) {
@@ -1367,6 +1381,7 @@ sdsl_status sdsl_setup(const sdsl_options* opt, int64_t m, int64_t n, const int6
     return fail(SDSL_ERR_ARG, "sweep_backoff_ns must be in -1..1000");
   if (opt->sweep_lane_entries < 0 || opt->sweep_lane_entries > 64)
     return fail(SDSL_ERR_ARG, "sweep_lane_entries must be in 0..64");
+  if (opt->sweep_wait < 0 || opt->sweep_wait > 2) return fail(SDSL_ERR_ARG, "sweep_wait must be in 0..2");
   if (opt->apply_prec != 0 && opt->apply_prec != 64 && opt->apply_prec != 32)
     return fail(SDSL_ERR_ARG, "apply_prec must be 0, 32 or 64");
   if (opt->factor_prec == 64 && opt->apply_prec == 32)

@@ -84,11 +84,12 @@ cudaError_t tile_fill(int dir, int64_t ntiles, int RW, int prec, const int32_t* 
 cudaError_t vt_fill(int dir, int64_t ntiles, const int32_t* tile_rows_ptr, const int32_t* plan_rows,
                     const int8_t* plan_logv, const int32_t* row_block, const int64_t* bp, const int64_t* prp,
                     const int32_t* pci, const int64_t* pdiag, const double* F, const double* dinv, int prec,
-                    const int64_t* toff, unsigned char* stream, cudaStream_t st);
-// Dynamic shared memory of the TMA-staged solve.
+                    const int64_t* toff, const int32_t* tile_meta, unsigned char* stream, cudaStream_t st);
 // Dynamic shared memory of the staged solve kernel (sweep.cu): y in both
-// directions, the warps' tile rings and the block's staged tile offsets.
-size_t staged_smem_bytes(int64_t max_block, size_t tc_size, int warps, int slot_bytes, int slots, int64_t max_tiles);
+// directions, the warps' tile rings, the block's staged tile offsets and
+// its per-level completion counters.
+size_t staged_smem_bytes(int64_t max_block, size_t tc_size, int warps, int slot_bytes, int slots, int64_t max_tiles,
+                         int64_t max_levels);
 
 
 // ---- krylov.cu: SpMV, PCG iteration kernels, residuals
@@ -159,6 +160,8 @@ struct TriSolve {  // block triangular factors on the layout of P
   int tma;              // 1: staged level tiles (cp.async copies into a per-warp shared-memory ring)
   int slot_bytes;       // ring slot size; larger tiles are read from global memory directly
   int kreg;             // entries per lane and gather round of the staged solves (8 or 16)
+  int level_wait;       // staged solves: 1 = per-level completion counters, 0 = per-value readiness
+  int max_levels;       // largest level count of a block (either direction): counters in shared memory
   int64_t max_tiles;    // max over blocks of (forward tiles + backward tiles): staged tile offsets
   int slots;            // ring slots per warp
   int sync_free;        // 1: packed flag-synchronised solves (block fits in shared memory)

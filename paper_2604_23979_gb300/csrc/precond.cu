@@ -535,7 +535,7 @@ __global__ void k_tile_fill(int dir, int64_t ntiles, int RW, const int32_t* __re
 // Variable-width tiles.  A tile holds rows of one level; row r of the tile
 // gets V_r lanes (a power of two, a planned number of entries per lane),
 // groups packed at V-aligned lane offsets.  Layout (16-byte aligned parts):
-//   int32 nr, ne, 0, 0
+//   int32 nr, ne, level of the tile in its block, tiles of the previous level
 //   lane record x 32 (8 bytes each): uint16 row (block-local; 0xFFFF = idle),
 //     uint16 first (index of the lane's first entry in the tile), uint8 count
 //     (entries of the lane, strided by V), uint8 log2 V, uint8 r, uint8 0
@@ -549,7 +549,7 @@ __global__ void k_vt_fill(int dir, int64_t ntiles, const int32_t* __restrict__ t
                           const int64_t* __restrict__ prp, const int32_t* __restrict__ pci,
                           const int64_t* __restrict__ pdiag, const double* __restrict__ F,
                           const double* __restrict__ dinv, const int64_t* __restrict__ toff,
-                          unsigned char* __restrict__ stream) {
+                          const int32_t* __restrict__ tile_meta, unsigned char* __restrict__ stream) {
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < ntiles; t += (int64_t)gridDim.x * blockDim.x) {
     unsigned char* base = stream + toff[t];
     const int r0 = tile_rows_ptr[t], nr = tile_rows_ptr[t + 1] - r0;
@@ -582,8 +582,8 @@ __global__ void k_vt_fill(int dir, int64_t ntiles, const int32_t* __restrict__ t
     }
     hdr[0] = nr;
     hdr[1] = ne;
-    hdr[2] = 0;
-    hdr[3] = 0;
+    hdr[2] = tile_meta ? tile_meta[2 * t] : 0;      // level of the tile within its block
+    hdr[3] = tile_meta ? tile_meta[2 * t + 1] : 0;  // tiles of the block's previous level
     uint16_t* col = reinterpret_cast<uint16_t*>(base + 16 + 256 + r16((int64_t)nr * sizeof(TS)));
     TS* val = reinterpret_cast<TS*>(reinterpret_cast<unsigned char*>(col) + r16(2 * (int64_t)ne));
     int at = 0;
@@ -755,13 +755,13 @@ cudaError_t tile_fill(int dir, int64_t ntiles, int RW, int prec, const int32_t* 
 cudaError_t vt_fill(int dir, int64_t ntiles, const int32_t* tile_rows_ptr, const int32_t* plan_rows,
                     const int8_t* plan_logv, const int32_t* row_block, const int64_t* bp, const int64_t* prp,
                     const int32_t* pci, const int64_t* pdiag, const double* F, const double* dinv, int prec,
-                    const int64_t* toff, unsigned char* stream, cudaStream_t st) {
+                    const int64_t* toff, const int32_t* tile_meta, unsigned char* stream, cudaStream_t st) {
   if (prec == 32) {
     k_vt_fill<float><<<grid_for(ntiles, 128), 128, 0, st>>>(dir, ntiles, tile_rows_ptr, plan_rows, plan_logv,
-                                                            row_block, bp, prp, pci, pdiag, F, dinv, toff, stream); count_launch();
+                                                            row_block, bp, prp, pci, pdiag, F, dinv, toff, tile_meta, stream); count_launch();
   } else {
     k_vt_fill<double><<<grid_for(ntiles, 128), 128, 0, st>>>(dir, ntiles, tile_rows_ptr, plan_rows, plan_logv,
-                                                             row_block, bp, prp, pci, pdiag, F, dinv, toff, stream); count_launch();
+                                                             row_block, bp, prp, pci, pdiag, F, dinv, toff, tile_meta, stream); count_launch();
   }
   return cudaGetLastError();
 }

@@ -48,11 +48,16 @@ __device__ __forceinline__ T segmented_sum(T v, int V, int Vmax) {
 }
 
 // One sweep of a block.  `in` holds the right-hand side, `out` the solution
-// (sentinel until solved).  Only warps w < W take tiles.
+// (sentinel until solved).  Only warps w < W take tiles.  Readiness is per
+// value (`done` null: a tile waits until no value it reads is the sentinel)
+// or per level (a tile waits until every tile of the previous level has
+// counted itself in done[level - 1]; since each of those waited for its own
+// previous level, every lower level is then complete too).
 template <typename TS, typename TC, int SLOTS, int KREG>
 __device__ __forceinline__ void sweep_staged(const unsigned char* __restrict__ stream, const int64_t* toff_s,
                                              int ntile, unsigned char* ring, int slot_bytes, volatile TC* in,
-                                             volatile TC* out, bool unit, int* timeout, int W, unsigned backoff) {
+                                             volatile TC* out, bool unit, int* timeout, int W, unsigned backoff,
+                                             int* done) {
   const int lane = lane_id(), w = threadIdx.x >> 5;
   if (w >= W) return;
   const int nk = ntile > w ? (ntile - w + W - 1) / W : 0;  // tiles of this warp
@@ -87,6 +92,8 @@ __device__ __forceinline__ void sweep_staged(const unsigned char* __restrict__ s
     const unsigned char* base = bytes <= slot_bytes ? ring + (k % SLOTS) * slot_bytes : stream + a;
     const int nr = reinterpret_cast<const int32_t*>(base)[0];
     const int ne = reinterpret_cast<const int32_t*>(base)[1];
+    const int level = reinterpret_cast<const int32_t*>(base)[2];
+    const int need = reinterpret_cast<const int32_t*>(base)[3];
     const uint2 rec = reinterpret_cast<const uint2*>(base + 16)[lane];  // this lane's role, one load
     const int row = (int)(rec.x & 0xFFFFu);
     const int first = (int)(rec.x >> 16);
@@ -121,6 +128,26 @@ __device__ __forceinline__ void sweep_staged(const unsigned char* __restrict__ s
         jj[k2] = ok ? (int)cols[e] : -1;
         vv[k2] = ok ? (TC)vals[e] : TC(0);
       }
+      if (done) {
+        if (c == 0 && level > 0) {
+          // every lane polls the same counter (a broadcast load): warp-uniform
+          volatile int* cnt = done + level - 1;
+          int spins = 0;
+          while (*cnt < need) {
+            if (backoff) __nanosleep(backoff);
+            if (++spins > kSpinLimit / 8) { *timeout = 1; break; }
+          }
+          __threadfence_block();  // order the value loads after the counter
+        }
+#pragma unroll
+        for (int k2 = 0; k2 < KREG; ++k2) xv[k2] = jj[k2] >= 0 ? (TC)out[jj[k2]] : TC(0);
+#pragma unroll
+        for (int k2 = 0; k2 < KREG; k2 += 2) {
+          acc = fma(vv[k2], xv[k2], acc);
+          acc2 = fma(vv[k2 + 1], xv[k2 + 1], acc2);
+        }
+        continue;
+      }
       bool ready = true;
 #pragma unroll
       for (int k2 = 0; k2 < KREG; ++k2) {
@@ -153,6 +180,10 @@ __device__ __forceinline__ void sweep_staged(const unsigned char* __restrict__ s
     acc = segmented_sum(acc + acc2, V, Vmax);
     if (leader) out[row] = (inr - acc) * dvr;
     __syncwarp();  // the slot of tile k-1 is free: refill it with tile k+SLOTS-1
+    if (done && lane == 0) {
+      __threadfence_block();  // the tile's values before its count
+      atomicAdd(done + level, 1);
+    }
     issue(k + SLOTS - 1);
   }
   cp_async_wait<0>();
@@ -189,8 +220,11 @@ __global__ void __launch_bounds__(kSweepWarps * 32) k_pcg_update_staged(TriSolve
   const int64_t tb0 = M.bwd_tile[b];
   const int ntb = (int)(M.bwd_tile[b + 1] - tb0);
   int64_t* toff_b = toff_f + ntf + 1;
+  int* done = M.level_wait ? reinterpret_cast<int*>(toff_f + M.max_tiles + 2) : nullptr;
   for (int t = threadIdx.x; t <= ntf; t += blockDim.x) toff_f[t] = M.fwd_toff[tf0 + t];
   for (int t = threadIdx.x; t <= ntb; t += blockDim.x) toff_b[t] = M.bwd_toff[tb0 + t];
+  if (done)
+    for (int t = threadIdx.x; t < M.max_levels; t += blockDim.x) done[t] = 0;
   if (threadIdx.x == 0) timeout = 0;
   double rr = 0.0;
   if (mode == 0) {
@@ -214,12 +248,14 @@ __global__ void __launch_bounds__(kSweepWarps * 32) k_pcg_update_staged(TriSolve
   const double rrb = block_sum(rr, sh);
   __syncthreads();
   sweep_staged<TS, TC, SLOTS, KREG>(M.fwd_stream, toff_f, ntf, ring, M.slot_bytes, yb, yf, M.unit_lower != 0,
-                                    &timeout, M.sweep_warps, (unsigned)M.backoff_ns);
+                                    &timeout, M.sweep_warps, (unsigned)M.backoff_ns, done);
   __syncthreads();
   for (int64_t i = threadIdx.x; i < e0 - s0; i += blockDim.x) yb[i] = S;
+  if (done)
+    for (int t = threadIdx.x; t < M.max_levels; t += blockDim.x) done[t] = 0;
   __syncthreads();
   sweep_staged<TS, TC, SLOTS, KREG>(M.bwd_stream, toff_b, ntb, ring, M.slot_bytes, yf, yb, false, &timeout,
-                                    M.sweep_warps, (unsigned)M.backoff_ns);
+                                    M.sweep_warps, (unsigned)M.backoff_ns, done);
   __syncthreads();
   double rz = 0.0, zq = 0.0;
   for (int64_t i = s0 + threadIdx.x; i < e0; i += blockDim.x) {
@@ -237,7 +273,8 @@ __global__ void __launch_bounds__(kSweepWarps * 32) k_pcg_update_staged(TriSolve
 template <typename TS, typename TC, int SLOTS, int KREG>
 cudaError_t launch_staged(const TriSolve& M, const double* p, const double* q, double* x, double* r, double* z,
                           double* pp, double* part, PcgState* s, int mode, cudaStream_t st) {
-  const size_t need = staged_smem_bytes(M.max_block, sizeof(TC), kSweepWarps, M.slot_bytes, M.slots, M.max_tiles);
+  const size_t need = staged_smem_bytes(M.max_block, sizeof(TC), kSweepWarps, M.slot_bytes, M.slots, M.max_tiles,
+                                        M.level_wait ? M.max_levels : 0);
   auto kern = k_pcg_update_staged<TS, TC, SLOTS, KREG>;
   SDSL_CUDA_TRY((allow_max_dynamic_smem<k_pcg_update_staged<TS, TC, SLOTS, KREG>>()));
   kern<<<(unsigned)M.nblocks, kSweepWarps * 32, need, st>>>(M, p, q, x, r, z, pp, part, s, mode); count_launch();
@@ -263,9 +300,10 @@ cudaError_t launch_shape(const TriSolve& M, const double* p, const double* q, do
 
 }  // namespace
 
-size_t staged_smem_bytes(int64_t max_block, size_t tc_size, int warps, int slot_bytes, int slots, int64_t max_tiles) {
+size_t staged_smem_bytes(int64_t max_block, size_t tc_size, int warps, int slot_bytes, int slots, int64_t max_tiles,
+                         int64_t max_levels) {
   return 2 * align128((size_t)max_block * tc_size) + (size_t)warps * slots * (size_t)slot_bytes +
-         (size_t)(max_tiles + 2) * sizeof(int64_t);
+         (size_t)(max_tiles + 2) * sizeof(int64_t) + (size_t)max_levels * sizeof(int);
 }
 
 cudaError_t update_staged(const TriSolve& M, const double* p, const double* q, double* x, double* r, double* z,
