@@ -569,20 +569,59 @@ sdsl_status build_bbd(sdsl_handle h) {
   TRY(h->pc.get(&h->Sinv, m * m));
   TRY(h->pc.get(&h->ipiv, m));
   TRY_CUDA(schur_init(m, h->b0, h->p_rp, h->p_ci, h->p_v, h->SB, h->st));
-  int64_t maxb = 0;
-  for (int64_t k = 0; k < nb; ++k) maxb = std::max(maxb, h->h_bp[k + 1] - h->h_bp[k]);
   Arena tmp;
   tmp.st = h->st;
-  double* X;
   float* work;
-  TRY(tmp.get(&X, (size_t)schur_tiles(m) * maxb * 32));
+  // Waves of blocks assembled at once: every block writes its own dense
+  // contribution, then the wave's contributions are subtracted from S_B in
+  // block order -- the same per-entry order as one block at a time.  A wave
+  // is bounded by the scratch it needs (about a quarter of free memory, at
+  // most 6 GiB of solve scratch) and by 128 blocks.
+  size_t free_b = 0, total_b = 0;
+  TRY_CUDA(cudaMemGetInfo(&free_b, &total_b));
+  const int64_t tiles = schur_tiles(m);
+  const size_t xcap = std::max<size_t>(std::min<size_t>(free_b / 4, (size_t)6 << 30), (size_t)1 << 20);
+  const size_t ccap = std::max<size_t>(free_b / 8, (size_t)m * m * sizeof(double));
+  std::vector<std::vector<SchurJob>> waves(1);
+  size_t xw = 0;
+  int64_t xmax = 0, jmax = 0;
+  for (int64_t k = 0; k < nb; ++k) {
+    const int64_t rows = h->h_bp[k + 1] - h->h_bp[k];
+    const size_t xk = (size_t)tiles * rows * 32 * sizeof(double);
+    auto& w = waves.back();
+    if (!w.empty() && (xw + xk > xcap || w.size() >= 128 || (w.size() + 1) * (size_t)m * m * sizeof(double) > ccap)) {
+      waves.emplace_back();
+      xw = 0;
+    }
+    SchurJob J;
+    J.s = h->h_bp[k];
+    J.e = h->h_bp[k + 1];
+    J.xoff = (int64_t)(xw / sizeof(double));
+    J.L0 = h->h_lev_off_lo[k];
+    J.L1 = h->h_lev_off_lo[k + 1];
+    J.U0 = h->h_lev_off_up[k];
+    J.U1 = h->h_lev_off_up[k + 1];
+    waves.back().push_back(J);
+    xw += xk;
+    xmax = std::max<int64_t>(xmax, (int64_t)(xw / sizeof(double)));
+    jmax = std::max<int64_t>(jmax, (int64_t)waves.back().size());
+  }
+  double *X, *Cpart;
+  SchurJob* d_jobs;
+  TRY(tmp.get(&X, (size_t)std::max<int64_t>(xmax, 1)));
+  TRY(tmp.get(&Cpart, (size_t)jmax * m * m));
+  TRY(tmp.get(&d_jobs, (size_t)nb));
   cudaEvent_t ev[3];
   for (auto& e : ev) TRY_CUDA(cudaEventCreate(&e));
   TRY_CUDA(cudaEventRecord(ev[0], h->st));
-  for (int64_t k = 0; k < nb; ++k)  // blocks in order: deterministic accumulation
-    TRY_CUDA(schur_block(h->h_bp[k], h->h_bp[k + 1], h->b0, m, h->p_rp, h->p_ci, h->p_v, h->F, h->dinv, h->p_diag,
-                         h->h_lev_off_lo[k], h->h_lev_off_lo[k + 1], h->lev_ptr_lo, h->lev_rows_lo,
-                         h->h_lev_off_up[k], h->h_lev_off_up[k + 1], h->lev_ptr_up, h->lev_rows_up, X, h->SB, h->st));
+  int64_t jo = 0;
+  for (const auto& w : waves) {  // waves in block order: deterministic accumulation
+    if (w.empty()) continue;
+    TRY(to_dev(h, d_jobs + jo, w.data(), w.size()));
+    TRY_CUDA(schur_wave((int)w.size(), d_jobs + jo, h->b0, m, h->p_rp, h->p_ci, h->p_v, h->F, h->dinv, h->p_diag,
+                        h->lev_ptr_lo, h->lev_rows_lo, h->lev_ptr_up, h->lev_rows_up, X, Cpart, h->SB, h->st));
+    jo += (int64_t)w.size();
+  }
   TRY_CUDA(cudaEventRecord(ev[1], h->st));
   TRY_CUDA(cudaMemsetAsync(h->flag, 0, sizeof(int), h->st));
   TRY_CUDA(dense_lu_f32(m, h->SB, h->LU32, h->ipiv, h->flag, h->st));

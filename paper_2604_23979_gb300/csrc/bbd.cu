@@ -39,19 +39,23 @@ __global__ void k_schur_init(int64_t nb, int64_t b0, const int64_t* __restrict__
       if (pci[t] >= b0) SB[r * nb + (pci[t] - b0)] = pv[t];
 }
 
-// One CTA per tile of kR border columns [c0, c0+kR) of block k:
-//   X = E_k[:, tile]  ->  X = U_k^{-1} L_k^{-1} X  ->  S_B[:, tile] -= F_k X.
-// X is the block's rows x kR (row-major, one column per lane) in scratch.
-__global__ void k_schur_tile(int64_t s, int64_t e, int64_t b0, int64_t nb, const int64_t* __restrict__ prp,
-                             const int32_t* __restrict__ pci, const double* __restrict__ pv,
-                             const double* __restrict__ F, const double* __restrict__ dinv,
-                             const int64_t* __restrict__ pdiag, int32_t L0, int32_t L1,
+// One CTA per (tile of kR border columns [c0, c0+kR), block k of the wave):
+//   X = E_k[:, tile]  ->  X = U_k^{-1} L_k^{-1} X  ->  C_k[:, tile] = F_k X.
+// X is the block's rows x kR (row-major, one column per lane) in scratch;
+// C_k is the block's own dense nb x nb contribution (subtracted from S_B in
+// block order by k_schur_reduce, the same order as one block at a time).
+__global__ void k_schur_wave(const SchurJob* __restrict__ jobs, int64_t b0, int64_t nb,
+                             const int64_t* __restrict__ prp, const int32_t* __restrict__ pci,
+                             const double* __restrict__ pv, const double* __restrict__ F,
+                             const double* __restrict__ dinv, const int64_t* __restrict__ pdiag,
                              const int32_t* __restrict__ lev_ptr_lo, const int32_t* __restrict__ lev_rows_lo,
-                             int32_t U0, int32_t U1, const int32_t* __restrict__ lev_ptr_up,
-                             const int32_t* __restrict__ lev_rows_up, double* __restrict__ Xall,
-                             double* __restrict__ SB) {
+                             const int32_t* __restrict__ lev_ptr_up, const int32_t* __restrict__ lev_rows_up,
+                             double* __restrict__ Xall, double* __restrict__ Cpart) {
+  const SchurJob J = jobs[blockIdx.y];
+  const int64_t s = J.s, e = J.e;
   const int64_t c0 = (int64_t)blockIdx.x * kR;
-  double* X = Xall + (int64_t)blockIdx.x * (e - s) * kR;
+  double* X = Xall + J.xoff + (int64_t)blockIdx.x * (e - s) * kR;
+  double* C = Cpart + (int64_t)blockIdx.y * nb * nb;
   const int lane = lane_id(), w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int64_t c = c0 + lane;
   // scatter E_k[:, tile]
@@ -65,7 +69,7 @@ __global__ void k_schur_tile(int64_t s, int64_t e, int64_t b0, int64_t nb, const
   }
   __syncthreads();
   // forward, unit lower, level by level
-  for (int32_t L = L0; L < L1; ++L) {
+  for (int32_t L = J.L0; L < J.L1; ++L) {
     for (int32_t q = lev_ptr_lo[L] + w; q < lev_ptr_lo[L + 1]; q += nw) {
       const int64_t i = lev_rows_lo[q];
       double acc = X[(i - s) * kR + lane];
@@ -78,7 +82,7 @@ __global__ void k_schur_tile(int64_t s, int64_t e, int64_t b0, int64_t nb, const
     __syncthreads();
   }
   // backward with U (in-block columns only)
-  for (int32_t L = U0; L < U1; ++L) {
+  for (int32_t L = J.U0; L < J.U1; ++L) {
     for (int32_t q = lev_ptr_up[L] + w; q < lev_ptr_up[L + 1]; q += nw) {
       const int64_t i = lev_rows_up[q];
       double acc = X[(i - s) * kR + lane];
@@ -90,7 +94,7 @@ __global__ void k_schur_tile(int64_t s, int64_t e, int64_t b0, int64_t nb, const
     }
     __syncthreads();
   }
-  // S_B[:, tile] -= F_k X   (border rows, block-k columns).  A border row
+  // C_k[:, tile] = F_k X   (border rows, block-k columns).  A border row
   // spans every block; its columns are sorted, so only the block's range is
   // visited (first in-block entry by binary search).
   for (int64_t r = w; r < nb; r += nw) {
@@ -101,7 +105,17 @@ __global__ void k_schur_tile(int64_t s, int64_t e, int64_t b0, int64_t nb, const
       if (j >= e) break;
       acc = __fma_rn(pv[t], X[(j - s) * kR + lane], acc);
     }
-    if (c < nb) SB[r * nb + c] -= acc;
+    if (c < nb) C[r * nb + c] = acc;
+  }
+}
+
+// S_B -= C_0, C_1, ... in the wave's block order (element-wise).
+__global__ void k_schur_reduce(int64_t nb, int nk, const double* __restrict__ Cpart, double* __restrict__ SB) {
+  const int64_t tot = nb * nb;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < tot; i += (int64_t)gridDim.x * blockDim.x) {
+    double v = SB[i];
+    for (int k = 0; k < nk; ++k) v -= Cpart[(int64_t)k * tot + i];
+    SB[i] = v;
   }
 }
 
@@ -405,15 +419,17 @@ cudaError_t schur_init(int64_t nb, int64_t b0, const int64_t* prp, const int32_t
 
 int64_t schur_tiles(int64_t nb) { return (nb + kR - 1) / kR; }
 
-cudaError_t schur_block(int64_t s, int64_t e, int64_t b0, int64_t nb, const int64_t* prp, const int32_t* pci,
-                        const double* pv, const double* F, const double* dinv, const int64_t* pdiag, int32_t L0,
-                        int32_t L1, const int32_t* lev_ptr_lo, const int32_t* lev_rows_lo, int32_t U0, int32_t U1,
-                        const int32_t* lev_ptr_up, const int32_t* lev_rows_up, double* X, double* SB,
-                        cudaStream_t st) {
-  if (nb == 0 || e <= s) return cudaSuccess;
-  k_schur_tile<<<(unsigned)schur_tiles(nb), 256, 0, st>>>(s, e, b0, nb, prp, pci, pv, F, dinv, pdiag, L0, L1,
-                                                          lev_ptr_lo, lev_rows_lo, U0, U1, lev_ptr_up, lev_rows_up, X,
-                                                          SB); count_launch();
+cudaError_t schur_wave(int njobs, const SchurJob* jobs, int64_t b0, int64_t nb, const int64_t* prp,
+                       const int32_t* pci, const double* pv, const double* F, const double* dinv,
+                       const int64_t* pdiag, const int32_t* lev_ptr_lo, const int32_t* lev_rows_lo,
+                       const int32_t* lev_ptr_up, const int32_t* lev_rows_up, double* X, double* Cpart, double* SB,
+                       cudaStream_t st) {
+  if (njobs == 0 || nb == 0) return cudaSuccess;
+  const dim3 grid((unsigned)schur_tiles(nb), (unsigned)njobs);
+  k_schur_wave<<<grid, 256, 0, st>>>(jobs, b0, nb, prp, pci, pv, F, dinv, pdiag, lev_ptr_lo, lev_rows_lo, lev_ptr_up,
+                                     lev_rows_up, X, Cpart); count_launch();
+  SDSL_CUDA_TRY(cudaGetLastError());
+  k_schur_reduce<<<grid_for(nb * nb, 256), 256, 0, st>>>(nb, njobs, Cpart, SB); count_launch();
   return cudaGetLastError();
 }
 

@@ -250,12 +250,19 @@ cudaError_t pcg_init_state(PcgState* s, double tol2, long long maxit, cudaStream
 cudaError_t schur_init(int64_t nb, int64_t b0, const int64_t* prp, const int32_t* pci, const double* pv, double* SB,
                        cudaStream_t st);
 int64_t schur_tiles(int64_t nb);
-// S_B -= F_k (L_k U_k)^{-1} E_k for block [s, e); X: schur_tiles(nb) * (e-s) * 32 doubles.
-cudaError_t schur_block(int64_t s, int64_t e, int64_t b0, int64_t nb, const int64_t* prp, const int32_t* pci,
-                        const double* pv, const double* F, const double* dinv, const int64_t* pdiag, int32_t L0,
-                        int32_t L1, const int32_t* lev_ptr_lo, const int32_t* lev_rows_lo, int32_t U0, int32_t U1,
-                        const int32_t* lev_ptr_up, const int32_t* lev_rows_up, double* X, double* SB,
-                        cudaStream_t st);
+// One interior block of a Schur wave: rows [s, e), its scratch at X + xoff
+// (schur_tiles(nb) * (e - s) * 32 doubles), its level ranges.
+struct SchurJob {
+  int64_t s, e, xoff;
+  int32_t L0, L1, U0, U1;
+};
+// S_B -= F_k (L_k U_k)^{-1} E_k for the njobs blocks of a wave (all at once;
+// Cpart: njobs * nb * nb doubles), subtracted from S_B in the jobs' order.
+cudaError_t schur_wave(int njobs, const SchurJob* jobs, int64_t b0, int64_t nb, const int64_t* prp,
+                       const int32_t* pci, const double* pv, const double* F, const double* dinv,
+                       const int64_t* pdiag, const int32_t* lev_ptr_lo, const int32_t* lev_rows_lo,
+                       const int32_t* lev_ptr_up, const int32_t* lev_rows_up, double* X, double* Cpart, double* SB,
+                       cudaStream_t st);
 // FP32 LU with partial pivoting of the FP64 matrix SB (status = 1 on a zero pivot).
 cudaError_t dense_lu_f32(int64_t n, const double* SB, float* LU, int32_t* ipiv, int* status, cudaStream_t st);
 // Explicit inverse from the LU factors; work: n*n floats.
