@@ -55,6 +55,8 @@ def parse():
                     help="c2: the headline Block-Jacobi solve (default); c3: BBD GMRES(30) on the block-angular "
                          "KKT system; c4: 30-step IPM sequence with preconditioner reuse; c5: served stream")
     ap.add_argument("--maxit", type=int, default=0, help="c3: cap on GMRES iterations (0: the workload's)")
+    ap.add_argument("--schur-lu", type=int, default=0, help="c3: 0 tensor-core blocked LU, 1 CUDA-core blocked, "
+                                                             "2 unblocked")
     ap.add_argument("--count", type=int, default=200, help="c5: requests in the stream")
     ap.add_argument("--rates", default="200", help="c5: comma-separated Poisson rates (requests/s) to sweep")
     ap.add_argument("--slots", type=int, default=8, help="c5: concurrent requests at most")
@@ -392,6 +394,7 @@ def run_c3(args, local):
         o, keep = sdsl.options_for(prob, factor_prec=args.prec, stream=torch.cuda.current_stream(dev).cuda_stream)
         if args.maxit:
             o.maxit = args.maxit
+        o.schur_lu = args.schur_lu
         h = sdsl.sdsl_setup(o, prob.A.nrows, prob.A.ncols, *arrs)
         try:
             sdsl.sdsl_factor(h)
@@ -413,6 +416,7 @@ def run_c3(args, local):
             "status": sdsl.sdsl_status_str_py(st.status), "iters": int(st.iters), "rel_res_true": st.rel_res_true,
             "ms": {"setup": round(fs.ms_setup, 1), "factor": round(fs.ms_factor, 1),
                    "schur_assembly": round(fs.ms_schur, 1), "dense_lu": round(fs.ms_dense_lu, 1),
+                   "dense_inverse": round(fs.ms_dense_inverse, 1),
                    "solve": round(st.ms_solve, 1), "per_gmres_iter": round(st.ms_solve / max(1, st.iters), 3)},
             "steps": args.steps, "warmup": args.warmup}
 

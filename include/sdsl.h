@@ -90,6 +90,8 @@ typedef struct {
   int sweep_backoff_ns;          /* sleep between unsuccessful readiness polls in those sweeps: -1 auto, 0..1000 */
   int sweep_lane_entries;        /* tile shape of those sweeps: a row gets the fewest lanes (a power of two)
                                     that leave at most this many of its entries per lane; 0 auto, 1..64 */
+  int schur_lu;                  /* BBD border Schur LU: 0 auto (blocked, trailing update on tensor cores),
+                                    1 blocked on CUDA cores, 2 unblocked (one column per step) */
   int sweep_wait;                /* readiness in those sweeps: 0 auto, 1 per value (a tile waits until every
                                     value it reads is solved), 2 per level (a tile waits until the previous
                                     level of its block is complete, one shared counter per level) */
@@ -122,7 +124,8 @@ typedef struct {
   int64_t product_lanes[2]; /* factored normal-equation product: lanes per row of A^T p and of A u
                                (0 when the explicit S is used) */
   double ms_schur;        /* BBD: device time of the border Schur complement assembly (part of ms_factor) */
-  double ms_dense_lu;     /* BBD: device time of its dense LU and FP32 inverse (part of ms_factor) */
+  double ms_dense_lu;     /* BBD: device time of its dense FP32 LU (part of ms_factor) */
+  double ms_dense_inverse; /* BBD: device time of the explicit FP32 inverse from that LU (part of ms_factor) */
 } sdsl_stats;
 
 typedef struct {

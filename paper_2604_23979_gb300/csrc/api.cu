@@ -611,7 +611,7 @@ sdsl_status build_bbd(sdsl_handle h) {
   TRY(tmp.get(&X, (size_t)std::max<int64_t>(xmax, 1)));
   TRY(tmp.get(&Cpart, (size_t)jmax * m * m));
   TRY(tmp.get(&d_jobs, (size_t)nb));
-  cudaEvent_t ev[3];
+  cudaEvent_t ev[4];
   for (auto& e : ev) TRY_CUDA(cudaEventCreate(&e));
   TRY_CUDA(cudaEventRecord(ev[0], h->st));
   int64_t jo = 0;
@@ -624,20 +624,24 @@ sdsl_status build_bbd(sdsl_handle h) {
   }
   TRY_CUDA(cudaEventRecord(ev[1], h->st));
   TRY_CUDA(cudaMemsetAsync(h->flag, 0, sizeof(int), h->st));
-  TRY_CUDA(dense_lu_f32(m, h->SB, h->LU32, h->ipiv, h->flag, h->st));
-  TRY(tmp.get(&work, (size_t)m * ((m + 31) / 32) * 32));
-  TRY_CUDA(dense_lu_inverse(m, h->LU32, h->ipiv, h->Sinv, work, h->st));
+  TRY_CUDA(dense_lu_f32(m, h->SB, h->LU32, h->ipiv, h->flag, h->opt.schur_lu, h->st));
   TRY_CUDA(cudaEventRecord(ev[2], h->st));
+  TRY(tmp.get(&work, (size_t)m * ((m + 31) / 32) * 32));
+  TRY_CUDA(dense_lu_inverse(m, h->LU32, h->ipiv, h->Sinv, work, h->opt.schur_lu, h->flag, h->st));
+  TRY_CUDA(cudaEventRecord(ev[3], h->st));
   int bad = 0;
   TRY(to_host(h, &bad, h->flag, 1));
   TRY(sync(h, "schur lu"));
-  float t0 = 0.f, t1 = 0.f;
+  float t0 = 0.f, t1 = 0.f, t2 = 0.f;
   cudaEventElapsedTime(&t0, ev[0], ev[1]);
   cudaEventElapsedTime(&t1, ev[1], ev[2]);
+  cudaEventElapsedTime(&t2, ev[2], ev[3]);
   h->stats.ms_schur = t0;
   h->stats.ms_dense_lu = t1;
+  h->stats.ms_dense_inverse = t2;
   for (auto& e : ev) cudaEventDestroy(e);
   tmp.release();
+  if (bad == 2) return fail(SDSL_ERR_TIMEOUT, "tensor-core update of the border Schur LU did not complete");
   if (bad) return fail(SDSL_ERR_BREAKDOWN, "zero pivot in the LU of the border Schur complement");
   return SDSL_OK;
 }
@@ -1364,6 +1368,7 @@ void sdsl_default_options(sdsl_options* o) {
   o->sweep_backoff_ns = -1;
   o->sweep_lane_entries = 0;
   o->sweep_wait = 0;
+  o->schur_lu = 0;
 }
 
 const char* sdsl_status_str(sdsl_status s) {
@@ -1421,6 +1426,7 @@ sdsl_status sdsl_setup(const sdsl_options* opt, int64_t m, int64_t n, const int6
   if (opt->sweep_lane_entries < 0 || opt->sweep_lane_entries > 64)
     return fail(SDSL_ERR_ARG, "sweep_lane_entries must be in 0..64");
   if (opt->sweep_wait < 0 || opt->sweep_wait > 2) return fail(SDSL_ERR_ARG, "sweep_wait must be in 0..2");
+  if (opt->schur_lu < 0 || opt->schur_lu > 2) return fail(SDSL_ERR_ARG, "schur_lu must be in 0..2");
   if (opt->apply_prec != 0 && opt->apply_prec != 64 && opt->apply_prec != 32)
     return fail(SDSL_ERR_ARG, "apply_prec must be 0, 32 or 64");
   if (opt->factor_prec == 64 && opt->apply_prec == 32)

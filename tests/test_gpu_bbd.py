@@ -97,6 +97,36 @@ def test_bbd_structures_schur_apply(seed, mild):
         sdsl.sdsl_free(h)
 
 
+@pytest.mark.parametrize("schur_lu", [0, 1, 2])
+def test_bbd_border_lu_modes(schur_lu):
+    """A 300-row border: the blocked LU (tensor-core or CUDA-core trailing
+    update, 64-column panels, ragged 128 x 128 tiles) and the unblocked LU
+    all give an FP32 factor good enough for the refined border solve: the
+    BBD apply matches the oracle's exact block-LU apply."""
+    p = kkt(seed=11, scale=0.01, nblocks=3, nlink=300, link_frac=0.05)
+    ref = oracle_bbd(p)
+    h, keep = gpu_setup(p, schur_lu=schur_lu)
+    try:
+        sdsl.sdsl_factor(h)
+        kbp = ref["kbp"]
+        n = len(ref["P"].rowptr) - 1
+        nb = n - kbp[-1]
+        assert nb == 300
+        SB = np.zeros(nb * nb)
+        assert sdsl.load().sdsl_export_schur(h, SB.ctypes.data) == 0
+        assert rel(SB.reshape(nb, nb), ref["SB"]) <= 1e-10
+        import torch
+        for k in range(2):
+            r = np.random.default_rng(100 + k).standard_normal(n)
+            rd, zd = torch.from_numpy(r).cuda(), torch.zeros(n, dtype=torch.float64, device="cuda")
+            sdsl.sdsl_precond_apply(h, rd, zd)
+            torch.cuda.synchronize()
+            zr = oracle.bbd_apply(ref["P"], ref["F"], kbp, ref["lu"], ref["ipiv"], r)
+            assert rel(zd.cpu().numpy(), zr) <= 1e-8
+    finally:
+        sdsl.sdsl_free(h)
+
+
 @pytest.mark.parametrize("seed", [5, 3])
 def test_bbd_gmres_matches_oracle(seed):
     p = kkt(seed=seed)
