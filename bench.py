@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--sweep-warps", type=int, default=0, help="warps per block in the staged sweeps (0 auto)")
     ap.add_argument("--backoff-ns", type=int, default=-1, help="poll backoff of the staged sweeps (-1 auto)")
     ap.add_argument("--lane-entries", type=int, default=0, help="entries per lane of the sweep tiles (0 auto)")
+    ap.add_argument("--spmv-form", type=int, default=0, help="PCG product: 0 auto, 1 explicit S, 2 factored CSR, "
+                                                              "3 factored sliced ELL")
     ap.add_argument("--sweep-wait", type=int, default=0, help="staged sweeps: 0 auto, 1 per value, 2 per level")
     ap.add_argument("--tune", type=int, default=0, help="1: autotune the product kernels' lane widths at factor time")
     ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5"],
@@ -229,6 +231,7 @@ def run_ours(args, ws, rank, local):
         o.sweep_lane_entries = args.lane_entries
         o.tune = args.tune
         o.sweep_wait = args.sweep_wait
+        o.spmv_form = args.spmv_form
         arrs = arrays if arrays is not None else (d_rp, d_ci, d_v, d_th)
         h = sdsl.sdsl_setup(o, A.nrows, A.ncols, *arrs)
         try:

@@ -83,8 +83,9 @@ typedef struct {
                                     level), 2 flag-synchronised (rows in level order, per-row ready flags
                                     in shared memory; needs the block to fit in shared memory), 3 as 2
                                     with level tiles staged into shared memory by TMA bulk copies */
-  int spmv_form;                 /* PCG product S p (normal form): 0 auto (fewer HBM bytes), 1 explicit
-                                    CSR of S, 2 factored A (theta o (A^T p)) + rho p */
+  int spmv_form;                 /* PCG product S p (normal form): 0 auto (fewer HBM bytes; sliced ELL copies
+                                    of A and A^T when their padding is small), 1 explicit CSR of S,
+                                    2 factored A (theta o (A^T p)) + rho p on CSR, 3 factored on sliced ELL */
   int orthog;                    /* GMRES orthogonalization: 0 modified Gram-Schmidt, 1 classical twice */
   int sweep_warps;               /* warps per block that run the staged triangular sweeps: 0 auto, 1..16 */
   int sweep_backoff_ns;          /* sleep between unsuccessful readiness polls in those sweeps: -1 auto, 0..1000 */
@@ -122,7 +123,7 @@ typedef struct {
   int64_t solve_lanes;    /* lanes per row of the block triangular solves in use */
   int64_t tuned_spmv_lanes; /* explicit-S SpMV lanes chosen by the autotuner (0 if it did not run) */
   int64_t product_lanes[2]; /* factored normal-equation product: lanes per row of A^T p and of A u
-                               (0 when the explicit S is used) */
+                               on CSR, -1 on the sliced ELL copies (0 when the explicit S is used) */
   double ms_schur;        /* BBD: device time of the border Schur complement assembly (part of ms_factor) */
   double ms_dense_lu;     /* BBD: device time of its dense FP32 LU (part of ms_factor) */
   double ms_dense_inverse; /* BBD: device time of the explicit FP32 inverse from that LU (part of ms_factor) */

@@ -110,6 +110,9 @@ struct sdsl_handle_s {
   long long graph_kernels = 0;     // kernels in one launch of the iteration graph
   // rows of the system matrix longer than long_thr (summed by one CTA each)
   bool long_planned = false;
+  // sliced ELL copies of A and A^T (normal form): built once per handle
+  bool sell_planned = false, sell_ok = false;
+  SellMat a_sell{}, at_sell{};
   int long_thr = 0;
   int64_t n_long = 0;
   int32_t* long_rows = nullptr;
@@ -380,7 +383,14 @@ void choose_spmv_plan(sdsl_handle h) {
   const int form = h->opt.spmv_form;
   const bool can = h->form == SDSL_FORM_NORMAL && h->method == SDSL_BJ_PCG;
   const bool fewer = 2.0 * (double)h->a_nnz < (double)h->s_nnz;
-  h->A.factored = can && (form == 2 || (form == 0 && fewer)) ? 1 : 0;
+  h->A.factored = can && (form == 2 || form == 3 || (form == 0 && fewer)) ? 1 : 0;
+  h->A.sell = h->A.factored && h->sell_ok && (form == 3 || form == 0) ? 1 : 0;
+  if (h->A.sell) {
+    h->A.a_sell = h->a_sell;
+    h->A.at_sell = h->at_sell;
+    h->A.sell_at_grid = sell_grid_for(h->at_sell.nslices, h->sms * std::min(sell_occupancy(0), 8));
+    h->A.sell_a_grid = sell_grid_for(h->a_sell.nslices, h->sms * std::min(sell_occupancy(1), 8));
+  }
   if (h->A.factored) {
     h->A.ncols = h->n;
     h->A.a_rp = h->a_rp; h->A.a_ci = h->a_ci; h->A.a_v = h->a_v;
@@ -500,6 +510,59 @@ sdsl_status plan_long_rows(sdsl_handle h) {
     TRY(to_dev(h, h->long_rows, rows.data(), h->n_long));
   }
   h->long_planned = true;
+  return SDSL_OK;
+}
+
+// SELL-32 copy of one CSR matrix; *ok = false (nothing kept) when padding
+// would add more than 30 % to its entries.
+sdsl_status build_sell(sdsl_handle h, int64_t nrows, const int64_t* rp, const int32_t* ci, const double* v,
+                       int64_t nnz, SellMat* S, bool* ok) {
+  *ok = false;
+  const int64_t ns = (nrows + 31) / 32;
+  int32_t *perm, *wid;
+  int64_t* off;
+  TRY(h->sys.get(&perm, std::max<int64_t>(ns * 32, 1)));
+  TRY(h->sys.get(&wid, std::max<int64_t>(ns, 1)));
+  TRY(h->sys.get(&off, ns + 1));
+  Arena tmp;
+  tmp.st = h->st;
+  struct Release {
+    Arena& a;
+    ~Release() { a.release(); }
+  } release_tmp{tmp};
+  int64_t* scratch;
+  TRY(tmp.get(&scratch, scan_scratch_elems(ns) + 1));
+  TRY_CUDA(sell_rank_widths(nrows, rp, perm, wid, off, h->st));
+  TRY_CUDA(exclusive_scan_i64(off, ns, scratch, h->st));
+  int64_t total = 0;
+  TRY(to_host(h, &total, off + ns, 1));
+  TRY(sync(h, "sell widths"));
+  if ((double)total > 1.3 * (double)nnz + 32.0 * 64.0) return SDSL_OK;
+  int32_t* col;
+  double* val;
+  TRY(h->sys.get(&col, std::max<int64_t>(total, 1)));
+  TRY(h->sys.get(&val, std::max<int64_t>(total, 1)));
+  TRY_CUDA(sell_fill(nrows, rp, ci, v, perm, off, wid, col, val, h->st));
+  S->nrows = nrows;
+  S->nslices = ns;
+  S->perm = perm;
+  S->off = off;
+  S->wid = wid;
+  S->col = col;
+  S->val = val;
+  *ok = true;
+  return SDSL_OK;
+}
+
+sdsl_status plan_sell(sdsl_handle h) {
+  if (h->sell_planned) return SDSL_OK;
+  h->sell_planned = true;
+  if (h->form != SDSL_FORM_NORMAL || h->method != SDSL_BJ_PCG) return SDSL_OK;
+  if (h->opt.spmv_form == 1 || h->opt.spmv_form == 2) return SDSL_OK;
+  bool ok_a = false, ok_at = false;
+  TRY(build_sell(h, h->m, h->a_rp, h->a_ci, h->a_v, h->a_nnz, &h->a_sell, &ok_a));
+  if (ok_a) TRY(build_sell(h, h->n, h->at_rp, h->at_ci, h->at_v, h->a_nnz, &h->at_sell, &ok_at));
+  h->sell_ok = ok_a && ok_at;
   return SDSL_OK;
 }
 
@@ -1223,6 +1286,7 @@ sdsl_status factor_impl(sdsl_handle h) {
     }
   }
   TRY(plan_long_rows(h));
+  TRY(plan_sell(h));
   choose_spmv_plan(h);
   if (h->opt.tune) TRY(tune_spmv(h));
   if (h->method == SDSL_BJ_PCG && !h->opt.profile) TRY(build_graph(h));
@@ -1235,8 +1299,8 @@ sdsl_status factor_impl(sdsl_handle h) {
   h->stats.nnz_precond = h->p_nnz;
   h->stats.nnz_factor = h->method == SDSL_BBD_GMRES ? h->p_nnz : (h->p_nnz + N) / 2;
   h->stats.spmv_lanes = h->A.lanes;
-  h->stats.product_lanes[0] = h->A.factored ? h->A.at_lanes : 0;
-  h->stats.product_lanes[1] = h->A.factored ? h->A.a_lanes : 0;
+  h->stats.product_lanes[0] = h->A.factored ? (h->A.sell ? -1 : h->A.at_lanes) : 0;
+  h->stats.product_lanes[1] = h->A.factored ? (h->A.sell ? -1 : h->A.a_lanes) : 0;
   h->stats.solve_lanes = h->M.lanes;
   h->stats.levels_lower = h->tot_lo;
   h->stats.levels_upper = h->tot_up;
@@ -1418,7 +1482,7 @@ sdsl_status sdsl_setup(const sdsl_options* opt, int64_t m, int64_t n, const int6
   if (opt->method != SDSL_BJ_PCG && opt->method != SDSL_BBD_GMRES) return fail(SDSL_ERR_ARG, "unknown method");
   if (opt->factor_prec != 64 && opt->factor_prec != 32) return fail(SDSL_ERR_ARG, "factor_prec must be 64 or 32");
   if (opt->solve_kernel < 0 || opt->solve_kernel > 3) return fail(SDSL_ERR_ARG, "solve_kernel must be 0..3");
-  if (opt->spmv_form < 0 || opt->spmv_form > 2) return fail(SDSL_ERR_ARG, "spmv_form must be 0, 1 or 2");
+  if (opt->spmv_form < 0 || opt->spmv_form > 3) return fail(SDSL_ERR_ARG, "spmv_form must be in 0..3");
   if (opt->orthog < 0 || opt->orthog > 1) return fail(SDSL_ERR_ARG, "orthog must be 0 or 1");
   if (opt->sweep_warps < 0 || opt->sweep_warps > 16) return fail(SDSL_ERR_ARG, "sweep_warps must be in 0..16");
   if (opt->sweep_backoff_ns < -1 || opt->sweep_backoff_ns > 1000)

@@ -187,6 +187,17 @@ cudaError_t pack_fill(int dir, int64_t npos, const int32_t* row_block, const int
                       const double* dinv, int prec, const int64_t* off, int32_t* col, void* val, void* pdinv,
                       int32_t* prow, cudaStream_t st);
 
+// Sliced ELL copy of a CSR matrix (sell.cu): ranked rows perm, per slice of
+// 32 ranked rows its width and its offset into col/val (slot-major).
+struct SellMat {
+  int64_t nrows, nslices;
+  const int32_t* perm;
+  const int64_t* off;
+  const int32_t* wid;
+  const int32_t* col;
+  const double* val;
+};
+
 struct SpmvPlan {
   int64_t n;
   const int64_t* rp;
@@ -211,7 +222,23 @@ struct SpmvPlan {
   int64_t n_long;
   const int32_t* long_rows; // ascending
   double* long_ax;          // n_long values of the last product
+  // factored product on sliced ELL copies of A and A^T
+  int sell;
+  SellMat a_sell, at_sell;
+  unsigned sell_a_grid, sell_at_grid;
 };
+
+// SELL-32 construction (sell.cu): rank rows within windows and compute the
+// slice widths (cnt = width x 32, to be scanned into offsets), then fill.
+cudaError_t sell_rank_widths(int64_t nrows, const int64_t* rp, int32_t* perm, int32_t* wid, int64_t* cnt,
+                             cudaStream_t st);
+cudaError_t sell_fill(int64_t nrows, const int64_t* rp, const int32_t* ci, const double* v, const int32_t* perm,
+                      const int64_t* off, const int32_t* wid, int32_t* col, double* val, cudaStream_t st);
+// Factored normal-equation product on the SELL copies (pcg: partial p^T q, alpha).
+cudaError_t sell_factored_product(const SpmvPlan& A, const double* p, double* q, double* part, PcgState* s, int pcg,
+                                  cudaStream_t st);
+int sell_occupancy(int which);
+unsigned sell_grid_for(int64_t nslices, int max_ctas);
 
 cudaError_t spmv(const SpmvPlan& A, const double* x, double* y, cudaStream_t st);
 cudaError_t time_spmv(const SpmvPlan& A, const double* x, double* y, int reps, float* ms, cudaStream_t st);

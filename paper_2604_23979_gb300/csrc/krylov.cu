@@ -708,6 +708,7 @@ cudaError_t time_spmv(const SpmvPlan& A, const double* x, double* y, int reps, f
 
 cudaError_t factored_product(const SpmvPlan& A, const double* p, double* q, double* part, PcgState* s, int pcg,
                              cudaStream_t st) {
+  if (A.sell) return sell_factored_product(A, p, q, part, s, pcg, st);
   SDSL_CUDA_TRY(by_lanes(A.at_lanes, [&](auto V) -> cudaError_t {
     k_at_theta<decltype(V)::value><<<A.at_grid, kThreads, 0, st>>>(A.ncols, A.at_rp, A.at_ci, A.at_v, A.theta, p, A.u,
                                                                    pcg ? s : nullptr); count_launch();

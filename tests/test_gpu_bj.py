@@ -113,7 +113,7 @@ def test_staged_readiness_modes_agree(prec):
         check_solution(prob, ref_state, ref, g2)
 
 
-@pytest.mark.parametrize("form", [1, 2])
+@pytest.mark.parametrize("form", [1, 2, 3])
 def test_explicit_and_factored_products(form):
     """The PCG product with the explicit CSR of S and in the factored form
     A (theta o (A^T p)) + rho p are the same operator: both reach the oracle's
