@@ -171,10 +171,18 @@ class ClockSampler:
         return out
 
 
-def source_hash():
+# Source files that define each timed kernel (the DRAM traffic recorded in
+# profiles/traffic.json is valid only while these files are unchanged).
+KERNEL_SOURCES = {
+    "k_pcg_update": ["sweep.cu", "pcg_common.cuh", "common.cuh", "kernels.cuh"],
+    "k_pcg_spmv": ["sell.cu", "krylov.cu", "pcg_common.cuh", "common.cuh", "kernels.cuh"],
+}
+
+
+def source_hash(kernel):
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2604_23979_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
+    for f in KERNEL_SOURCES.get(kernel, sorted(os.listdir(d))):
         h.update(open(os.path.join(d, f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -194,7 +202,7 @@ def ncu_traffic(kernel):
     except (OSError, ValueError):
         return None
     e = t.get(kernel)
-    if not e or e.get("source_hash") != source_hash():
+    if not e or e.get("source_hash") != source_hash(kernel):
         return None
     return e.get("dram_bytes_per_launch")
 

@@ -1225,7 +1225,7 @@ sdsl_status factor_impl(sdsl_handle h) {
     return fail(SDSL_ERR_ARG, "flag-synchronised solves need the largest block to fit in shared memory");
   M.tma = (h->method == SDSL_BJ_PCG && (h->opt.solve_kernel == 3 || (h->opt.solve_kernel == 0 && fits_tma))) ? 1 : 0;
   M.sweep_warps = h->opt.sweep_warps > 0 ? h->opt.sweep_warps : 16;
-  M.backoff_ns = h->opt.sweep_backoff_ns >= 0 ? h->opt.sweep_backoff_ns : 20;
+  M.backoff_ns = h->opt.sweep_backoff_ns >= 0 ? h->opt.sweep_backoff_ns : 0;
   if (M.tma) {
     bool ok = false;
     TRY(build_vtiles(h, f32, apply, &ok));
