@@ -1091,8 +1091,17 @@ sdsl_status factor_impl(sdsl_handle h) {
     TRY(h->pc.get(&d_status, nb * kNS));
     TRY(h->pc.get(&d_choice, nb));
     TRY(to_dev(h, d_alpha, kShifts, kNS));
+    // largest blocks first: their factorizations start in the first wave
+    std::vector<int32_t> order(nb);
+    for (int64_t k = 0; k < nb; ++k) order[k] = (int32_t)k;
+    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+      return h->h_bp[a + 1] - h->h_bp[a] > h->h_bp[b + 1] - h->h_bp[b];
+    });
+    int32_t* d_order;
+    TRY(h->pc.get(&d_order, nb));
+    TRY(to_dev(h, d_order, order.data(), nb));
     TRY_CUDA(ic0_factor_all(nb, h->d_bp, h->p_rp, h->p_ci, h->p_v, h->p_diag, h->lev_off_lo, h->lev_ptr_lo,
-                            h->lev_rows_lo, d_alpha, kNS, h->p_nnz, N, Fall, dinv_all, d_status, h->st));
+                            h->lev_rows_lo, d_alpha, kNS, h->p_nnz, N, Fall, dinv_all, d_status, d_order, h->st));
     std::vector<int32_t> status(nb * kNS), choice(nb);
     TRY(to_host(h, status.data(), d_status, nb * kNS));
     TRY(sync(h, "factor"));

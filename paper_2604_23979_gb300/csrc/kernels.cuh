@@ -60,7 +60,8 @@ cudaError_t level_lists(int64_t nblocks, const int64_t* bp, const int32_t* lev, 
 cudaError_t ic0_factor_all(int64_t nblocks, const int64_t* bp, const int64_t* prp, const int32_t* pci,
                            const double* pv, const int64_t* pdiag, const int32_t* lev_off, const int32_t* level_ptr,
                            const int32_t* level_rows, const double* alpha, int nshift, int64_t nnz, int64_t n,
-                           double* Fall, double* dinv_all, int32_t* status, cudaStream_t st);
+                           double* Fall, double* dinv_all, int32_t* status, const int32_t* order,
+                           cudaStream_t st);
 cudaError_t pick_shift(const int64_t* bp, const int64_t* prp, const int32_t* choice, int64_t nnz, int64_t n,
                        const double* Fall, const double* dinv_all, double* F, double* dinv, const int32_t* rb,
                        int64_t nrows, cudaStream_t st);

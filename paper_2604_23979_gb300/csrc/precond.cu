@@ -258,8 +258,11 @@ __global__ void __launch_bounds__(kIcWarps * 32) k_ic0(const int64_t* __restrict
                       const int64_t* __restrict__ pdiag, const int32_t* __restrict__ lev_off,
                       const int32_t* __restrict__ level_ptr, const int32_t* __restrict__ level_rows,
                       const double* __restrict__ alpha, int nshift, int64_t nnz, int64_t n,
-                      double* __restrict__ Fall, double* __restrict__ dinv_all, int32_t* __restrict__ status) {
-  const int b = blockIdx.x / nshift, sh = blockIdx.x % nshift;
+                      double* __restrict__ Fall, double* __restrict__ dinv_all, int32_t* __restrict__ status,
+                      const int32_t* __restrict__ order) {
+  // blocks in the given order (largest first: the longest factorizations
+  // start in the first wave of CTAs)
+  const int b = order ? order[blockIdx.x / nshift] : (int)(blockIdx.x / nshift), sh = blockIdx.x % nshift;
   double* __restrict__ F = Fall + (int64_t)sh * nnz;
   double* __restrict__ dinv = dinv_all + (int64_t)sh * n;
   const int64_t s = bp[b];
@@ -669,11 +672,12 @@ cudaError_t level_lists(int64_t nblocks, const int64_t* bp, const int32_t* lev, 
 cudaError_t ic0_factor_all(int64_t nblocks, const int64_t* bp, const int64_t* prp, const int32_t* pci,
                            const double* pv, const int64_t* pdiag, const int32_t* lev_off, const int32_t* level_ptr,
                            const int32_t* level_rows, const double* alpha, int nshift, int64_t nnz, int64_t n,
-                           double* Fall, double* dinv_all, int32_t* status, cudaStream_t st) {
+                           double* Fall, double* dinv_all, int32_t* status, const int32_t* order,
+                           cudaStream_t st) {
   if (nblocks == 0) return cudaSuccess;
   k_ic0<<<(unsigned)(nblocks * nshift), kIcWarps * 32, 0, st>>>(bp, prp, pci, pv, pdiag, lev_off, level_ptr,
                                                                level_rows, alpha, nshift, nnz, n, Fall, dinv_all,
-                                                               status); count_launch();
+                                                               status, order); count_launch();
   return cudaGetLastError();
 }
 
