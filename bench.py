@@ -171,11 +171,11 @@ class ClockSampler:
         return out
 
 
-# Source files that define each timed kernel (the DRAM traffic recorded in
-# profiles/traffic.json is valid only while these files are unchanged).
+# Source files holding each timed kernel's device code (the DRAM traffic
+# recorded in profiles/traffic.json is valid only while these are unchanged).
 KERNEL_SOURCES = {
-    "k_pcg_update": ["sweep.cu", "pcg_common.cuh", "common.cuh", "kernels.cuh"],
-    "k_pcg_spmv": ["sell.cu", "krylov.cu", "pcg_common.cuh", "common.cuh", "kernels.cuh"],
+    "k_pcg_update": ["sweep.cu", "pcg_common.cuh", "common.cuh"],
+    "k_pcg_spmv": ["sell.cu", "krylov.cu", "pcg_common.cuh", "common.cuh"],
 }
 
 
