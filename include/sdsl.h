@@ -80,9 +80,10 @@ typedef struct {
   int flexible;                  /* PCG beta: 0 = rho_new/rho, 1 = flexible z_new^T(r_new - r_old)/rho
                                     (robust to an FP32 apply); -1 = 1 iff the apply is FP32 */
   int solve_kernel;              /* block triangular solves: 0 auto, 1 level-synchronous (barrier per
-                                    level), 2 flag-synchronised (rows in level order, per-row ready flags
-                                    in shared memory; needs the block to fit in shared memory), 3 as 2
-                                    with level tiles staged into shared memory by TMA bulk copies */
+                                    level), 2 flag-synchronised (rows in level order, readiness of every
+                                    value in shared memory; needs the block to fit in shared memory),
+                                    3 staged: level tiles copied into shared memory ahead of use
+                                    (cp.async) by 16 warps per block (blocks of at most 65,535 rows) */
   int spmv_form;                 /* PCG product S p (normal form): 0 auto (fewer HBM bytes; sliced ELL copies
                                     of A and A^T when their padding is small), 1 explicit CSR of S,
                                     2 factored A (theta o (A^T p)) + rho p on CSR, 3 factored on sliced ELL */

@@ -1240,7 +1240,7 @@ sdsl_status factor_impl(sdsl_handle h) {
     TRY(build_vtiles(h, f32, apply, &ok));
     if (!ok) {
       if (h->opt.solve_kernel == 3)
-        return fail(SDSL_ERR_ARG, "TMA-staged solves need the largest block to fit in shared memory");
+        return fail(SDSL_ERR_ARG, "staged solves need blocks of at most 65,535 rows that fit in shared memory");
       M.tma = 0;
     }
   }

@@ -73,14 +73,6 @@ cudaError_t ilu0_factor(int64_t nblocks, const int64_t* bp, const int64_t* prp, 
 cudaError_t ic0_finish(int64_t n, int64_t nnz, const int64_t* prp, const int64_t* pdiag, const int64_t* mir,
                        double* F, const double* dinv, float* Ff, float* dinvf, cudaStream_t st);
 cudaError_t to_float(int64_t n, const double* a, float* b, cudaStream_t st);
-// Tile streams of the TMA-staged solves (see TriSolve): bytes per tile, then fill.
-cudaError_t tile_count(int dir, int64_t ntiles, int RW, int tsz, const int32_t* sched, const int32_t* row_block,
-                       const int64_t* bp, const int64_t* prp, const int32_t* pci, const int64_t* pdiag,
-                       int64_t* tbytes, cudaStream_t st);
-cudaError_t tile_fill(int dir, int64_t ntiles, int RW, int prec, const int32_t* sched, const int32_t* row_block,
-                      const int64_t* bp, const int64_t* prp, const int32_t* pci, const int64_t* pdiag,
-                      const double* F, const double* dinv, const int64_t* toff, unsigned char* stream,
-                      cudaStream_t st);
 // Variable-width tiles (see precond.cu): fill the stream from a host-built plan.
 cudaError_t vt_fill(int dir, int64_t ntiles, const int32_t* tile_rows_ptr, const int32_t* plan_rows,
                     const int8_t* plan_logv, const int32_t* row_block, const int64_t* bp, const int64_t* prp,
@@ -149,7 +141,7 @@ struct TriSolve {  // block triangular factors on the layout of P
   const int32_t* bwd_row;
   const int64_t* fwd_pos;   // per block: first position of its padded schedule (nblocks+1)
   const int64_t* bwd_pos;
-  // TMA-staged tile streams (solve_kernel 3): tile t of a direction is the
+  // staged tile streams (solve_kernel 3): tile t of a direction is the
   // byte range [toff[t], toff[t+1]) of the stream; block b owns tiles
   // tile_ptr[b] .. tile_ptr[b+1]-1.
   const unsigned char* fwd_stream;

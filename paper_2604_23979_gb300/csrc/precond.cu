@@ -451,12 +451,10 @@ __global__ void k_pack_fill(int dir, int64_t npos, const int32_t* __restrict__ r
   }
 }
 
-// Tile stream for the TMA-staged solves.  Tile t = positions t*RW ..
-// t*RW+RW-1 of the padded level schedule (one level per tile).  Byte layout,
-// every part 16-byte aligned: int32 row[RW] (-1 = padding), int32 len[RW];
-// TS dinv[RW]; int32 col[ne] (block-local); TS val[ne]; rows' entries
-// consecutive in tile order.
+// Byte sizes of the staged tile streams are multiples of 16.
 __host__ __device__ inline int64_t r16(int64_t x) { return (x + 15) & ~(int64_t)15; }
+
+// Strict in-block entries of row i (dir 0: lower, 1: upper) of block [s, e).
 
 __device__ __forceinline__ int strict_count(int dir, int64_t i, int64_t s, int64_t e, const int64_t* prp,
                                             const int32_t* pci, const int64_t* pdiag) {
@@ -467,72 +465,6 @@ __device__ __forceinline__ int strict_count(int dir, int64_t i, int64_t s, int64
     for (int64_t t = pdiag[i] + 1; t < prp[i + 1]; ++t) c += pci[t] < e;
   }
   return c;
-}
-
-__global__ void k_tile_count(int dir, int64_t ntiles, int RW, int tsz, const int32_t* __restrict__ sched,
-                             const int32_t* __restrict__ rb, const int64_t* __restrict__ bp,
-                             const int64_t* __restrict__ prp, const int32_t* __restrict__ pci,
-                             const int64_t* __restrict__ pdiag, int64_t* __restrict__ tbytes) {
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < ntiles; t += (int64_t)gridDim.x * blockDim.x) {
-    int64_t ne = 0;
-    for (int r = 0; r < RW; ++r) {
-      const int64_t i = sched[t * RW + r];
-      if (i < 0) continue;
-      const int32_t b = rb[i];
-      ne += strict_count(dir, i, bp[b], bp[b + 1], prp, pci, pdiag);
-    }
-    tbytes[t] = r16(8 * RW) + r16((int64_t)RW * tsz) + r16(4 * ne) + r16(ne * tsz);
-  }
-}
-
-template <typename TS>
-__global__ void k_tile_fill(int dir, int64_t ntiles, int RW, const int32_t* __restrict__ sched,
-                            const int32_t* __restrict__ rb, const int64_t* __restrict__ bp,
-                            const int64_t* __restrict__ prp, const int32_t* __restrict__ pci,
-                            const int64_t* __restrict__ pdiag, const double* __restrict__ F,
-                            const double* __restrict__ dinv, const int64_t* __restrict__ toff,
-                            unsigned char* __restrict__ stream) {
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < ntiles; t += (int64_t)gridDim.x * blockDim.x) {
-    unsigned char* base = stream + toff[t];
-    int32_t* hrow = reinterpret_cast<int32_t*>(base);
-    int32_t* hlen = hrow + RW;
-    TS* hd = reinterpret_cast<TS*>(base + r16(8 * RW));
-    int64_t ne = 0;
-    for (int r = 0; r < RW; ++r) {
-      const int64_t i = sched[t * RW + r];
-      int c = 0;
-      if (i >= 0) {
-        const int32_t b = rb[i];
-        c = strict_count(dir, i, bp[b], bp[b + 1], prp, pci, pdiag);
-      }
-      hlen[r] = c;
-      ne += c;
-    }
-    int32_t* col = reinterpret_cast<int32_t*>(base + r16(8 * RW) + r16((int64_t)RW * sizeof(TS)));
-    TS* val = reinterpret_cast<TS*>(reinterpret_cast<unsigned char*>(col) + r16(4 * ne));
-    int64_t at = 0;
-    for (int r = 0; r < RW; ++r) {
-      const int64_t i = sched[t * RW + r];
-      if (i < 0) {
-        hrow[r] = -1;
-        hd[r] = (TS)1;
-        continue;
-      }
-      const int32_t b = rb[i];
-      const int64_t s = bp[b], e = bp[b + 1];
-      hrow[r] = (int32_t)(i - s);
-      hd[r] = (TS)dinv[i];
-      const int64_t t0 = dir == 0 ? prp[i] : pdiag[i] + 1;
-      const int64_t t1 = dir == 0 ? pdiag[i] : prp[i + 1];
-      for (int64_t q = t0; q < t1; ++q) {
-        const int32_t j = pci[q];
-        if (j < s || j >= e) continue;
-        col[at] = (int32_t)(j - s);
-        val[at] = (TS)F[q];
-        ++at;
-      }
-    }
-  }
 }
 
 // Variable-width tiles.  A tile holds rows of one level; row r of the tile
@@ -730,28 +662,6 @@ cudaError_t pack_fill(int dir, int64_t npos, const int32_t* row_block, const int
     k_pack_fill<double><<<grid_for(npos, 256), 256, 0, st>>>(dir, npos, row_block, bp, prp, pci, pdiag, lev_rows,
                                                              F, dinv, off, col, static_cast<double*>(val),
                                                              static_cast<double*>(pdinv), prow); count_launch();
-  }
-  return cudaGetLastError();
-}
-
-cudaError_t tile_count(int dir, int64_t ntiles, int RW, int tsz, const int32_t* sched, const int32_t* row_block,
-                       const int64_t* bp, const int64_t* prp, const int32_t* pci, const int64_t* pdiag,
-                       int64_t* tbytes, cudaStream_t st) {
-  k_tile_count<<<grid_for(ntiles, 256), 256, 0, st>>>(dir, ntiles, RW, tsz, sched, row_block, bp, prp, pci, pdiag,
-                                                      tbytes); count_launch();
-  return cudaGetLastError();
-}
-
-cudaError_t tile_fill(int dir, int64_t ntiles, int RW, int prec, const int32_t* sched, const int32_t* row_block,
-                      const int64_t* bp, const int64_t* prp, const int32_t* pci, const int64_t* pdiag,
-                      const double* F, const double* dinv, const int64_t* toff, unsigned char* stream,
-                      cudaStream_t st) {
-  if (prec == 32) {
-    k_tile_fill<float><<<grid_for(ntiles, 256), 256, 0, st>>>(dir, ntiles, RW, sched, row_block, bp, prp, pci, pdiag,
-                                                              F, dinv, toff, stream); count_launch();
-  } else {
-    k_tile_fill<double><<<grid_for(ntiles, 256), 256, 0, st>>>(dir, ntiles, RW, sched, row_block, bp, prp, pci,
-                                                               pdiag, F, dinv, toff, stream); count_launch();
   }
   return cudaGetLastError();
 }
