@@ -98,6 +98,20 @@ def test_both_solve_kernels_fp64(case, kernel):
     check_solution(prob, ref_state, ref, g)
 
 
+def test_block_beyond_staged_limit():
+    """A single 70,000-row block: more rows than the staged sweeps' 16-bit
+    block-local indices allow, so the solve falls back to the
+    level-synchronous sweeps (in global memory) and still meets the oracle's
+    bars; forcing the staged kernel is refused with an argument error."""
+    prob = W.config1(m=70000, n=175000, nblocks=1)
+    ref_state, ref = oracle.bj_solve(prob)
+    assert ref.status == 0
+    g = run_bj(prob, 64)
+    check_solution(prob, ref_state, ref, g)
+    with pytest.raises(sdsl.SdslError):
+        run_bj(prob, 32, solve_kernel=3)
+
+
 @pytest.mark.parametrize("prec", [64, 32])
 def test_staged_readiness_modes_agree(prec):
     """The staged sweeps with per-value readiness and with per-level counters
