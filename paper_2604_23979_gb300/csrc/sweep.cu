@@ -33,6 +33,17 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
+// Level completion counters: a release increment by the producing warp (after
+// its lanes' stores, ordered by __syncwarp) and acquire loads by the waiters.
+__device__ __forceinline__ void red_release_cta(unsigned addr) {
+  asm volatile("red.release.cta.shared::cta.add.s32 [%0], 1;" ::"r"(addr) : "memory");
+}
+__device__ __forceinline__ int ld_acquire_cta(unsigned addr) {
+  int v;
+  asm volatile("ld.acquire.cta.shared::cta.s32 %0, [%1];" : "=r"(v) : "r"(addr) : "memory");
+  return v;
+}
+
 __host__ __device__ inline size_t align128(size_t x) { return (x + 127) & ~(size_t)127; }
 
 // Sum within aligned lane groups of size V (a power of two, per lane): every
@@ -129,18 +140,22 @@ __device__ __forceinline__ void sweep_staged(const unsigned char* __restrict__ s
         vv[k2] = ok ? (TC)vals[e] : TC(0);
       }
       if (done) {
+        // Speculative loads before the wait: a value still holding the
+        // sentinel is reloaded after it (only those from the last levels).
+#pragma unroll
+        for (int k2 = 0; k2 < KREG; ++k2) xv[k2] = jj[k2] >= 0 ? (TC)out[jj[k2]] : TC(0);
         if (c == 0 && level > 0) {
-          // every lane polls the same counter (a broadcast load): warp-uniform
-          volatile int* cnt = done + level - 1;
+          // every lane polls the same counter (a broadcast acquire load)
+          const unsigned cnt = smem_u32(done + level - 1);
           int spins = 0;
-          while (*cnt < need) {
+          while (ld_acquire_cta(cnt) < need) {
             if (backoff) __nanosleep(backoff);
             if (++spins > kSpinLimit / 8) { *timeout = 1; break; }
           }
-          __threadfence_block();  // order the value loads after the counter
         }
 #pragma unroll
-        for (int k2 = 0; k2 < KREG; ++k2) xv[k2] = jj[k2] >= 0 ? (TC)out[jj[k2]] : TC(0);
+        for (int k2 = 0; k2 < KREG; ++k2)
+          if (jj[k2] >= 0 && is_sentinel(xv[k2])) xv[k2] = (TC)out[jj[k2]];
 #pragma unroll
         for (int k2 = 0; k2 < KREG; k2 += 2) {
           acc = fma(vv[k2], xv[k2], acc);
@@ -180,10 +195,7 @@ __device__ __forceinline__ void sweep_staged(const unsigned char* __restrict__ s
     acc = segmented_sum(acc + acc2, V, Vmax);
     if (leader) out[row] = (inr - acc) * dvr;
     __syncwarp();  // the slot of tile k-1 is free: refill it with tile k+SLOTS-1
-    if (done && lane == 0) {
-      __threadfence_block();  // the tile's values before its count
-      atomicAdd(done + level, 1);
-    }
+    if (done && lane == 0) red_release_cta(smem_u32(done + level));  // the tile's values before its count
     issue(k + SLOTS - 1);
   }
   cp_async_wait<0>();
