@@ -287,11 +287,34 @@ __global__ void __launch_bounds__(kIcWarps * 32) k_ic0(const int64_t* __restrict
       if (staged)
         for (int64_t q = lane; q < len; q += 32) cols[q] = pci[t0 + q];
       __syncwarp();
-      for (int64_t t = 0; t < len; ++t) {
+      // Software pipeline over the row's entries t: row k_{t+1}'s pattern,
+      // its first 32 entries and its diagonal are loaded while entry t is
+      // computed (row k_{t+1} belongs to an earlier level, so they are final);
+      // every lane still sums its entries q = prp[k] + lane, +32, ... in order.
+      int64_t kd_c = 0, q0_c = 0;
+      int32_t j_c = -1;
+      double f_c = 0.0, d_c = 1.0;
+      auto fetch = [&](int64_t t, int64_t& q0, int64_t& kd, int32_t& j, double& f, double& d) {
         const int64_t k = pci[t0 + t];
+        q0 = prp[k];
+        kd = pdiag[k];
+        const int64_t q = q0 + lane;
+        j = q < kd ? pci[q] : -1;
+        f = q < kd ? F[q] : 0.0;
+        d = F[kd];
+      };
+      if (len > 0) fetch(0, q0_c, kd_c, j_c, f_c, d_c);
+      for (int64_t t = 0; t < len; ++t) {
+        int64_t kd_n = 0, q0_n = 0;
+        int32_t j_n = -1;
+        double f_n = 0.0, d_n = 1.0;
+        if (t + 1 < len) fetch(t + 1, q0_n, kd_n, j_n, f_n, d_n);
         double acc = 0.0;
-        const int64_t kd = pdiag[k];
-        for (int64_t q = prp[k] + lane; q < kd; q += 32) {
+        if (j_c >= s) {
+          const int64_t pos = staged ? bsearch_i32(cols, 0, t, j_c) : bsearch_i32(pci + t0, 0, t, j_c);
+          if (pos >= 0) acc = __fma_rn(staged ? vals[pos] : F[t0 + pos], f_c, acc);
+        }
+        for (int64_t q = q0_c + lane + 32; q < kd_c; q += 32) {
           const int32_t j = pci[q];
           if (j < s) continue;
           const int64_t pos = staged ? bsearch_i32(cols, 0, t, j) : bsearch_i32(pci + t0, 0, t, j);
@@ -299,10 +322,15 @@ __global__ void __launch_bounds__(kIcWarps * 32) k_ic0(const int64_t* __restrict
         }
         acc = warp_sum(acc);
         if (lane == 0) {
-          const double l = (pv[t0 + t] - acc) / F[kd];
+          const double l = (pv[t0 + t] - acc) / d_c;
           if (staged) vals[t] = l; else F[t0 + t] = l;
         }
         __syncwarp();
+        kd_c = kd_n;
+        q0_c = q0_n;
+        j_c = j_n;
+        f_c = f_n;
+        d_c = d_n;
       }
       double sq = 0.0;
       for (int64_t q = lane; q < len; q += 32) {
