@@ -323,7 +323,7 @@ def run_ours(args, ws, rank, local):
     }
 
     if not args.quick and rank == 0:
-        # plain FP64 form on the same GPU (the benchmark spec comparison)
+        # the plain FP64-factor form on the same GPU, for comparison with the mixed form
         other = 64 if args.prec == 32 else 32
         t_other, st_other = timed_steps(other, 2)
         out["other_form"] = {"factor_prec": other, "time_to_1e8_ms": round(statistics.median(t_other), 3),

@@ -332,7 +332,7 @@ def test_ic0_reproduces_pattern_entries(orc, seed):
 
 
 def test_ic0_tau0_one_block_is_unfiltered(orc):
-    """The benchmark spec invariant: drop tolerance 0, one block -> plain IC(0) of S."""
+    """Invariant: drop tolerance 0 and one block reproduce the plain IC(0) of S."""
     from paper_2604_23979_gb300 import workloads as W
     p = W.config1(m=300, n=750)
     S = orc.normal_matrix(p.A, p.theta, p.rho)
