@@ -97,6 +97,31 @@ def test_bbd_structures_schur_apply(seed, mild):
         sdsl.sdsl_free(h)
 
 
+def test_bbd_update_diag_keeps_factors():
+    """Augmented form: a new theta changes only the -1/theta diagonal of K,
+    bit-exact against the oracle's K for the new theta; the next solve uses
+    the kept BBD preconditioner and still reaches the true residual bar."""
+    p = kkt(seed=5)
+    h, keep = gpu_setup(p)
+    try:
+        sdsl.sdsl_factor(h)
+        x = np.zeros(len(p.b))
+        st = sdsl.sdsl_solve(h, p.b, x)
+        assert st.status == 0
+        theta2 = p.theta * np.exp(np.random.default_rng(4).normal(0.0, 0.2, len(p.theta)))
+        sdsl.sdsl_update_diag(h, theta2)
+        rp, ci, v = sdsl.sdsl_export_system(h)
+        K2, pos, kbp = oracle.augmented(p.A, theta2, p.rho, p.row_block_ptr, p.col_block_ptr)
+        assert np.array_equal(rp, K2.rowptr) and np.array_equal(ci, K2.col)
+        assert np.array_equal(bits(v), bits(K2.val))
+        x2 = np.zeros(len(p.b))
+        st2 = sdsl.sdsl_solve(h, p.b, x2)
+        assert st2.status == 0 and st2.rebuilt == 0
+        assert relres(K2, x2, p.b) <= p.rtol
+    finally:
+        sdsl.sdsl_free(h)
+
+
 @pytest.mark.parametrize("schur_lu", [0, 1, 2])
 def test_bbd_border_lu_modes(schur_lu):
     """A 300-row border: the blocked LU (tensor-core or CUDA-core trailing
