@@ -22,7 +22,9 @@
  *                      the factor options of Sec. 3.1;
  *   or_pcg             right-preconditioned Block-Jacobi CG (Sec. 2.2-2.3);
  *   or_bbd_* / or_gmres  BBD Schur complement, block solve (Sec. 2.4) and
- *                      right-preconditioned restarted GMRES (Sec. 2.2).
+ *                      right-preconditioned restarted GMRES (Sec. 2.2);
+ *   or_bicgstab        right-preconditioned BiCGSTAB, the method paired with
+ *                      Block Jacobi in Sec. 4.3 (van der Vorst 1992).
  *
  * Conventions: CSR with int64 row pointers, int32 sorted column indices,
  * double values.  Blocks are contiguous index ranges block_ptr[b] ..
@@ -830,6 +832,90 @@ done:
   return status;
 }
 
+/* Right-preconditioned BiCGSTAB (van der Vorst, SIAM J. Sci. Stat. Comput.
+ * 13, 1992), the Krylov method the paper pairs with Block Jacobi (Sec. 4.3).
+ * The residual r is that of S x = b itself (right preconditioning, Sec. 2.2);
+ * the shadow vector is r at the (re)start.  One pass is
+ *   p  = r                         (first pass after a (re)start)
+ *   p  = r + beta (p - omega v)    (later passes)
+ *   ph = M^{-1} p,  v = S ph,  alpha = rho / (rt . v)
+ *   x  = x + alpha ph,  s = r - alpha v     -- stop here if ||s|| <= tol
+ *   sh = M^{-1} s,  t = S sh,  omega = (t . s) / (t . t)
+ *   x  = x + omega sh,  r = s - omega t
+ *   rho' = rt . r,  beta = (rho' / rho) (alpha / omega)
+ * The count is the number of passes started.  A recurrence residual at the
+ * tolerance (after either half) is confirmed with the true residual; if that
+ * is still above it, the iteration restarts from r = b - S x.  Breakdown:
+ * rt . v = 0, t . t = 0, omega = 0, rho' = 0, or a non-finite scalar. */
+int or_bicgstab(int64_t n, const int64_t* rp, const int32_t* ci, const double* v, const or_precond* M,
+                const double* b, double* x, double rtol, int64_t maxit, int64_t* iters, double* out) {
+  size_t sz = sizeof(double) * (size_t)(n > 0 ? n : 1);
+  double *r = (double*)malloc(sz), *rt = (double*)malloc(sz), *p = (double*)malloc(sz);
+  double *ph = (double*)malloc(sz), *vv = (double*)malloc(sz), *sh = (double*)malloc(sz);
+  double *t = (double*)malloc(sz);
+  int status = OR_NOT_CONVERGED;
+  int64_t it = 0;
+  double bnorm = nrm2(n, b), tol = rtol * bnorm, rnorm = 0.0, tnorm = 0.0;
+  or_spmv(n, rp, ci, v, x, t);
+  for (int64_t i = 0; i < n; ++i) r[i] = b[i] - t[i];
+  rnorm = tnorm = nrm2(n, r);
+  if (bnorm == 0.0) { for (int64_t i = 0; i < n; ++i) x[i] = 0.0; rnorm = tnorm = 0.0; status = OR_OK; goto done; }
+  if (rnorm <= tol) { status = OR_OK; goto done; }
+  for (;;) {
+    /* (re)start: shadow vector and rho from the current residual */
+    memcpy(rt, r, sz);
+    double rho = dot(n, rt, r), alpha = 0.0, omega = 0.0, beta = 0.0;
+    int first = 1, reached = 0;
+    while (it < maxit) {
+      ++it;
+      if (first) {
+        memcpy(p, r, sz);
+        first = 0;
+      } else {
+        for (int64_t i = 0; i < n; ++i) p[i] = r[i] + beta * (p[i] - omega * vv[i]);
+      }
+      precond_apply(M, p, ph);
+      or_spmv(n, rp, ci, v, ph, vv);
+      double rv = dot(n, rt, vv);
+      if (rv == 0.0 || !isfinite(rv)) { status = OR_BREAKDOWN; break; }
+      alpha = rho / rv;
+      for (int64_t i = 0; i < n; ++i) { x[i] = x[i] + alpha * ph[i]; r[i] = r[i] - alpha * vv[i]; }
+      rnorm = nrm2(n, r);
+      if (rnorm <= tol) { reached = 1; break; }
+      precond_apply(M, r, sh);
+      or_spmv(n, rp, ci, v, sh, t);
+      double tt = dot(n, t, t), ts = dot(n, t, r);
+      if (!(tt > 0.0) || !isfinite(tt) || !isfinite(ts)) { status = OR_BREAKDOWN; break; }
+      omega = ts / tt;
+      for (int64_t i = 0; i < n; ++i) { x[i] = x[i] + omega * sh[i]; r[i] = r[i] - omega * t[i]; }
+      rnorm = nrm2(n, r);
+      if (rnorm <= tol) { reached = 1; break; }
+      if (it >= maxit) break;
+      double rho_new = dot(n, rt, r);
+      if (rho_new == 0.0 || omega == 0.0 || !isfinite(rho_new) || !isfinite(omega)) { status = OR_BREAKDOWN; break; }
+      beta = (rho_new / rho) * (alpha / omega);
+      rho = rho_new;
+    }
+    if (!reached) break;
+    or_spmv(n, rp, ci, v, x, t);
+    for (int64_t i = 0; i < n; ++i) t[i] = b[i] - t[i];
+    tnorm = nrm2(n, t);
+    if (tnorm <= tol) { status = OR_OK; goto done; }
+    if (it >= maxit) goto done;
+    memcpy(r, t, sz);
+    rnorm = tnorm;
+  }
+  or_spmv(n, rp, ci, v, x, t);
+  for (int64_t i = 0; i < n; ++i) t[i] = b[i] - t[i];
+  tnorm = nrm2(n, t);
+done:
+  *iters = it;
+  out[0] = bnorm > 0.0 ? tnorm / bnorm : 0.0;
+  out[1] = bnorm > 0.0 ? rnorm / bnorm : 0.0;
+  free(r); free(rt); free(p); free(ph); free(vv); free(sh); free(t);
+  return status;
+}
+
 /* Entry points that build the preconditioner descriptor for Python callers. */
 int or_pcg_bj(int64_t n, const int64_t* rp, const int32_t* ci, const double* v, const int64_t* prp,
               const int32_t* pci, const double* F, int64_t nblocks, const int64_t* block_ptr,
@@ -853,6 +939,14 @@ int or_gmres_pre(int kind, int64_t n, const int64_t* rp, const int32_t* ci, cons
                  int64_t* iters, double* out) {
   or_precond M = {kind, n, prp, pci, pv, F, nblocks, block_ptr, lu, ipiv};
   return or_gmres(n, rp, ci, v, &M, b, x, rtol, maxit, restart, iters, out);
+}
+
+int or_bicgstab_pre(int kind, int64_t n, const int64_t* rp, const int32_t* ci, const double* v,
+                    const int64_t* prp, const int32_t* pci, const double* pv, const double* F,
+                    int64_t nblocks, const int64_t* block_ptr, const double* b, double* x, double rtol,
+                    int64_t maxit, int64_t* iters, double* out) {
+  or_precond M = {kind, n, prp, pci, pv, F, nblocks, block_ptr, NULL, NULL};
+  return or_bicgstab(n, rp, ci, v, &M, b, x, rtol, maxit, iters, out);
 }
 
 void or_precond_apply(int kind, int64_t n, const int64_t* prp, const int32_t* pci, const double* pv,

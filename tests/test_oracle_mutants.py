@@ -43,6 +43,16 @@ MUTANTS = [
      [pins.test_bbd_schur_and_apply_match_dense]),
     ("lu-pivot", "if (fabs(a[i * nb + k]) > best)", "if (fabs(a[i * nb + k]) < best)",
      [pins.test_dense_lu_matches_scipy]),
+    ("bicgstab-beta", "beta = (rho_new / rho) * (alpha / omega);", "beta = (rho_new / rho) * (omega / alpha);",
+     [lambda o: pins.test_bicgstab_terminates_after_k_passes(o, 3)]),
+    ("bicgstab-omega", "omega = ts / tt;", "omega = tt / ts;",
+     [pins.test_bicgstab_first_pass_is_galerkin_then_minimal_residual]),
+    ("bicgstab-x-operand", "x[i] = x[i] + alpha * ph[i];", "x[i] = x[i] + alpha * p[i];",
+     [pins.test_bicgstab_exact_preconditioner_one_pass, pins.test_bicgstab_recurrence_tracks_true_residual]),
+    ("bicgstab-shadow", "double rv = dot(n, rt, vv);", "double rv = dot(n, r, vv);",
+     [lambda o: pins.test_bicgstab_terminates_after_k_passes(o, 3)]),
+    ("bicgstab-s-sign", "r[i] = r[i] - alpha * vv[i];", "r[i] = r[i] + alpha * vv[i];",
+     [pins.test_bicgstab_identity_one_half_pass]),
 ]
 
 

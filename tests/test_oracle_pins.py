@@ -533,6 +533,123 @@ def test_gmres_restarts(orc):
     assert np.linalg.norm(b - D @ res.x) / np.linalg.norm(b) <= 1e-10
 
 
+# ------------------------------------------- BiCGSTAB (Block Jacobi, Sec. 4.3)
+
+def _distinct_eigen(rng, n, lams):
+    """Non-symmetric, diagonalisable n x n matrix whose eigenvalues are the
+    values of lams repeated (V diag V^-1 with a well-conditioned V)."""
+    V = np.eye(n) + 0.3 * rng.standard_normal((n, n)) / np.sqrt(n)
+    d = np.array([lams[i % len(lams)] for i in range(n)], float)
+    return V @ np.diag(d) @ np.linalg.inv(V)
+
+
+def test_bicgstab_identity_one_half_pass(orc):
+    n = 12
+    b = np.random.default_rng(110).standard_normal(n)
+    res = orc.bicgstab(orc.from_dense(np.eye(n)), b)
+    assert res.status == 0 and res.iters == 1
+    np.testing.assert_array_equal(res.x, b)
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 4])
+def test_bicgstab_terminates_after_k_passes(orc, k):
+    """k distinct eigenvalues: the BiCG residual polynomial of degree k
+    annihilates r0, so the k-th pass ends at its first half with s = 0 (and
+    not earlier for a generic right-hand side)."""
+    rng = np.random.default_rng(111 + k)
+    n = 24
+    D = _distinct_eigen(rng, n, [1.0, 2.5, 4.0, 7.0][:k])
+    b = rng.standard_normal(n)
+    res = orc.bicgstab(orc.from_dense(D), b, rtol=1e-9)
+    assert res.status == 0 and res.iters == k
+    np.testing.assert_allclose(res.x, np.linalg.solve(D, b), rtol=1e-8, atol=1e-10)
+
+
+def test_bicgstab_first_pass_is_galerkin_then_minimal_residual(orc):
+    """After one pass from x0 = 0: s = b - alpha A b is the vector of that form
+    orthogonal to the shadow b, and omega minimises ||s - omega A s||."""
+    rng = np.random.default_rng(115)
+    n = 30
+    D = rng.standard_normal((n, n)) + 6 * np.eye(n)
+    b = rng.standard_normal(n)
+    res = orc.bicgstab(orc.from_dense(D), b, rtol=1e-300, maxit=1)
+    assert res.status == 5 and res.iters == 1
+    Ab = D @ b
+    # the alpha with b^T (b - alpha A b) = 0 (the 1 x 1 Galerkin system)
+    alpha = np.linalg.solve([[b @ Ab]], [b @ b])[0]
+    s = b - alpha * Ab
+    assert abs(b @ s) <= 1e-12 * np.linalg.norm(b) * np.linalg.norm(s)
+    As = D @ s
+    omega = np.linalg.lstsq(As[:, None], s, rcond=None)[0][0]
+    r1 = s - omega * As
+    assert res.relres_rec == pytest.approx(np.linalg.norm(r1) / np.linalg.norm(b), rel=1e-9)
+    np.testing.assert_allclose(res.x, alpha * b + omega * s, rtol=1e-10, atol=1e-13)
+
+
+def test_bicgstab_exact_preconditioner_one_pass(orc):
+    """ILU(0) on the full pattern is the exact LU: M^-1 S = I, one half pass."""
+    rng = np.random.default_rng(116)
+    n = 20
+    D = rng.standard_normal((n, n)) + 8 * np.eye(n)
+    K = orc.from_dense(D)
+    bp = np.array([0, n])
+    F, _, _ = orc.ilu0(K, bp)
+    b = rng.standard_normal(n)
+    res = orc.bicgstab(K, b, orc.PRE_BJ_ILU0, K, F, bp)
+    assert res.status == 0 and res.iters == 1
+    np.testing.assert_allclose(res.x, np.linalg.solve(D, b), rtol=1e-10)
+
+
+def test_bicgstab_recurrence_tracks_true_residual(orc):
+    """With a Block-Jacobi IC(0) preconditioner, after k passes the recurrence
+    residual equals ||b - S x|| (x and r are updated with the same steps)."""
+    from paper_2604_23979_gb300 import workloads as W
+    p = W.config1(m=200, n=500)
+    st = orc.bj_setup_factor(p.A, p.theta, p.rho, p.block_ptr, p.tau, p.delta)
+    Sd = st.S.dense()
+    for k in (1, 3, 6):
+        res = orc.bicgstab(st.S, p.b, orc.PRE_BJ_IC0, st.P, st.F, p.block_ptr, rtol=1e-300, maxit=k)
+        assert res.iters == k
+        true = np.linalg.norm(p.b - Sd @ res.x) / np.linalg.norm(p.b)
+        assert res.relres_true == pytest.approx(true, rel=1e-9)
+        assert res.relres_rec == pytest.approx(true, rel=1e-6, abs=1e-14)
+
+
+def test_bicgstab_bj_matches_dense_solve(orc):
+    from paper_2604_23979_gb300 import workloads as W
+    p = W.config1(m=200, n=500)
+    st = orc.bj_setup_factor(p.A, p.theta, p.rho, p.block_ptr, p.tau, p.delta)
+    res = orc.bicgstab(st.S, p.b, orc.PRE_BJ_IC0, st.P, st.F, p.block_ptr, rtol=1e-8, maxit=2000)
+    ref = np.linalg.solve(st.S.dense(), p.b)
+    assert res.status == 0 and res.relres_true <= 1e-8
+    assert np.linalg.norm(res.x - ref) / np.linalg.norm(ref) <= 1e-6
+    # right preconditioning: no more passes than PCG needs products, twice over
+    pcg = orc.pcg_bj(st.S, st.P, st.F, p.block_ptr, p.b)
+    assert res.iters <= pcg.iters
+
+
+def test_bicgstab_nonsymmetric_matches_dense_solve(orc):
+    rng = np.random.default_rng(117)
+    n = 40
+    D = rng.standard_normal((n, n)) + 10 * np.eye(n)
+    b = rng.standard_normal(n)
+    res = orc.bicgstab(orc.from_dense(D), b, rtol=1e-12)
+    assert res.status == 0
+    np.testing.assert_allclose(res.x, np.linalg.solve(D, b), rtol=1e-9, atol=1e-12)
+
+
+def test_bicgstab_edge_cases(orc):
+    n = 10
+    S = orc.from_dense(2 * np.eye(n))
+    res = orc.bicgstab(S, np.zeros(n))
+    assert res.status == 0 and res.iters == 0 and not res.x.any()
+    b = np.ones(n)
+    res = orc.bicgstab(S, b, x0=b / 2)
+    assert res.status == 0 and res.iters == 0
+    res = orc.bicgstab(S, b, maxit=0)
+    assert res.status == 5 and res.iters == 0
+
+
 # ------------------------------------------------------------ BBD (Sec. 2.4)
 
 def _small_bbd(orc, seed=3):
