@@ -229,8 +229,10 @@ def run_ours(args, ws, rank, local):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > 129 MB L2
     stream = torch.cuda.current_stream(dev)
 
-    def one_solve(prec, profile=False, host_io=False, xbuf=None, bbuf=None, arrays=None):
+    def one_solve(prec, profile=False, host_io=False, xbuf=None, bbuf=None, arrays=None, method=None):
         o, keep = sdsl.options_for(prob, factor_prec=prec, graph_iters=16, stream=stream.cuda_stream)
+        if method is not None:
+            o.method = method
         o.profile = 1 if profile else 0
         o.solve_kernel = args.solve_kernel
         o.apply_prec = args.apply_prec if prec == 32 else 0
@@ -252,14 +254,14 @@ def run_ours(args, ws, rank, local):
             sdsl.sdsl_free(h)
         return st, setup_st, end
 
-    def timed_steps(prec, k, l2flush=True):
+    def timed_steps(prec, k, l2flush=True, method=None):
         times, stats = [], []
         for _ in range(k):
             if l2flush:
                 flush.zero_()
             start = torch.cuda.Event(enable_timing=True)
             start.record(stream)
-            st, sst, end = one_solve(prec)
+            st, sst, end = one_solve(prec, method=method)
             end.synchronize()
             times.append(start.elapsed_time(end))
             stats.append((st, sst))
@@ -330,6 +332,13 @@ def run_ours(args, ws, rank, local):
                              "iters": int(st_other[-1][0].iters),
                              "solve_ms": round(st_other[-1][0].ms_solve, 3),
                              "factor_ms": round(st_other[-1][1].ms_factor, 3)}
+        # the other Krylov method on the same preconditioner (BiCGSTAB is the
+        # pairing of Sec. 4.3; a pass holds two products and two applies)
+        t_k, st_k = timed_steps(args.prec, 2, method=sdsl.BJ_BICGSTAB)
+        sk = st_k[-1][0]
+        out["other_krylov"] = {"method": "bicgstab", "factor_prec": args.prec, "status": int(sk.status),
+                               "time_to_1e8_ms": round(statistics.median(t_k), 3), "iters": int(sk.iters),
+                               "rel_res_true": sk.rel_res_true, "solve_ms": round(sk.ms_solve, 3)}
         # per-kernel device times inside one real solve (profile mode: events around every kernel)
         pst, _, end = one_solve(args.prec, profile=True)
         end.synchronize()

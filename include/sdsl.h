@@ -10,9 +10,10 @@
  * K = [[-diag(1/theta), A^T], [A, rho I]]).  The scaling changes every
  * iteration (Sec. 3.4), which is what sdsl_update_diag models.
  *
- * Two parallel methods (Sec. 2.3, 2.4): Block Jacobi (per-block IC(0), PCG)
- * and bordered block diagonal (per-block ILU(0) + dense Schur complement of
- * the border, GMRES(m)).  Both build the preconditioner from the numerics-
+ * Two parallel methods (Sec. 2.3, 2.4): Block Jacobi (per-block IC(0), with
+ * PCG or with BiCGSTAB, the Krylov method Sec. 4.3 pairs with it) and
+ * bordered block diagonal (per-block ILU(0) + dense Schur complement of the
+ * border, GMRES(m)).  Both build the preconditioner from the numerics-
  * based filter (Eq. filter) and the diagonal correction (Eq. diagcorr).
  *
  * Conventions shared by every entry point:
@@ -51,12 +52,18 @@ typedef enum {
 } sdsl_status;
 
 enum { SDSL_FORM_CSR = 0, SDSL_FORM_NORMAL = 1, SDSL_FORM_AUGMENTED = 2 };
-enum { SDSL_BJ_PCG = 0, SDSL_BBD_GMRES = 1 };
+/* SDSL_BJ_BICGSTAB: right-preconditioned BiCGSTAB (van der Vorst 1992; right
+ * preconditioning as in Sec. 2.2) with the Block-Jacobi preconditioner of
+ * SDSL_BJ_PCG, on the same forms (normal or CSR).  stats.iters counts passes
+ * (two products and two preconditioner applies each); a pass whose first
+ * half meets the tolerance ends there.  Breakdown (a zero or non-finite
+ * rt.v, t.t, omega or rho) returns SDSL_ERR_BREAKDOWN. */
+enum { SDSL_BJ_PCG = 0, SDSL_BBD_GMRES = 1, SDSL_BJ_BICGSTAB = 2 };
 enum { SDSL_MEM_HOST = 0, SDSL_MEM_DEVICE = 1 };
 
 typedef struct {
   int form;                      /* SDSL_FORM_*: what sdsl_setup receives */
-  int method;                    /* SDSL_BJ_PCG (Sec. 2.3) or SDSL_BBD_GMRES (Sec. 2.4) */
+  int method;                    /* SDSL_BJ_PCG, SDSL_BJ_BICGSTAB (Sec. 2.3) or SDSL_BBD_GMRES (Sec. 2.4) */
   int64_t nblocks;               /* number of diagonal blocks (Sec. 2.3 "partition") */
   const int64_t* block_ptr;      /* host, nblocks+1 row offsets of the blocks; NULL = equal split.
                                     Augmented form: row blocks of A (last entry = m - border) */
@@ -76,7 +83,8 @@ typedef struct {
   int graph_iters;               /* Krylov iterations captured per CUDA graph launch; 0 = no graphs */
   int tune;                      /* 1 = time candidate launch shapes at factor time and keep the fastest */
   int profile;                   /* 1 = time every Krylov kernel with CUDA events (no graphs; slower) */
-  int apply_prec;                /* arithmetic of the triangular solves: 64 or 32; 0 = factor_prec */
+  int apply_prec;                /* arithmetic of the triangular solves: 64 or 32; 0 = factor_prec
+                                    (BiCGSTAB: 0 = 64, its recurrences assume a fixed linear M) */
   int flexible;                  /* PCG beta: 0 = rho_new/rho, 1 = flexible z_new^T(r_new - r_old)/rho
                                     (robust to an FP32 apply); -1 = 1 iff the apply is FP32 */
   int solve_kernel;              /* block triangular solves: 0 auto, 1 level-synchronous (barrier per
@@ -100,7 +108,8 @@ typedef struct {
 } sdsl_options;
 
 typedef struct {
-  int64_t iters;          /* products with the system matrix in the last solve */
+  int64_t iters;          /* Krylov iterations of the last solve: products with the system matrix
+                             (PCG, GMRES) or BiCGSTAB passes */
   int64_t restarts;       /* PCG true-residual restarts / GMRES cycles */
   int rebuilt;            /* 1 if the last solve was preceded by an automatic rebuild */
   int status;             /* sdsl_status of the last solve */

@@ -151,6 +151,9 @@ struct sdsl_handle_s {
   // Krylov workspace
   double *b = nullptr, *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *u = nullptr;
   double *part = nullptr, *part_blk = nullptr, *scalars = nullptr;
+  // BiCGSTAB: shadow residual, preconditioned direction, t = S M^{-1} s
+  double *rt = nullptr, *ph = nullptr, *tv = nullptr;
+  BicgScalars* bicg = nullptr;
   int64_t* scan_scratch = nullptr;
   int* flag = nullptr;
   PcgState* state = nullptr;
@@ -176,6 +179,10 @@ struct sdsl_handle_s {
 };
 
 namespace {
+
+// Block Jacobi (Sec. 2.3) under either Krylov method: the same IC(0)
+// preconditioner, staged sweeps and product plans.
+inline bool bj_method(const sdsl_handle h) { return h->method == SDSL_BJ_PCG || h->method == SDSL_BJ_BICGSTAB; }
 
 struct Scope {  // join the caller's stream on entry and exit
   sdsl_handle h;
@@ -236,6 +243,16 @@ sdsl_status alloc_workspace(sdsl_handle h) {
   TRY(h->sys.get(&h->scalars, 16));
   TRY(h->sys.get(&h->state, 1));
   if (!h->h_state) TRY_CUDA(cudaMallocHost(&h->h_state, sizeof(PcgState)));
+  if (h->method == SDSL_BJ_BICGSTAB) {
+    TRY(h->sys.get(&h->rt, N));
+    TRY(h->sys.get(&h->ph, N));
+    TRY(h->sys.get(&h->tv, N));
+    TRY(h->sys.get(&h->bicg, 1));
+    BicgScalars c{};
+    TRY(h->sys.get(&c.part, 2 * kBicgMaxCtas));
+    TRY(to_dev(h, h->bicg, &c, 1));
+    TRY(sync(h, "bicgstab scalars"));
+  }
   TRY_CUDA(cudaMemsetAsync(h->part, 0, sizeof(double) * (152 * 32 + 64), h->st));
   TRY_CUDA(cudaMemsetAsync(h->state, 0, sizeof(PcgState), h->st));
   TRY_CUDA(cudaMemsetAsync(h->x, 0, sizeof(double) * (size_t)N, h->st));
@@ -381,7 +398,7 @@ void choose_spmv_plan(sdsl_handle h) {
   // nnz(S) multiply-adds and HBM entries.  Auto picks it when it moves fewer
   // bytes; the explicit S stays for the filter and the true residual.
   const int form = h->opt.spmv_form;
-  const bool can = h->form == SDSL_FORM_NORMAL && h->method == SDSL_BJ_PCG;
+  const bool can = h->form == SDSL_FORM_NORMAL && bj_method(h);
   const bool fewer = 2.0 * (double)h->a_nnz < (double)h->s_nnz;
   h->A.factored = can && (form == 2 || form == 3 || (form == 0 && fewer)) ? 1 : 0;
   h->A.sell = h->A.factored && h->sell_ok && (form == 3 || form == 0) ? 1 : 0;
@@ -465,6 +482,32 @@ sdsl_status enqueue_pcg_iteration(sdsl_handle h) {
   TRY_CUDA(pcg_update_precond(h->M, h->p, h->q, h->x, h->r, h->z, h->part_blk, h->state, h->st));
   TRY_CUDA(pcg_direction(h->N, h->z, h->p, h->state, h->st));
   return SDSL_OK;
+}
+
+// The system product S y: factored (A (theta o (A^T y)) + rho y) or explicit.
+cudaError_t product(sdsl_handle h, const double* y, double* out) {
+  if (h->A.factored) return factored_product(h->A, y, out, nullptr, nullptr, 0, h->st);
+  return spmv(h->A, y, out, h->st);
+}
+
+// One BiCGSTAB pass (bicgstab.cu).  The mode-0 PCG update computes
+// x += alpha ph, s = r - alpha v (in r), sh = M^{-1} s (in z) and ||s||^2
+// with its convergence test; v is kept in q.
+sdsl_status enqueue_bicg_iteration(sdsl_handle h) {
+  const int64_t N = h->N;
+  TRY_CUDA(bicg_direction(N, h->r, h->q, h->p, h->state, h->bicg, h->st));
+  TRY_CUDA(precond_apply(h->M, h->p, h->ph, nullptr, h->part_blk, h->state, 2, h->st));
+  TRY_CUDA(product(h, h->ph, h->q));
+  TRY_CUDA(bicg_alpha(N, h->rt, h->q, h->state, h->bicg, h->st));
+  TRY_CUDA(pcg_update_precond(h->M, h->ph, h->q, h->x, h->r, h->z, h->part_blk, h->state, h->st));
+  TRY_CUDA(product(h, h->z, h->tv));
+  TRY_CUDA(bicg_omega(N, h->tv, h->r, h->state, h->bicg, h->st));
+  TRY_CUDA(bicg_finish(N, h->z, h->tv, h->rt, h->x, h->r, h->state, h->bicg, h->st));
+  return SDSL_OK;
+}
+
+sdsl_status enqueue_iteration(sdsl_handle h) {
+  return h->method == SDSL_BJ_BICGSTAB ? enqueue_bicg_iteration(h) : enqueue_pcg_iteration(h);
 }
 
 // Profile mode: one iteration with CUDA events around each kernel; the
@@ -557,7 +600,7 @@ sdsl_status build_sell(sdsl_handle h, int64_t nrows, const int64_t* rp, const in
 sdsl_status plan_sell(sdsl_handle h) {
   if (h->sell_planned) return SDSL_OK;
   h->sell_planned = true;
-  if (h->form != SDSL_FORM_NORMAL || h->method != SDSL_BJ_PCG) return SDSL_OK;
+  if (h->form != SDSL_FORM_NORMAL || !bj_method(h)) return SDSL_OK;
   if (h->opt.spmv_form == 1 || h->opt.spmv_form == 2) return SDSL_OK;
   bool ok_a = false, ok_at = false;
   TRY(build_sell(h, h->m, h->a_rp, h->a_ci, h->a_v, h->a_nnz, &h->a_sell, &ok_a));
@@ -568,13 +611,16 @@ sdsl_status plan_sell(sdsl_handle h) {
 
 sdsl_status build_graph(sdsl_handle h) {
   destroy_graph(h);
-  const int G = h->opt.graph_iters;
+  // BiCGSTAB: the apply and the products of the passes captured after the
+  // converged one still run (only the scalar steps return early), so its
+  // graphs are kept short.
+  const int G = h->method == SDSL_BJ_BICGSTAB ? std::min(h->opt.graph_iters, 4) : h->opt.graph_iters;
   if (G <= 0) return SDSL_OK;
   cudaGraph_t g = nullptr;
   const long long before = launches_so_far();
   TRY_CUDA(cudaStreamBeginCapture(h->st, cudaStreamCaptureModeRelaxed));
   sdsl_status s = SDSL_OK;
-  for (int i = 0; i < G && s == SDSL_OK; ++i) s = enqueue_pcg_iteration(h);
+  for (int i = 0; i < G && s == SDSL_OK; ++i) s = enqueue_iteration(h);
   cudaError_t e = cudaStreamEndCapture(h->st, &g);
   h->graph_kernels = launches_so_far() - before;
   count_launch(-h->graph_kernels);  // captured, not executed: counted per graph launch
@@ -1081,7 +1127,7 @@ sdsl_status factor_impl(sdsl_handle h) {
   std::vector<int> tries(nb, 0);
   h->h_alpha.assign(nb, 0.0);
   int64_t shifted = 0;
-  if (h->method == SDSL_BJ_PCG) {
+  if (bj_method(h)) {
     // IC(0): every shift of the ladder at once (nblocks x 5 CTAs), then pick
     double *Fall, *dinv_all, *d_alpha;
     int32_t *d_status, *d_choice;
@@ -1210,7 +1256,11 @@ sdsl_status factor_impl(sdsl_handle h) {
   }
   TRY(h->pc.get(&h->part_blk, 3 * nb + 32));
   // level-ordered packed triangles for the flag-synchronised solves
-  const int apply = h->opt.apply_prec == 0 ? (f32 ? 32 : 64) : h->opt.apply_prec;
+  // Auto: FP32 arithmetic for FP32 factors under PCG (its flexible beta
+  // absorbs the rounding of an FP32 apply), FP64 arithmetic on the FP32
+  // values under BiCGSTAB, whose recurrences assume one fixed linear M.
+  const int apply = h->opt.apply_prec != 0 ? h->opt.apply_prec
+                    : (f32 && h->method != SDSL_BJ_BICGSTAB) ? 32 : 64;
   M.apply_prec = apply;
   M.flexible = h->opt.flexible < 0 ? (apply == 32 ? 1 : 0) : (h->opt.flexible ? 1 : 0);
   M.threads = 1024;
@@ -1232,7 +1282,7 @@ sdsl_status factor_impl(sdsl_handle h) {
   const bool fits_tma = staged_smem_bytes(maxb, apply == 32 ? 4 : 8, 16, 1024, 2, M.max_tiles, 0) <= (size_t)225 * 1024;
   if ((h->opt.solve_kernel == 2 && !fits) || (h->opt.solve_kernel == 3 && !fits_tma))
     return fail(SDSL_ERR_ARG, "flag-synchronised solves need the largest block to fit in shared memory");
-  M.tma = (h->method == SDSL_BJ_PCG && (h->opt.solve_kernel == 3 || (h->opt.solve_kernel == 0 && fits_tma))) ? 1 : 0;
+  M.tma = (bj_method(h) && (h->opt.solve_kernel == 3 || (h->opt.solve_kernel == 0 && fits_tma))) ? 1 : 0;
   M.sweep_warps = h->opt.sweep_warps > 0 ? h->opt.sweep_warps : 16;
   M.backoff_ns = h->opt.sweep_backoff_ns >= 0 ? h->opt.sweep_backoff_ns : 0;
   if (M.tma) {
@@ -1244,7 +1294,7 @@ sdsl_status factor_impl(sdsl_handle h) {
       M.tma = 0;
     }
   }
-  M.sync_free = (h->method == SDSL_BJ_PCG && !M.tma && (h->opt.solve_kernel == 2 || (h->opt.solve_kernel == 0 && fits)))
+  M.sync_free = (bj_method(h) && !M.tma && (h->opt.solve_kernel == 2 || (h->opt.solve_kernel == 0 && fits)))
                     ? 1 : 0;
   if (M.sync_free) {
     M.lanes = sweep_lanes;
@@ -1298,7 +1348,7 @@ sdsl_status factor_impl(sdsl_handle h) {
   TRY(plan_sell(h));
   choose_spmv_plan(h);
   if (h->opt.tune) TRY(tune_spmv(h));
-  if (h->method == SDSL_BJ_PCG && !h->opt.profile) TRY(build_graph(h));
+  if (bj_method(h) && !h->opt.profile) TRY(build_graph(h));
   cudaEventRecord(h->ev_b, h->st);
   TRY(sync(h, "factor end"));
   h->factored = true;
@@ -1412,6 +1462,84 @@ sdsl_status pcg_solve(sdsl_handle h, sdsl_stats* st_out) {
                                                    : "PCG reached maxit before the tolerance");
 }
 
+// Right-preconditioned BiCGSTAB with the Block-Jacobi IC(0) preconditioner
+// (Sec. 4.3 pairs them).  The count is the number of passes started; a pass
+// whose first half already meets the tolerance ends there.  Convergence of
+// the recurrence is confirmed with the true residual; if that is still above
+// the tolerance the iteration restarts from r = b - S x (new shadow vector).
+sdsl_status bicg_solve(sdsl_handle h) {
+  const int64_t N = h->N;
+  double* bn2 = h->scalars;
+  TRY_CUDA(norm2_sq(N, h->b, h->part, bn2, reinterpret_cast<unsigned int*>(h->part + 152 * 32), h->st));
+  TRY_CUDA(pcg_init_state(h->state, 0.0, h->opt.maxit, h->st));
+  TRY_CUDA(true_residual(h->A, h->b, h->x, h->r, h->part, h->state, 1, h->st));
+  double bnorm2 = 0.0;
+  TRY(to_host(h, &bnorm2, bn2, 1));
+  TRY(to_host(h, h->h_state, h->state, 1));
+  TRY(sync(h, "bicgstab init"));
+  const double tol = h->opt.rtol * std::sqrt(bnorm2);
+  const double tol2 = tol * tol;
+  sdsl_stats& S = h->stats;
+  S.iters = 0;
+  S.restarts = 0;
+  if (bnorm2 == 0.0) {
+    TRY_CUDA(cudaMemsetAsync(h->x, 0, sizeof(double) * (size_t)N, h->st));
+    S.rel_res_true = S.rel_res_rec = 0.0;
+    S.status = SDSL_OK;
+    return SDSL_OK;
+  }
+  S.rel_res_true = S.rel_res_rec = std::sqrt(h->h_state->tr / bnorm2);
+  if (h->h_state->tr <= tol2) {
+    S.status = SDSL_OK;
+    return SDSL_OK;
+  }
+  if (h->opt.maxit == 0) {
+    S.status = SDSL_ERR_NOT_CONVERGED;
+    return fail(SDSL_ERR_NOT_CONVERGED, "BiCGSTAB reached maxit before the tolerance");
+  }
+  // the pass limit is tested by k_bicg_finish; the mode-0 update's own limit
+  // test is kept out of the way
+  const long long kNoLimit = (long long)1 << 62;
+  TRY_CUDA(pcg_init_state(h->state, tol2, kNoLimit, h->st));
+  TRY_CUDA(bicg_init(h->bicg, h->opt.maxit, h->st));
+  TRY_CUDA(bicg_restart(N, h->r, h->rt, h->bicg, h->st));
+  sdsl_status result = SDSL_ERR_NOT_CONVERGED;
+  for (;;) {
+    if (h->graph) {
+      TRY_CUDA(cudaGraphLaunch(h->graph, h->st));
+      count_launch(h->graph_kernels);
+    } else {
+      for (int i = 0; i < 4; ++i) TRY(enqueue_bicg_iteration(h));
+    }
+    TRY(to_host(h, h->h_state, h->state, 1));
+    TRY(sync(h, "bicgstab passes"));
+    const PcgState& hs = *h->h_state;
+    if (hs.err) return fail(SDSL_ERR_TIMEOUT, "a triangular-solve wait exceeded its bound");
+    if (!hs.done) continue;
+    if (hs.done == 3) { result = SDSL_ERR_BREAKDOWN; break; }
+    if (hs.done == 2) { result = SDSL_ERR_NOT_CONVERGED; break; }
+    TRY_CUDA(true_residual(h->A, h->b, h->x, h->r, h->part, h->state, 0, h->st));
+    TRY(to_host(h, h->h_state, h->state, 1));
+    TRY(sync(h, "true residual"));
+    if (h->h_state->tr <= tol2) { result = SDSL_OK; break; }
+    if (h->h_state->iters >= h->opt.maxit) { result = SDSL_ERR_NOT_CONVERGED; break; }
+    S.restarts += 1;
+    TRY_CUDA(true_residual(h->A, h->b, h->x, h->r, h->part, h->state, 1, h->st));
+    TRY_CUDA(bicg_restart(N, h->r, h->rt, h->bicg, h->st));
+    TRY_CUDA(cudaMemsetAsync(&h->state->done, 0, sizeof(int), h->st));
+  }
+  TRY_CUDA(true_residual(h->A, h->b, h->x, h->r, h->part, h->state, 0, h->st));
+  TRY(to_host(h, h->h_state, h->state, 1));
+  TRY(sync(h, "final residual"));
+  S.iters = h->h_state->iters;
+  S.rel_res_true = std::sqrt(h->h_state->tr / bnorm2);
+  S.rel_res_rec = std::sqrt(h->h_state->rr / bnorm2);
+  S.status = result;
+  if (result == SDSL_OK) return SDSL_OK;
+  return fail(result, result == SDSL_ERR_BREAKDOWN ? "BiCGSTAB breakdown (a zero or non-finite scalar)"
+                                                   : "BiCGSTAB reached maxit before the tolerance");
+}
+
 }  // namespace
 
 // ========================================================================= ABI
@@ -1488,7 +1616,8 @@ sdsl_status sdsl_setup(const sdsl_options* opt, int64_t m, int64_t n, const int6
   if (!opt) return fail(SDSL_ERR_ARG, "options are NULL");
   if (m < 0 || n < 0 || m >= INT32_MAX || n >= INT32_MAX) return fail(SDSL_ERR_ARG, "m, n must be in [0, 2^31-1)");
   if (opt->form < SDSL_FORM_CSR || opt->form > SDSL_FORM_AUGMENTED) return fail(SDSL_ERR_ARG, "unknown form");
-  if (opt->method != SDSL_BJ_PCG && opt->method != SDSL_BBD_GMRES) return fail(SDSL_ERR_ARG, "unknown method");
+  if (opt->method != SDSL_BJ_PCG && opt->method != SDSL_BBD_GMRES && opt->method != SDSL_BJ_BICGSTAB)
+    return fail(SDSL_ERR_ARG, "unknown method");
   if (opt->factor_prec != 64 && opt->factor_prec != 32) return fail(SDSL_ERR_ARG, "factor_prec must be 64 or 32");
   if (opt->solve_kernel < 0 || opt->solve_kernel > 3) return fail(SDSL_ERR_ARG, "solve_kernel must be 0..3");
   if (opt->spmv_form < 0 || opt->spmv_form > 3) return fail(SDSL_ERR_ARG, "spmv_form must be in 0..3");
@@ -1633,7 +1762,9 @@ sdsl_status sdsl_solve(sdsl_handle h, const double* b, double* x, int x0_zero, s
   TRY(to_dev(h, h->b, b, h->N));
   if (x0_zero) TRY_CUDA(cudaMemsetAsync(h->x, 0, sizeof(double) * (size_t)h->N, h->st));
   else TRY(to_dev(h, h->x, (const double*)x, h->N));
-  sdsl_status s = h->method == SDSL_BBD_GMRES ? gmres_solve(h) : pcg_solve(h, st);
+  sdsl_status s = h->method == SDSL_BBD_GMRES      ? gmres_solve(h)
+                  : h->method == SDSL_BJ_BICGSTAB ? bicg_solve(h)
+                                                  : pcg_solve(h, st);
   TRY(to_host(h, x, h->x, h->N));
   cudaEventRecord(h->ev_b, h->st);
   TRY(sync(h, "solve end"));

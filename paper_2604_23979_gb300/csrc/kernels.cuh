@@ -103,6 +103,19 @@ struct PcgState {
   unsigned int ticket[4];
 };
 
+// Device scalars of BiCGSTAB (bicgstab.cu); iters, alpha, done, err, tol2
+// and rr live in the solve's PcgState.
+constexpr int kBicgMaxCtas = 152 * 4;
+struct BicgScalars {
+  double rho;      // rt . r of the current pass
+  double omega, beta;
+  double rv, ts, tt;
+  double* part;    // 2 x kBicgMaxCtas partial sums
+  long long maxit;
+  int first;       // 1: the next pass starts with p = r
+  unsigned int ticket;
+};
+
 struct TriSolve {  // block triangular factors on the layout of P
   int64_t nblocks;
   const int64_t* bp;
@@ -265,6 +278,17 @@ cudaError_t true_residual(const SpmvPlan& A, const double* b, const double* x, d
 // ||a||^2 -> *out; part holds up to 608 partials, *ticket must start at 0.
 cudaError_t norm2_sq(int64_t n, const double* a, double* part, double* out, unsigned int* ticket, cudaStream_t st);
 cudaError_t pcg_init_state(PcgState* s, double tol2, long long maxit, cudaStream_t st);
+
+// ---- bicgstab.cu: the vector steps of right-preconditioned BiCGSTAB
+cudaError_t bicg_init(BicgScalars* c, long long maxit, cudaStream_t st);
+// rt = r, rho = r . r, first pass next (a start or a restart).
+cudaError_t bicg_restart(int64_t n, const double* r, double* rt, BicgScalars* c, cudaStream_t st);
+cudaError_t bicg_direction(int64_t n, const double* r, const double* v, double* p, const PcgState* s,
+                           const BicgScalars* c, cudaStream_t st);
+cudaError_t bicg_alpha(int64_t n, const double* rt, const double* v, PcgState* s, BicgScalars* c, cudaStream_t st);
+cudaError_t bicg_omega(int64_t n, const double* t, const double* sv, PcgState* s, BicgScalars* c, cudaStream_t st);
+cudaError_t bicg_finish(int64_t n, const double* sh, const double* t, const double* rt, double* x, double* r,
+                        PcgState* s, BicgScalars* c, cudaStream_t st);
 
 // ---- bbd.cu: BBD Schur complement, dense border LU, BBD apply, GMRES helpers
 cudaError_t schur_init(int64_t nb, int64_t b0, const int64_t* prp, const int32_t* pci, const double* pv, double* SB,
