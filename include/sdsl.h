@@ -80,7 +80,9 @@ typedef struct {
                                     last build; 0 disables automatic rebuilds */
   int mem_space;                 /* SDSL_MEM_HOST or SDSL_MEM_DEVICE for matrix/vector pointers */
   void* stream;                  /* cudaStream_t to order all work on; NULL = the legacy default stream */
-  int graph_iters;               /* Krylov iterations captured per CUDA graph launch; 0 = no graphs */
+  int graph_iters;               /* Krylov iterations captured per CUDA graph launch; 0 = no graphs
+                                    (BiCGSTAB captures at most 4 passes: the applies and products of
+                                    passes after the converged one still run) */
   int tune;                      /* 1 = time candidate launch shapes at factor time and keep the fastest */
   int profile;                   /* 1 = time every Krylov kernel with CUDA events (no graphs; slower) */
   int apply_prec;                /* arithmetic of the triangular solves: 64 or 32; 0 = factor_prec
