@@ -87,6 +87,8 @@ def _bind(L):
         L.or_bicgstab_pre.argtypes = [C.c_int, _I64, _i64p, _i32p, _f64p, _i64p, _i32p, _VP, _VP, _I64, _VP,
                                       _f64p, _f64p, _F64, _I64, _i64p, _f64p]
         L.or_bicgstab_pre.restype = C.c_int
+        L.or_gcr_pre.argtypes = L.or_gmres_pre.argtypes
+        L.or_gcr_pre.restype = C.c_int
     return L
 
 
@@ -376,6 +378,31 @@ def bicgstab(S, b, kind=PRE_NONE, P=None, F=None, block_ptr=None, x0=None, rtol=
     st = lib().or_bicgstab_pre(int(kind), S.nrows, S.rowptr, S.col, S.val, Pm.rowptr, Pm.col,
                                p(Pm.val, np.float64), p(F, np.float64), len(bp) - 1, p(bp, np.int64),
                                _c(b, np.float64), x, float(rtol), int(maxit), it, out)
+    return SolveResult(x, int(it[0]), float(out[0]), float(out[1]), st)
+
+
+def gcr(K, b, kind=PRE_NONE, P=None, F=None, block_ptr=None, lu=None, ipiv=None, x0=None, rtol=1e-8,
+        maxit=3000, restart=30) -> SolveResult:
+    """Restarted right-preconditioned GCR(restart), the "IGCR(m)" of Sec. 4.3."""
+    K = as_mat(K)
+    x = np.zeros(K.nrows) if x0 is None else _c(x0, np.float64).copy()
+    it = np.zeros(1, np.int64)
+    out = np.zeros(2)
+    keep = []
+
+    def p(a, dt):
+        if a is None:
+            return None
+        a = _c(a, dt)
+        keep.append(a)
+        return a.ctypes.data_as(_VP)
+
+    Pm = as_mat(P) if P is not None else K
+    bp = _c(block_ptr if block_ptr is not None else np.zeros(1, np.int64), np.int64)
+    st = lib().or_gcr_pre(int(kind), K.nrows, K.rowptr, K.col, K.val, Pm.rowptr, Pm.col, p(Pm.val, np.float64),
+                          p(F, np.float64), len(bp) - 1, p(bp, np.int64),
+                          p(None if lu is None else np.asarray(lu).reshape(-1), np.float64), p(ipiv, np.int32),
+                          _c(b, np.float64), x, float(rtol), int(maxit), int(restart), it, out)
     return SolveResult(x, int(it[0]), float(out[0]), float(out[1]), st)
 
 

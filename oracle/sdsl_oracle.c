@@ -24,7 +24,9 @@
  *   or_bbd_* / or_gmres  BBD Schur complement, block solve (Sec. 2.4) and
  *                      right-preconditioned restarted GMRES (Sec. 2.2);
  *   or_bicgstab        right-preconditioned BiCGSTAB, the method paired with
- *                      Block Jacobi in Sec. 4.3 (van der Vorst 1992).
+ *                      Block Jacobi in Sec. 4.3 (van der Vorst 1992);
+ *   or_gcr             restarted right-preconditioned GCR(m), the "IGCR(m)"
+ *                      paired with BBD in Sec. 4.3 (Eisenstat et al. 1983).
  *
  * Conventions: CSR with int64 row pointers, int32 sorted column indices,
  * double values.  Blocks are contiguous index ranges block_ptr[b] ..
@@ -916,6 +918,69 @@ done:
   return status;
 }
 
+/* Restarted, right-preconditioned GCR(m) (Eisenstat, Elman and Schultz,
+ * SIAM J. Numer. Anal. 20, 1983), the "IGCR(m)" the paper pairs with BBD
+ * (Sec. 4.2, 4.3).  Step j of a cycle:
+ *   p_j = M^{-1} r,  q_j = S p_j
+ *   for i < j (modified Gram-Schmidt on the images):
+ *       c = q_i . q_j,  q_j = q_j - c q_i,  p_j = p_j - c p_i
+ *   d = ||q_j||,  q_j = q_j / d,  p_j = p_j / d
+ *   a = q_j . r,  x = x + a p_j,  r = r - a q_j
+ * so the q_i are orthonormal and S p_i = q_i; the iterate minimises
+ * ||b - S x|| over the directions of the cycle.  The count is the number of
+ * steps (products S p).  A cycle ends after m steps, on ||r|| <= rtol ||b||
+ * (confirmed with the true residual; the next cycle starts from it) or when
+ * q_j vanishes (breakdown). */
+int or_gcr(int64_t n, const int64_t* rp, const int32_t* ci, const double* v, const or_precond* M,
+           const double* b, double* x, double rtol, int64_t maxit, int64_t restart, int64_t* iters, double* out) {
+  int64_t m = restart > 0 ? restart : 1;
+  size_t sz = sizeof(double) * (size_t)(n > 0 ? n : 1);
+  double* P = (double*)malloc(sz * (size_t)m);
+  double* Q = (double*)malloc(sz * (size_t)m);
+  double* r = (double*)malloc(sz);
+  double* t = (double*)malloc(sz);
+  int status = OR_NOT_CONVERGED;
+  int64_t it = 0;
+  double bnorm = nrm2(n, b), tol = rtol * bnorm, rnorm = 0.0, tnorm = 0.0;
+  if (bnorm == 0.0) { for (int64_t i = 0; i < n; ++i) x[i] = 0.0; status = OR_OK; goto done; }
+  for (;;) {
+    or_spmv(n, rp, ci, v, x, t);
+    for (int64_t i = 0; i < n; ++i) r[i] = b[i] - t[i];
+    rnorm = tnorm = nrm2(n, r);
+    if (tnorm <= tol) { status = OR_OK; break; }
+    if (it >= maxit) break;
+    int breakdown = 0;
+    for (int64_t j = 0; j < m && it < maxit; ++j) {
+      double* pj = P + j * n;
+      double* qj = Q + j * n;
+      precond_apply(M, r, pj);
+      or_spmv(n, rp, ci, v, pj, qj);
+      ++it;
+      for (int64_t i = 0; i < j; ++i) {
+        double c = dot(n, Q + i * n, qj);
+        for (int64_t l = 0; l < n; ++l) { qj[l] = qj[l] - c * Q[i * n + l]; pj[l] = pj[l] - c * P[i * n + l]; }
+      }
+      double d = nrm2(n, qj);
+      if (!(d > 0.0) || !isfinite(d)) { breakdown = 1; break; }
+      for (int64_t l = 0; l < n; ++l) { qj[l] = qj[l] / d; pj[l] = pj[l] / d; }
+      double a = dot(n, qj, r);
+      for (int64_t l = 0; l < n; ++l) { x[l] = x[l] + a * pj[l]; r[l] = r[l] - a * qj[l]; }
+      rnorm = nrm2(n, r);
+      if (rnorm <= tol) break;
+    }
+    if (breakdown) { status = OR_BREAKDOWN; break; }
+  }
+  or_spmv(n, rp, ci, v, x, t);
+  for (int64_t i = 0; i < n; ++i) t[i] = b[i] - t[i];
+  tnorm = nrm2(n, t);
+done:
+  *iters = it;
+  out[0] = bnorm > 0.0 ? tnorm / bnorm : 0.0;
+  out[1] = bnorm > 0.0 ? rnorm / bnorm : 0.0;
+  free(P); free(Q); free(r); free(t);
+  return status;
+}
+
 /* Entry points that build the preconditioner descriptor for Python callers. */
 int or_pcg_bj(int64_t n, const int64_t* rp, const int32_t* ci, const double* v, const int64_t* prp,
               const int32_t* pci, const double* F, int64_t nblocks, const int64_t* block_ptr,
@@ -947,6 +1012,15 @@ int or_bicgstab_pre(int kind, int64_t n, const int64_t* rp, const int32_t* ci, c
                     int64_t maxit, int64_t* iters, double* out) {
   or_precond M = {kind, n, prp, pci, pv, F, nblocks, block_ptr, NULL, NULL};
   return or_bicgstab(n, rp, ci, v, &M, b, x, rtol, maxit, iters, out);
+}
+
+int or_gcr_pre(int kind, int64_t n, const int64_t* rp, const int32_t* ci, const double* v,
+               const int64_t* prp, const int32_t* pci, const double* pv, const double* F,
+               int64_t nblocks, const int64_t* block_ptr, const double* lu, const int32_t* ipiv,
+               const double* b, double* x, double rtol, int64_t maxit, int64_t restart,
+               int64_t* iters, double* out) {
+  or_precond M = {kind, n, prp, pci, pv, F, nblocks, block_ptr, lu, ipiv};
+  return or_gcr(n, rp, ci, v, &M, b, x, rtol, maxit, restart, iters, out);
 }
 
 void or_precond_apply(int kind, int64_t n, const int64_t* prp, const int32_t* pci, const double* pv,

@@ -53,6 +53,13 @@ MUTANTS = [
      [lambda o: pins.test_bicgstab_terminates_after_k_passes(o, 3)]),
     ("bicgstab-s-sign", "r[i] = r[i] - alpha * vv[i];", "r[i] = r[i] + alpha * vv[i];",
      [pins.test_bicgstab_identity_one_half_pass]),
+    ("gcr-direction-sign", "pj[l] = pj[l] - c * P[i * n + l];", "pj[l] = pj[l] + c * P[i * n + l];",
+     [pins.test_gcr_minimal_residual]),
+    ("gcr-no-preconditioner", "precond_apply(M, r, pj);", "memcpy(pj, r, sz);",
+     [pins.test_gcr_right_preconditioned_minimal_residual]),
+    ("gcr-step-operand", "double a = dot(n, qj, r);", "double a = dot(n, pj, r);",
+     [pins.test_gcr_minimal_residual]),
+    ("gcr-normalise", "pj[l] = pj[l] / d;", "pj[l] = pj[l] * d;", [pins.test_gcr_minimal_residual]),
 ]
 
 

@@ -740,3 +740,118 @@ def test_bbd_gmres_small_kkt(orc):
     res = orc.gmres(K, p.b, orc.PRE_BBD, P, F, kbp, lu, ipiv, maxit=3000)
     assert res.status == 0
     assert np.linalg.norm(p.b - K.dense() @ res.x) / np.linalg.norm(p.b) <= 1e-8
+
+
+# ------------------------------------------------ GCR(m), "IGCR(m)" (Sec. 4.3)
+
+def _krylov_min_residual(D, Minv, b, k):
+    """min ||b - D Minv V y|| over the k-dimensional Krylov space of D Minv
+    from b (right preconditioning), by a dense least-squares solve."""
+    n = len(b)
+    Kry = np.empty((n, k))
+    v = b.copy()
+    for j in range(k):
+        Kry[:, j] = v
+        v = D @ (Minv @ v)
+    Q, _ = np.linalg.qr(Kry)
+    y, *_ = np.linalg.lstsq(D @ Minv @ Q, b, rcond=None)
+    return np.linalg.norm(b - D @ Minv @ Q @ y) / np.linalg.norm(b), Minv @ Q @ y
+
+
+def test_gcr_minimal_residual(orc):
+    """Each step of a cycle minimises ||b - K x|| over the Krylov space (the
+    GMRES property); the recurrence residual is the same value."""
+    rng = np.random.default_rng(120)
+    n = 20
+    D = rng.standard_normal((n, n)) + 3 * np.eye(n)
+    K = orc.from_dense(D)
+    b = rng.standard_normal(n)
+    for k in range(1, 9):
+        res = orc.gcr(K, b, rtol=1e-300, maxit=k, restart=30)
+        best, xbest = _krylov_min_residual(D, np.eye(n), b, k)
+        assert res.iters == k and res.status == 5
+        assert res.relres_true == pytest.approx(best, rel=1e-7)
+        assert res.relres_rec == pytest.approx(best, rel=1e-7)
+        np.testing.assert_allclose(res.x, xbest, rtol=1e-7, atol=1e-10)
+
+
+def test_gcr_right_preconditioned_minimal_residual(orc):
+    """With a Block-Jacobi ILU(0) preconditioner (three blocks, not exact),
+    the iterate is M^-1 times the minimiser over the Krylov space of K M^-1."""
+    rng = np.random.default_rng(121)
+    n = 24
+    D = rng.standard_normal((n, n)) * (rng.random((n, n)) < 0.3) + 5 * np.eye(n)
+    K = orc.from_dense(D)
+    bp = np.array([0, 8, 15, n])
+    F, _, _ = orc.ilu0(K, bp)
+    Minv = np.column_stack([orc.precond_apply(orc.PRE_BJ_ILU0, K, F, bp, e) for e in np.eye(n)])
+    b = rng.standard_normal(n)
+    for k in (1, 3, 6):
+        res = orc.gcr(K, b, orc.PRE_BJ_ILU0, K, F, bp, rtol=1e-300, maxit=k, restart=30)
+        best, xbest = _krylov_min_residual(D, Minv, b, k)
+        assert res.relres_true == pytest.approx(best, rel=1e-7)
+        np.testing.assert_allclose(res.x, xbest, rtol=1e-7, atol=1e-10)
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 4])
+def test_gcr_terminates_after_k_steps(orc, k):
+    rng = np.random.default_rng(122 + k)
+    n = 24
+    D = _distinct_eigen(rng, n, [1.0, 2.5, 4.0, 7.0][:k])
+    b = rng.standard_normal(n)
+    res = orc.gcr(orc.from_dense(D), b, rtol=1e-9)
+    assert res.status == 0 and res.iters == k
+    np.testing.assert_allclose(res.x, np.linalg.solve(D, b), rtol=1e-8, atol=1e-10)
+
+
+def test_gcr_exact_preconditioner_one_step(orc):
+    rng = np.random.default_rng(126)
+    n = 20
+    D = rng.standard_normal((n, n)) + 8 * np.eye(n)
+    K = orc.from_dense(D)
+    bp = np.array([0, n])
+    F, _, _ = orc.ilu0(K, bp)
+    res = orc.gcr(K, rng.standard_normal(n), orc.PRE_BJ_ILU0, K, F, bp)
+    assert res.status == 0 and res.iters == 1
+
+
+def test_gcr_restarts(orc):
+    rng = np.random.default_rng(127)
+    n = 60
+    D = rng.standard_normal((n, n)) + 4 * np.sqrt(n) * np.eye(n)
+    b = rng.standard_normal(n)
+    res = orc.gcr(orc.from_dense(D), b, rtol=1e-10, restart=5)
+    assert res.status == 0 and res.iters > 5
+    assert np.linalg.norm(b - D @ res.x) / np.linalg.norm(b) <= 1e-10
+
+
+def test_gcr_bbd_small_kkt(orc):
+    """The BBD preconditioner on a small, mildly scaled KKT system: GCR(30)
+    reaches the 1e-8 true residual and the dense solution."""
+    from paper_2604_23979_gb300 import workloads as W
+    p = W.config3(seed=5, scale=0.002, nblocks=3, nlink=5, link_frac=0.3)
+    rng = np.random.default_rng(0)
+    p.theta = np.exp(rng.uniform(np.log(1e-2), np.log(1e2), len(p.theta)))
+    p.rho = 1e-2
+    K, pos, kbp = orc.augmented(p.A, p.theta, p.rho, p.row_block_ptr, p.col_block_ptr)
+    P = orc.filter_correct(K, kbp, p.tau, p.delta, whole=True)
+    F, alpha, st = orc.ilu0(P, kbp)
+    lu, ipiv, _ = orc.dense_lu(orc.bbd_schur(P, F, kbp))
+    res = orc.gcr(K, p.b, orc.PRE_BBD, P, F, kbp, lu, ipiv, maxit=3000)
+    Kd = K.dense()
+    assert res.status == 0
+    assert np.linalg.norm(p.b - Kd @ res.x) / np.linalg.norm(p.b) <= 1e-8
+    ref = np.linalg.solve(Kd, p.b)
+    assert np.linalg.norm(res.x - ref) / np.linalg.norm(ref) <= 1e-5
+
+
+def test_gcr_edge_cases(orc):
+    n = 10
+    S = orc.from_dense(2 * np.eye(n))
+    res = orc.gcr(S, np.zeros(n))
+    assert res.status == 0 and res.iters == 0 and not res.x.any()
+    b = np.ones(n)
+    res = orc.gcr(S, b, x0=b / 2)
+    assert res.status == 0 and res.iters == 0
+    res = orc.gcr(S, b, maxit=0)
+    assert res.status == 5 and res.iters == 0
