@@ -34,6 +34,12 @@ MUTANTS = [
     ("ic0-diag-term", "dsum = dsum - F[q] * F[q];", "dsum = dsum - F[q] * F[q] * 0.5;",
      [pins.test_ic0_tridiagonal_equals_cholesky]),
     ("ilu0-divide", "F[p] = F[p] / F[kd];", "F[p] = F[p] * F[kd];", [pins.test_ilu0_dense_equals_lu]),
+    ("ilu0-no-shift", "F[p] = (j == i) ? shifted(pv[p], alpha) : pv[p];", "F[p] = pv[p];",
+     [pins.test_ilu0_shift_retry_and_breakdown]),
+    ("ilu0-zero-pivot-accepted", "if (F[dpos] == 0.0 || !isfinite(F[dpos])) return 1;",
+     "if (!isfinite(F[dpos])) return 1;", [pins.test_ilu0_shift_retry_and_breakdown]),
+    ("ilu0-shift-sign", "return alpha == 0.0 ? pii : pii + alpha * pii;", "return alpha == 0.0 ? pii : pii - alpha * pii;",
+     [pins.test_ilu0_shift_retry_and_breakdown]),
     ("pcg-beta", "double beta = rho_new / rho;", "double beta = rho / rho_new;",
      [pins.test_pcg_matches_dense_solve]),
     ("pcg-alpha", "double alpha = rho / pq;", "double alpha = pq / rho;", [pins.test_pcg_matches_dense_solve]),

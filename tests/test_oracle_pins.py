@@ -360,6 +360,44 @@ def test_ic0_shift_retry_and_breakdown(orc):
     assert st == orc.BREAKDOWN and alpha[0] == -1
 
 
+def test_ilu0_shift_retry_and_breakdown(orc):
+    """The ILU(0) shift ladder (the breakdown rule for the BBD block factors).
+
+    By hand, in exact dyadic arithmetic: A = [[1,1,0],[1,2,1],[0,1,1]] is
+    tridiagonal (fill-closed, so ILU(0) = LU without pivoting) with u11 = 1,
+    l21 = 1, u22 = 2 - 1 = 1, l32 = 1, u33 = 1 - 1 = 0: the unshifted factor
+    has a zero last pivot.  With alpha = 1e-3 the diagonal becomes 1.001,
+    2.002, 1.001 and u33 = 1.001 - 1/(2.002 - 1/1.001) ~ 0.004 != 0, so the
+    ladder stops at its second rung."""
+    A = np.array([[1.0, 1.0, 0.0], [1.0, 2.0, 1.0], [0.0, 1.0, 1.0]])
+    P = orc.from_dense(A)
+    # the unshifted rung alone breaks down (zero pivot, not a non-finite one)
+    F0, alpha0, st0 = orc.ilu0(P, np.array([0, 3]), shifts=[0.0])
+    assert st0 == orc.BREAKDOWN and alpha0[0] == -1
+    F, alpha, st = orc.ilu0(P, np.array([0, 3]))
+    assert st == 0 and alpha[0] == 1e-3
+    # the factor reproduces the shifted matrix A + alpha diag(A) on the pattern
+    Ash = A + 1e-3 * np.diag(np.diag(A))
+    Fm = orc.Mat(3, 3, P.rowptr, P.col, F).dense()
+    L = np.tril(Fm, -1) + np.eye(3)
+    U = np.triu(Fm)
+    np.testing.assert_allclose((L @ U)[A != 0], Ash[A != 0], rtol=1e-13)
+    u33 = 1.001 - 1.0 / (2.002 - 1.0 / 1.001)
+    np.testing.assert_allclose(U[2, 2], u33, rtol=1e-10)
+    # a second block that needs no shift keeps alpha = 0 (the rule is per block)
+    B = np.zeros((5, 5))
+    B[:3, :3] = A
+    B[3:, 3:] = [[4.0, 1.0], [1.0, 4.0]]
+    F2, alpha2, st2 = orc.ilu0(orc.from_dense(B), np.array([0, 3, 5]))
+    assert st2 == 0 and list(alpha2) == [1e-3, 0.0]
+    # a zero diagonal defeats every shift (alpha p_ii = 0): breakdown
+    F, alpha, st = orc.ilu0(orc.from_dense(np.array([[0.0, 1.0], [1.0, 0.0]])), np.array([0, 2]))
+    assert st == orc.BREAKDOWN and alpha[0] == -1
+    # a non-finite pivot is a breakdown too (l21 overflows for every shift)
+    F, alpha, st = orc.ilu0(orc.from_dense(np.array([[1e-300, 1e300], [1e300, 1.0]])), np.array([0, 2]))
+    assert st == orc.BREAKDOWN and alpha[0] == -1
+
+
 def test_ilu0_dense_equals_lu(orc):
     rng = np.random.default_rng(60)
     n = 14
