@@ -76,8 +76,11 @@ typedef struct {
   double rtol;                   /* relative residual target ||b - A x|| / ||b|| (1e-8 in Sec. 4) */
   int64_t maxit;                 /* iteration cap (products with the system matrix) */
   int restart;                   /* GMRES restart length m */
-  double refactor_ratio;         /* reuse rule (Sec. 3.4): rebuild when iters > ratio * iters after the
-                                    last build; 0 disables automatic rebuilds */
+  double refactor_ratio;         /* reuse rule (Sec. 3.4): rebuild before the next solve when a converged
+                                    solve needs more than ratio * the iterations of the first converged solve
+                                    after the last build, or when a solve does not converge; a solve that does
+                                    not converge under a reused preconditioner is repeated after a rebuild in
+                                    the same call.  0 disables automatic rebuilds */
   int mem_space;                 /* SDSL_MEM_HOST or SDSL_MEM_DEVICE for matrix/vector pointers */
   void* stream;                  /* cudaStream_t to order all work on; NULL = the legacy default stream */
   int graph_iters;               /* Krylov iterations captured per CUDA graph launch; 0 = no graphs
@@ -85,8 +88,11 @@ typedef struct {
                                     passes after the converged one still run) */
   int tune;                      /* 1 = time candidate launch shapes at factor time and keep the fastest */
   int profile;                   /* 1 = time every Krylov kernel with CUDA events (no graphs; slower) */
-  int apply_prec;                /* arithmetic of the triangular solves: 64 or 32; 0 = factor_prec
-                                    (BiCGSTAB: 0 = 64, its recurrences assume a fixed linear M) */
+  int apply_prec;                /* arithmetic of the triangular solves with FP32 factors: 32 (FP32),
+                                    48 (float-float: pairs of FP32 numbers with error-free products and
+                                    compensated sums, linear to ~1e-14; staged solves only) or 64 (FP64);
+                                    0 = auto: 48 with FP32 factors where the staged solves run, else 64.
+                                    FP64 factors are always applied in FP64 */
   int flexible;                  /* PCG beta: 0 = rho_new/rho, 1 = flexible z_new^T(r_new - r_old)/rho
                                     (robust to an FP32 apply); -1 = 1 iff the apply is FP32 */
   int solve_kernel;              /* block triangular solves: 0 auto, 1 level-synchronous (barrier per
@@ -107,6 +113,9 @@ typedef struct {
   int sweep_wait;                /* readiness in those sweeps: 0 auto, 1 per value (a tile waits until every
                                     value it reads is solved), 2 per level (a tile waits until the previous
                                     level of its block is complete, one shared counter per level) */
+  int wait_limit;                /* polls after which a wait in those sweeps gives up and the solve returns
+                                    SDSL_ERR_TIMEOUT; 0 = default (2^23 polls, about a second).  Small values
+                                    exist to exercise the timeout path */
 } sdsl_options;
 
 typedef struct {
@@ -139,6 +148,9 @@ typedef struct {
   double ms_schur;        /* BBD: device time of the border Schur complement assembly (part of ms_factor) */
   double ms_dense_lu;     /* BBD: device time of its dense FP32 LU (part of ms_factor) */
   double ms_dense_inverse; /* BBD: device time of the explicit FP32 inverse from that LU (part of ms_factor) */
+  int64_t iters_discarded; /* iterations of a first attempt of the last solve that did not converge under a
+                              reused preconditioner and was repeated after a rebuild (0 if none); ms_solve
+                              covers both attempts */
 } sdsl_stats;
 
 typedef struct {
@@ -186,9 +198,13 @@ sdsl_status sdsl_factor(sdsl_handle h);
 
 /* Solve A x = b to options.rtol (Krylov loop in FP64 on the device).  b and x
  * have the system dimension and live in options.mem_space; x is the initial
- * guess on entry unless x0_zero != 0, and the solution on exit.  If a reuse
- * rule is set and the last solve exceeded it, the preconditioner is rebuilt
- * first (st->rebuilt).  st may be NULL.  Errors: SDSL_ERR_STATE before
+ * guess on entry unless x0_zero != 0, and the solution on exit.  With a reuse
+ * rule set (refactor_ratio > 0, Sec. 3.4): if the last solve requested a
+ * rebuild the preconditioner is rebuilt first; if this solve does not
+ * converge under a preconditioner that earlier solves already used, the
+ * preconditioner is rebuilt from the current system and the solve repeated
+ * from the same initial guess (st->rebuilt = 1, st->iters_discarded = the
+ * first attempt's iterations).  st may be NULL.  Errors: SDSL_ERR_STATE before
  * sdsl_factor, SDSL_ERR_NOT_CONVERGED (x = last iterate), SDSL_ERR_BREAKDOWN. */
 sdsl_status sdsl_solve(sdsl_handle h, const double* b, double* x, int x0_zero, sdsl_stats* st);
 
@@ -251,10 +267,11 @@ sdsl_status sdsl_precond_apply(sdsl_handle h, const double* r, double* z);
  *   stream     cudaStream_t (NULL: the legacy default stream); the call only
  *              enqueues work and returns without synchronising.
  * The intermediate theta o (A^T x) lives in a file-scope __device__ array
- * of SDSL_NOALLOC_MAX_COLS doubles.  The first call on a device looks up that
- * array's address with the device current (the library's module is loaded
- * then if it was not yet), so make the first call on each device before any
- * stream capture begins.  All calls share the array: calls whose kernels
+ * of SDSL_NOALLOC_MAX_COLS doubles.  The first call on a device (and the
+ * first after its context was re-created, e.g. by cudaDeviceReset) looks up
+ * that array's address with the device current (the library's module is
+ * loaded then if it was not yet), so make that call before any stream
+ * capture begins.  All calls share the array: calls whose kernels
  * overlap on the GPU (different streams without ordering between them) race
  * on it.  Each call writes every scratch entry it reads, so nothing carries
  * over between calls.  Errors: SDSL_ERR_ARG for bad sizes, NULL pointers or

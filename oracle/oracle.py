@@ -25,6 +25,11 @@ _VP = C.c_void_p
 OK, ARG, OOM, BREAKDOWN, NOT_CONVERGED = 0, 1, 2, 4, 5
 
 
+def threads() -> int:
+    """Host threads the oracle's parallel block and row loops use (1 without OpenMP)."""
+    return int(lib().or_threads())
+
+
 def lib():
     global _lib
     if _lib is None:
@@ -72,6 +77,8 @@ def _bind(L):
         L.or_ic0_apply.argtypes = [_I64, _i64p, _i32p, _f64p, _I64, _i64p, _f64p, _f64p]
         L.or_ilu0_apply.argtypes = L.or_ic0_apply.argtypes
         L.or_spmv.argtypes = [_I64, _i64p, _i32p, _f64p, _f64p, _f64p]
+        L.or_threads.argtypes = []
+        L.or_threads.restype = C.c_int
         L.or_dense_lu.argtypes = [_I64, _f64p, _i32p]
         L.or_dense_lu.restype = C.c_int
         L.or_dense_lu_solve.argtypes = [_I64, _f64p, _i32p, _f64p]

@@ -37,6 +37,22 @@
 #include <stdlib.h>
 #include <string.h>
 
+/* Independent loops (rows of a product, blocks of a block-diagonal
+ * operation) run in parallel when the file is built with OpenMP; every
+ * reduction (dot products, norms, sums) stays serial in index order, and
+ * each parallel iteration writes only its own rows, so the results are the
+ * same bits with or without threads. */
+#if defined(_OPENMP)
+#include <omp.h>
+#define OR_PARALLEL_ROWS _Pragma("omp parallel for schedule(static)")
+#define OR_PARALLEL_BLOCKS _Pragma("omp parallel for schedule(dynamic, 1)")
+int or_threads(void) { return omp_get_max_threads(); }
+#else
+#define OR_PARALLEL_ROWS
+#define OR_PARALLEL_BLOCKS
+int or_threads(void) { return 1; }
+#endif
+
 #define OR_OK 0
 #define OR_BREAKDOWN 4
 #define OR_NOT_CONVERGED 5
@@ -144,6 +160,7 @@ void or_normal_values(int64_t m, int64_t n, const int64_t* rp, const int32_t* ci
                       const double* theta, double rho, const int64_t* srp, const int32_t* sci,
                       double* sv) {
   (void)n;
+  OR_PARALLEL_ROWS
   for (int64_t i = 0; i < m; ++i) {
     for (int64_t s = srp[i]; s < srp[i + 1]; ++s) {
       int64_t j = sci[s];
@@ -296,6 +313,7 @@ int64_t or_filter_correct(int64_t n, const int64_t* rp, const int32_t* ci, const
 void or_levels(int64_t n, const int64_t* rp, const int32_t* ci, int64_t nblocks,
                const int64_t* block_ptr, int32_t* lev_lo, int32_t* lev_up) {
   for (int64_t i = 0; i < n; ++i) { lev_lo[i] = -1; lev_up[i] = -1; }
+  OR_PARALLEL_BLOCKS
   for (int64_t b = 0; b < nblocks; ++b) {
     int64_t s = block_ptr[b], e = block_ptr[b + 1];
     for (int64_t i = s; i < e; ++i) {
@@ -391,6 +409,7 @@ int or_ic0(int64_t n, const int64_t* rp, const int32_t* ci, const double* pv, in
            const int64_t* block_ptr, const double* shifts, int nshifts, double* F, double* alpha_used) {
   (void)n;
   int status = OR_OK;
+  OR_PARALLEL_BLOCKS
   for (int64_t b = 0; b < nblocks; ++b) {
     alpha_used[b] = -1.0;
     for (int t = 0; t < nshifts; ++t) {
@@ -399,8 +418,9 @@ int or_ic0(int64_t n, const int64_t* rp, const int32_t* ci, const double* pv, in
         break;
       }
     }
-    if (alpha_used[b] < 0) status = OR_BREAKDOWN;
   }
+  for (int64_t b = 0; b < nblocks; ++b)
+    if (alpha_used[b] < 0) status = OR_BREAKDOWN;
   return status;
 }
 
@@ -444,6 +464,7 @@ int or_ilu0(int64_t n, const int64_t* rp, const int32_t* ci, const double* pv, i
             const int64_t* block_ptr, const double* shifts, int nshifts, double* F, double* alpha_used) {
   (void)n;
   int status = OR_OK;
+  OR_PARALLEL_BLOCKS
   for (int64_t b = 0; b < nblocks; ++b) {
     alpha_used[b] = -1.0;
     for (int t = 0; t < nshifts; ++t) {
@@ -452,8 +473,9 @@ int or_ilu0(int64_t n, const int64_t* rp, const int32_t* ci, const double* pv, i
         break;
       }
     }
-    if (alpha_used[b] < 0) status = OR_BREAKDOWN;
   }
+  for (int64_t b = 0; b < nblocks; ++b)
+    if (alpha_used[b] < 0) status = OR_BREAKDOWN;
   return status;
 }
 
@@ -465,6 +487,7 @@ int or_ilu0(int64_t n, const int64_t* rp, const int32_t* ci, const double* pv, i
 void or_ic0_apply(int64_t n, const int64_t* rp, const int32_t* ci, const double* F, int64_t nblocks,
                   const int64_t* block_ptr, const double* r, double* z) {
   (void)n;
+  OR_PARALLEL_BLOCKS
   for (int64_t b = 0; b < nblocks; ++b) {
     int64_t s = block_ptr[b], e = block_ptr[b + 1];
     /* forward: L y = r (y kept in z) */
@@ -528,6 +551,7 @@ static void ilu0_upper(const int64_t* rp, const int32_t* ci, const double* F, in
 void or_ilu0_apply(int64_t n, const int64_t* rp, const int32_t* ci, const double* F, int64_t nblocks,
                    const int64_t* block_ptr, const double* r, double* z) {
   double* y = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+  OR_PARALLEL_BLOCKS
   for (int64_t b = 0; b < nblocks; ++b) {
     ilu0_lower(rp, ci, F, block_ptr[b], block_ptr[b + 1], r, y);
     ilu0_upper(rp, ci, F, block_ptr[b], block_ptr[b + 1], y, z);
@@ -540,6 +564,7 @@ void or_ilu0_apply(int64_t n, const int64_t* rp, const int32_t* ci, const double
 /* ------------------------------------------------------------------ */
 
 void or_spmv(int64_t n, const int64_t* rp, const int32_t* ci, const double* v, const double* x, double* y) {
+  OR_PARALLEL_ROWS
   for (int64_t i = 0; i < n; ++i) {
     double acc = 0.0;
     for (int64_t p = rp[i]; p < rp[i + 1]; ++p) acc = acc + v[p] * x[ci[p]];

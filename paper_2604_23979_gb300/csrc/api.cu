@@ -174,7 +174,9 @@ struct sdsl_handle_s {
   std::vector<int32_t> h_lev_off_lo, h_lev_off_up;
   // reuse bookkeeping (Sec. 3.4)
   bool factored = false, need_rebuild = false;
-  int64_t iters_post_build = -1;
+  int64_t iters_post_build = -1;   // iterations of the first converged solve after the last build
+  int64_t solves_since_build = 0;
+  double* x0 = nullptr;            // the caller's initial guess, kept for a re-solve
   sdsl_stats stats{};
 };
 
@@ -234,6 +236,7 @@ sdsl_status alloc_workspace(sdsl_handle h) {
   const int64_t N = h->N;
   TRY(h->sys.get(&h->b, N));
   TRY(h->sys.get(&h->x, N));
+  TRY(h->sys.get(&h->x0, N));
   TRY(h->sys.get(&h->r, N));
   TRY(h->sys.get(&h->z, N));
   TRY(h->sys.get(&h->p, N));
@@ -1256,13 +1259,14 @@ sdsl_status factor_impl(sdsl_handle h) {
   }
   TRY(h->pc.get(&h->part_blk, 3 * nb + 32));
   // level-ordered packed triangles for the flag-synchronised solves
-  // Auto: FP32 arithmetic for FP32 factors under PCG (its flexible beta
-  // absorbs the rounding of an FP32 apply), FP64 arithmetic on the FP32
-  // values under BiCGSTAB, whose recurrences assume one fixed linear M.
-  const int apply = h->opt.apply_prec != 0 ? h->opt.apply_prec
-                    : (f32 && h->method != SDSL_BJ_BICGSTAB) ? 32 : 64;
+  // Auto: FP32-stored factors are applied in float-float arithmetic (48) by
+  // the staged sweeps -- one fixed linear operator to ~1e-14, as both PCG and
+  // BiCGSTAB assume, on the FP32 pipes; the other solve kernels apply them in
+  // FP64 arithmetic.  An FP32-arithmetic apply (32) is linear only to ~1e-7;
+  // PCG then needs the flexible beta.
+  int apply = h->opt.apply_prec != 0 ? h->opt.apply_prec : f32 ? 48 : 64;
+  if (!f32) apply = 64;
   M.apply_prec = apply;
-  M.flexible = h->opt.flexible < 0 ? (apply == 32 ? 1 : 0) : (h->opt.flexible ? 1 : 0);
   M.threads = 1024;
   const bool fits = sf_smem_bytes(maxb, apply == 32 ? 4 : 8) <= (size_t)200 * 1024;
   M.slot_bytes = apply == 32 ? 1536 : 1024;
@@ -1279,22 +1283,30 @@ sdsl_status factor_impl(sdsl_handle h) {
     }
     M.max_tiles = mt;
   }
-  const bool fits_tma = staged_smem_bytes(maxb, apply == 32 ? 4 : 8, 16, 1024, 2, M.max_tiles, 0) <= (size_t)225 * 1024;
-  if ((h->opt.solve_kernel == 2 && !fits) || (h->opt.solve_kernel == 3 && !fits_tma))
+  const bool fits_staged = staged_smem_bytes(maxb, apply == 32 ? 4 : 8, 16, 1024, 2, M.max_tiles, 0) <= (size_t)225 * 1024;
+  if ((h->opt.solve_kernel == 2 && !fits) || (h->opt.solve_kernel == 3 && !fits_staged))
     return fail(SDSL_ERR_ARG, "flag-synchronised solves need the largest block to fit in shared memory");
-  M.tma = (bj_method(h) && (h->opt.solve_kernel == 3 || (h->opt.solve_kernel == 0 && fits_tma))) ? 1 : 0;
+  M.staged = (bj_method(h) && (h->opt.solve_kernel == 3 || (h->opt.solve_kernel == 0 && fits_staged))) ? 1 : 0;
   M.sweep_warps = h->opt.sweep_warps > 0 ? h->opt.sweep_warps : 16;
   M.backoff_ns = h->opt.sweep_backoff_ns >= 0 ? h->opt.sweep_backoff_ns : 0;
-  if (M.tma) {
+  M.wait_limit = h->opt.wait_limit > 0 ? h->opt.wait_limit : (1 << 23);
+  if (M.staged) {
     bool ok = false;
     TRY(build_vtiles(h, f32, apply, &ok));
     if (!ok) {
       if (h->opt.solve_kernel == 3)
         return fail(SDSL_ERR_ARG, "staged solves need blocks of at most 65,535 rows that fit in shared memory");
-      M.tma = 0;
+      M.staged = 0;
     }
   }
-  M.sync_free = (bj_method(h) && !M.tma && (h->opt.solve_kernel == 2 || (h->opt.solve_kernel == 0 && fits)))
+  // float-float arithmetic exists in the staged sweeps only
+  if (M.apply_prec == 48 && !M.staged) {
+    if (h->opt.apply_prec == 48)
+      return fail(SDSL_ERR_ARG, "the float-float apply (apply_prec 48) needs the staged solves (solve_kernel 0 or 3)");
+    M.apply_prec = 64;
+  }
+  M.flexible = h->opt.flexible < 0 ? (M.apply_prec == 32 ? 1 : 0) : (h->opt.flexible ? 1 : 0);
+  M.sync_free = (bj_method(h) && !M.staged && (h->opt.solve_kernel == 2 || (h->opt.solve_kernel == 0 && fits)))
                     ? 1 : 0;
   if (M.sync_free) {
     M.lanes = sweep_lanes;
@@ -1354,6 +1366,7 @@ sdsl_status factor_impl(sdsl_handle h) {
   h->factored = true;
   h->need_rebuild = false;
   h->iters_post_build = -1;
+  h->solves_since_build = 0;
   h->stats.ms_factor = elapsed(h);
   h->stats.nnz_precond = h->p_nnz;
   h->stats.nnz_factor = h->method == SDSL_BBD_GMRES ? h->p_nnz : (h->p_nnz + N) / 2;
@@ -1629,10 +1642,11 @@ sdsl_status sdsl_setup(const sdsl_options* opt, int64_t m, int64_t n, const int6
     return fail(SDSL_ERR_ARG, "sweep_lane_entries must be in 0..64");
   if (opt->sweep_wait < 0 || opt->sweep_wait > 2) return fail(SDSL_ERR_ARG, "sweep_wait must be in 0..2");
   if (opt->schur_lu < 0 || opt->schur_lu > 2) return fail(SDSL_ERR_ARG, "schur_lu must be in 0..2");
-  if (opt->apply_prec != 0 && opt->apply_prec != 64 && opt->apply_prec != 32)
-    return fail(SDSL_ERR_ARG, "apply_prec must be 0, 32 or 64");
-  if (opt->factor_prec == 64 && opt->apply_prec == 32)
-    return fail(SDSL_ERR_ARG, "an FP32 apply needs FP32 factors (factor_prec 32)");
+  if (opt->wait_limit < 0) return fail(SDSL_ERR_ARG, "wait_limit must be >= 0");
+  if (opt->apply_prec != 0 && opt->apply_prec != 64 && opt->apply_prec != 48 && opt->apply_prec != 32)
+    return fail(SDSL_ERR_ARG, "apply_prec must be 0, 32, 48 or 64");
+  if (opt->factor_prec == 64 && (opt->apply_prec == 32 || opt->apply_prec == 48))
+    return fail(SDSL_ERR_ARG, "an FP32 or float-float apply needs FP32 factors (factor_prec 32)");
   if (!(opt->tau >= 0.0) || !(opt->delta >= 0.0) || !(opt->rtol > 0.0) || opt->maxit < 0)
     return fail(SDSL_ERR_ARG, "tau, delta must be >= 0, rtol > 0, maxit >= 0");
   if (opt->form == SDSL_FORM_CSR && m != n) return fail(SDSL_ERR_ARG, "CSR form needs a square matrix");
@@ -1758,25 +1772,55 @@ sdsl_status sdsl_solve(sdsl_handle h, const double* b, double* x, int x0_zero, s
     TRY(factor_impl(h));
     rebuilt = 1;
   }
-  cudaEventRecord(h->ev_a, h->st);
   TRY(to_dev(h, h->b, b, h->N));
-  if (x0_zero) TRY_CUDA(cudaMemsetAsync(h->x, 0, sizeof(double) * (size_t)h->N, h->st));
-  else TRY(to_dev(h, h->x, (const double*)x, h->N));
-  sdsl_status s = h->method == SDSL_BBD_GMRES      ? gmres_solve(h)
-                  : h->method == SDSL_BJ_BICGSTAB ? bicg_solve(h)
-                                                  : pcg_solve(h, st);
+  if (!x0_zero) TRY(to_dev(h, h->x0, (const double*)x, h->N));
+  // One Krylov solve from the initial guess (x0 or zero); ms_solve is its
+  // device time.
+  auto attempt = [&]() -> sdsl_status {
+    cudaEventRecord(h->ev_a, h->st);
+    if (x0_zero) TRY_CUDA(cudaMemsetAsync(h->x, 0, sizeof(double) * (size_t)h->N, h->st));
+    else TRY_CUDA(cudaMemcpyAsync(h->x, h->x0, sizeof(double) * (size_t)h->N, cudaMemcpyDeviceToDevice, h->st));
+    sdsl_status s = h->method == SDSL_BBD_GMRES      ? gmres_solve(h)
+                    : h->method == SDSL_BJ_BICGSTAB ? bicg_solve(h)
+                                                    : pcg_solve(h, st);
+    cudaEventRecord(h->ev_b, h->st);
+    sdsl_status e = sync(h, "solve end");
+    if (e != SDSL_OK) return e;
+    h->stats.ms_solve = elapsed(h);
+    return s;
+  };
+  const bool reused = h->solves_since_build > 0;
+  sdsl_status s = attempt();
+  int64_t discarded = 0;
+  // Reuse rule (Sec. 3.4), failure branch: a reused preconditioner under
+  // which the solve did not converge is rebuilt from the current system and
+  // the solve is repeated from the caller's initial guess in this call.
+  if ((s == SDSL_ERR_NOT_CONVERGED || s == SDSL_ERR_BREAKDOWN) && reused && h->opt.refactor_ratio > 0.0) {
+    discarded = h->stats.iters;
+    const double ms_first = h->stats.ms_solve;
+    TRY(factor_impl(h));
+    rebuilt = 1;
+    s = attempt();
+    h->stats.ms_solve += ms_first;
+  }
+  h->solves_since_build += 1;
   TRY(to_host(h, x, h->x, h->N));
-  cudaEventRecord(h->ev_b, h->st);
-  TRY(sync(h, "solve end"));
-  h->stats.ms_solve = elapsed(h);
+  TRY(sync(h, "solve copy-out"));
   h->stats.rebuilt = rebuilt;
-  // reuse rule (Sec. 3.4): remember the first solve after a build; request a
-  // rebuild once a later solve needs more than ratio times as many iterations
-  if (s == SDSL_OK || s == SDSL_ERR_NOT_CONVERGED) {
-    if (h->iters_post_build < 0) h->iters_post_build = h->stats.iters;
-    else if (h->opt.refactor_ratio > 0.0 &&
-             (double)h->stats.iters > h->opt.refactor_ratio * (double)h->iters_post_build)
+  h->stats.iters_discarded = discarded;
+  // Reuse rule, slow branch: the first converged solve after a build sets
+  // the baseline; a later converged solve that needs more than ratio times
+  // as many iterations requests a rebuild before the next solve.  A solve
+  // that did not converge never becomes the baseline: with a fresh
+  // preconditioner it also requests a rebuild (for the next system).
+  if (h->opt.refactor_ratio > 0.0) {
+    if (s == SDSL_OK) {
+      if (h->iters_post_build < 0) h->iters_post_build = h->stats.iters;
+      else if ((double)h->stats.iters > h->opt.refactor_ratio * (double)h->iters_post_build)
+        h->need_rebuild = true;
+    } else if (s == SDSL_ERR_NOT_CONVERGED || s == SDSL_ERR_BREAKDOWN) {
       h->need_rebuild = true;
+    }
   }
   if (st) *st = h->stats;
   return s;

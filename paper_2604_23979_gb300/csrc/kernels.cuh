@@ -163,7 +163,7 @@ struct TriSolve {  // block triangular factors on the layout of P
   const unsigned char* bwd_stream;
   const int64_t* bwd_toff;
   const int64_t* bwd_tile;
-  int tma;              // 1: staged level tiles (cp.async copies into a per-warp shared-memory ring)
+  int staged;           // 1: staged level tiles (cp.async copies into a per-warp shared-memory ring)
   int slot_bytes;       // ring slot size; larger tiles are read from global memory directly
   int kreg;             // entries per lane and gather round of the staged solves (8 or 16)
   int level_wait;       // staged solves: 1 = per-level completion counters, 0 = per-value readiness
@@ -176,6 +176,7 @@ struct TriSolve {  // block triangular factors on the layout of P
   int threads;          // CTA size of the solve kernel
   int sweep_warps;      // warps of the staged solve that take tiles (the rest only stage and reduce)
   int backoff_ns;       // sleep between unsuccessful readiness polls
+  int wait_limit;       // polls after which a staged-sweep wait gives up (sets the timeout flag)
 };
 
 // Packed level-ordered triangle of one direction (dir 0 = strict lower in

@@ -650,7 +650,7 @@ cudaError_t update_any(const TriSolve& M, const double* p, const double* q, doub
                        double* pp, double* part, PcgState* s, int mode, cudaStream_t st) {
   return by_lanes(M.lanes, [&](auto V) -> cudaError_t {
     constexpr int kV = decltype(V)::value;
-    if (M.tma) return update_staged(M, p, q, x, r, z, pp, part, s, mode, st);
+    if (M.staged) return update_staged(M, p, q, x, r, z, pp, part, s, mode, st);
     if (M.sync_free) {
       if (M.prec == 64) return launch_update_sf<double, double, kV>(M, p, q, x, r, z, pp, part, s, mode, st);
       if (M.apply_prec == 64) return launch_update_sf<float, double, kV>(M, p, q, x, r, z, pp, part, s, mode, st);

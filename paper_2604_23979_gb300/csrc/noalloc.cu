@@ -38,14 +38,46 @@ constexpr int kRowsPerCta = 64;
 
 std::mutex g_mu;
 double* g_u_addr[kMaxDevices] = {};
+unsigned long long g_ctx_id[kMaxDevices] = {};
 int g_sms[kMaxDevices] = {};
+
+// Unique id of the calling thread's current CUDA context (0 if the driver
+// cannot tell).  The runtime re-creates a device's primary context after
+// cudaDeviceReset, and the module -- with g_normal_u -- is loaded anew in it,
+// so an address cached for the old context would be stale.  Context ids are
+// never reused within a process.
+unsigned long long current_context_id() {
+  typedef int (*GetCurrent)(void**);
+  typedef int (*GetId)(void*, unsigned long long*);
+  static GetCurrent get_current = nullptr;
+  static GetId get_id = nullptr;
+  static bool looked_up = false;
+  if (!looked_up) {
+    cudaDriverEntryPointQueryResult q1, q2;
+    void* f1 = nullptr;
+    void* f2 = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) == cudaSuccess &&
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) == cudaSuccess &&
+        q1 == cudaDriverEntryPointSuccess && q2 == cudaDriverEntryPointSuccess) {
+      get_current = reinterpret_cast<GetCurrent>(f1);
+      get_id = reinterpret_cast<GetId>(f2);
+    }
+    cudaGetLastError();
+    looked_up = true;
+  }
+  void* ctx = nullptr;
+  unsigned long long id = 0;
+  if (get_current && get_id && get_current(&ctx) == 0 && ctx && get_id(ctx, &id) == 0) return id;
+  return 0;
+}
 
 // Device address of g_normal_u on the current device (in host code the name
 // g_normal_u only stands for the symbol; it is not a device address).  Looked
-// up once per device, with that device current.
+// up once per device and context, with that device current.
 sdsl_status scratch_address(int dev, double** out, int* sms) {
   std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_u_addr[dev]) {
+  const unsigned long long ctx = current_context_id();
+  if (!g_u_addr[dev] || g_ctx_id[dev] != ctx) {
     double* ptr = nullptr;
     cudaError_t e = cudaGetSymbolAddress((void**)&ptr, g_normal_u);
     if (e != cudaSuccess)
@@ -56,6 +88,7 @@ sdsl_status scratch_address(int dev, double** out, int* sms) {
       return report_error(SDSL_ERR_CUDA, std::string("cudaDeviceGetAttribute: ") + cudaGetErrorString(e));
     g_sms[dev] = n_sm > 0 ? n_sm : 1;
     g_u_addr[dev] = ptr;
+    g_ctx_id[dev] = ctx;
   }
   *out = g_u_addr[dev];
   *sms = g_sms[dev];

@@ -15,6 +15,8 @@
 // shared memory, initialised to a signalling-NaN sentinel; a tile waits
 // (warp-uniformly, bounded) until every value it reads is no longer the
 // sentinel, so no barrier separates the levels.
+#include <type_traits>
+
 #include "pcg_common.cuh"
 
 namespace sdsl {
@@ -58,6 +60,57 @@ __device__ __forceinline__ T segmented_sum(T v, int V, int Vmax) {
   return v;
 }
 
+// ---- float-float arithmetic of the FP32-factor apply (apply_prec 48)
+// A value is an unevaluated sum h + l of two floats (|l| <= ulp(h)/2 after
+// renormalisation): about 48 significant bits on the FP32 pipes.  The
+// building blocks are the error-free transformations TwoSum (Knuth) and
+// TwoProd via a fused multiply-add (Dekker 1971), and the compensated dot
+// product Dot2 of Ogita, Rump and Oishi (2005): every product's and every
+// addition's rounding error is carried in a second accumulator.  The
+// explicit _rn intrinsics keep the compiler from contracting or
+// reassociating them.  With this arithmetic the apply of the FP32-stored
+// factors is one fixed linear operator to ~1e-14 relative, as PCG assumes.
+struct ff_tag {};
+constexpr unsigned long long kFFSentinel = 0x7FA5A5A57FA5A5A5ull;  // hi word: the FP32 sentinel
+
+__device__ __forceinline__ unsigned long long ff_pack(float h, float l) {
+  return ((unsigned long long)__float_as_uint(h) << 32) | (unsigned long long)__float_as_uint(l);
+}
+__device__ __forceinline__ float ff_hi(unsigned long long v) { return __uint_as_float((unsigned)(v >> 32)); }
+__device__ __forceinline__ float ff_lo(unsigned long long v) { return __uint_as_float((unsigned)v); }
+// s + e = a + b exactly, s = fl(a + b)
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+// (h, l) += (bh, bl), renormalised
+__device__ __forceinline__ void ff_add(float& h, float& l, float bh, float bl) {
+  float s, e;
+  two_sum(h, bh, s, e);
+  e = __fadd_rn(e, __fadd_rn(l, bl));
+  h = __fadd_rn(s, e);
+  l = __fsub_rn(e, __fsub_rn(h, s));
+}
+// Dot2 step: (s, c) += v * (xh + xl); s is the running sum, c collects the
+// rounding errors of every product and sum.
+__device__ __forceinline__ void dot2_step(float v, float xh, float xl, float& s, float& c) {
+  const float p = __fmul_rn(v, xh);
+  float pe = __fmaf_rn(v, xh, -p);  // exact: v*xh - p
+  pe = __fmaf_rn(v, xl, pe);
+  float t, e;
+  two_sum(s, p, t, e);
+  s = t;
+  c = __fadd_rn(c, __fadd_rn(e, pe));
+}
+// (h, l) = split of a double into two floats, h + l = d to ~2^-48
+__device__ __forceinline__ unsigned long long ff_from_double(double d) {
+  const float h = __double2float_rn(d);
+  const float l = __double2float_rn(d - (double)h);
+  return ff_pack(h, l);
+}
+__device__ __forceinline__ double ff_to_double(unsigned long long v) { return (double)ff_hi(v) + (double)ff_lo(v); }
+
 // One sweep of a block.  `in` holds the right-hand side, `out` the solution
 // (sentinel until solved).  Only warps w < W take tiles.  Readiness is per
 // value (`done` null: a tile waits until no value it reads is the sentinel)
@@ -68,7 +121,7 @@ template <typename TS, typename TC, int SLOTS, int KREG>
 __device__ __forceinline__ void sweep_staged(const unsigned char* __restrict__ stream, const int64_t* toff_s,
                                              int ntile, unsigned char* ring, int slot_bytes, volatile TC* in,
                                              volatile TC* out, bool unit, int* timeout, int W, unsigned backoff,
-                                             int* done) {
+                                             int* done, int limit) {
   const int lane = lane_id(), w = threadIdx.x >> 5;
   if (w >= W) return;
   const int nk = ntile > w ? (ntile - w + W - 1) / W : 0;  // tiles of this warp
@@ -150,7 +203,7 @@ __device__ __forceinline__ void sweep_staged(const unsigned char* __restrict__ s
           int spins = 0;
           while (ld_acquire_cta(cnt) < need) {
             if (backoff) __nanosleep(backoff);
-            if (++spins > kSpinLimit / 8) { *timeout = 1; break; }
+            if (++spins > limit) { *timeout = 1; break; }
           }
         }
 #pragma unroll
@@ -178,7 +231,7 @@ __device__ __forceinline__ void sweep_staged(const unsigned char* __restrict__ s
           if (jj[k2] >= 0 && is_sentinel(xv[k2])) xv[k2] = (TC)out[jj[k2]];
           if (is_sentinel(xv[k2])) ready = false;
         }
-        if (++spins > kSpinLimit / 8) {
+        if (++spins > limit) {
           *timeout = 1;
           ready = true;
 #pragma unroll
@@ -201,6 +254,151 @@ __device__ __forceinline__ void sweep_staged(const unsigned char* __restrict__ s
   cp_async_wait<0>();
 }
 
+// The same sweep in float-float arithmetic: `in` and `out` hold packed
+// (h, l) pairs (64-bit words, so a value and its readiness are published by
+// one aligned store; the sentinel is a pair whose high word is the FP32
+// sentinel, which no arithmetic result has).  Factor values and inverse
+// diagonals are the stored FP32 numbers, exact in this arithmetic.
+template <int SLOTS, int KREG>
+__device__ __forceinline__ void sweep_staged_ff(const unsigned char* __restrict__ stream, const int64_t* toff_s,
+                                                int ntile, unsigned char* ring, int slot_bytes,
+                                                volatile unsigned long long* in, volatile unsigned long long* out,
+                                                bool unit, int* timeout, int W, unsigned backoff, int* done,
+                                                int limit) {
+  const int lane = lane_id(), w = threadIdx.x >> 5;
+  if (w >= W) return;
+  const int nk = ntile > w ? (ntile - w + W - 1) / W : 0;
+  if (nk == 0) return;
+  auto issue = [&](int k) {
+    if (k < nk) {
+      const int t = w + k * W;
+      const int64_t a = toff_s[t];
+      const int n16 = (int)((toff_s[t + 1] - a) >> 4);
+      if (n16 * 16 <= slot_bytes) {
+        unsigned char* dst = ring + (k % SLOTS) * slot_bytes;
+        const unsigned char* src = stream + a;
+        for (int c = lane; c < n16; c += 32) cp_async16(dst + 16 * c, src + 16 * c);
+      }
+    }
+    cp_async_commit();
+  };
+#pragma unroll
+  for (int d = 0; d < SLOTS - 1; ++d) issue(d);
+  for (int k = 0; k < nk; ++k) {
+    const int t = w + k * W;
+    const int64_t a = toff_s[t];
+    const int bytes = (int)(toff_s[t + 1] - a);
+    cp_async_wait<SLOTS - 2>();
+    __syncwarp();
+    const unsigned char* base = bytes <= slot_bytes ? ring + (k % SLOTS) * slot_bytes : stream + a;
+    const int nr = reinterpret_cast<const int32_t*>(base)[0];
+    const int ne = reinterpret_cast<const int32_t*>(base)[1];
+    const int level = reinterpret_cast<const int32_t*>(base)[2];
+    const int need = reinterpret_cast<const int32_t*>(base)[3];
+    const uint2 rec = reinterpret_cast<const uint2*>(base + 16)[lane];
+    const int row = (int)(rec.x & 0xFFFFu);
+    const int first = (int)(rec.x >> 16);
+    const int cnt = (int)(rec.y & 0xFFu);
+    const int V = 1 << ((rec.y >> 8) & 0xFFu);
+    const int r = (int)((rec.y >> 16) & 0xFFu);
+    const bool leader = ((rec.y >> 24) & 1u) != 0;
+    const int Vmax = (int)__reduce_max_sync(0xffffffffu, (unsigned)V);
+    const float* dv = reinterpret_cast<const float*>(base + 16 + 256);
+    const uint16_t* cols = reinterpret_cast<const uint16_t*>(base + 16 + 256 + ((nr * 4 + 15) & ~15));
+    const float* vals = reinterpret_cast<const float*>(reinterpret_cast<const unsigned char*>(cols) + ((2 * ne + 15) & ~15));
+    const unsigned long long inr = leader ? in[row] : 0ull;
+    const float dvr = leader && !unit ? dv[r] : 1.0f;
+    float s0 = 0.f, c0 = 0.f, s1 = 0.f, c1 = 0.f;  // two Dot2 accumulators
+    const int rounds = __reduce_max_sync(0xffffffffu, (unsigned)((cnt + KREG - 1) / KREG));
+    for (int c = 0; c < rounds; ++c) {
+      int jj[KREG];
+      float vv[KREG];
+      unsigned long long xv[KREG];
+#pragma unroll
+      for (int k2 = 0; k2 < KREG; ++k2) {
+        const int idx = c * KREG + k2;
+        const bool ok = idx < cnt;
+        const int e = first + idx * V;
+        jj[k2] = ok ? (int)cols[e] : -1;
+        vv[k2] = ok ? vals[e] : 0.f;
+      }
+      if (done) {
+#pragma unroll
+        for (int k2 = 0; k2 < KREG; ++k2) xv[k2] = jj[k2] >= 0 ? out[jj[k2]] : 0ull;
+        if (c == 0 && level > 0) {
+          const unsigned cnt_addr = smem_u32(done + level - 1);
+          int spins = 0;
+          while (ld_acquire_cta(cnt_addr) < need) {
+            if (backoff) __nanosleep(backoff);
+            if (++spins > limit) { *timeout = 1; break; }
+          }
+        }
+#pragma unroll
+        for (int k2 = 0; k2 < KREG; ++k2)
+          if (jj[k2] >= 0 && xv[k2] == kFFSentinel) xv[k2] = out[jj[k2]];
+      } else {
+        bool ready = true;
+#pragma unroll
+        for (int k2 = 0; k2 < KREG; ++k2) {
+          xv[k2] = jj[k2] >= 0 ? out[jj[k2]] : 0ull;
+          if (xv[k2] == kFFSentinel) ready = false;
+        }
+        int spins = 0;
+        while (!__all_sync(0xffffffffu, ready)) {
+          if (backoff) __nanosleep(backoff);
+          ready = true;
+#pragma unroll
+          for (int k2 = 0; k2 < KREG; ++k2) {
+            if (jj[k2] >= 0 && xv[k2] == kFFSentinel) xv[k2] = out[jj[k2]];
+            if (xv[k2] == kFFSentinel) ready = false;
+          }
+          if (++spins > limit) {
+            *timeout = 1;
+            ready = true;
+#pragma unroll
+            for (int k2 = 0; k2 < KREG; ++k2)
+              if (xv[k2] == kFFSentinel) xv[k2] = 0ull;
+          }
+        }
+      }
+#pragma unroll
+      for (int k2 = 0; k2 < KREG; k2 += 2) {
+        dot2_step(vv[k2], ff_hi(xv[k2]), ff_lo(xv[k2]), s0, c0);
+        dot2_step(vv[k2 + 1], ff_hi(xv[k2 + 1]), ff_lo(xv[k2 + 1]), s1, c1);
+      }
+    }
+    // this lane's sum as a renormalised pair, then the row's lane group
+    float ah, al;
+    two_sum(s0, s1, ah, al);
+    al = __fadd_rn(al, __fadd_rn(c0, c1));
+    {
+      const float hh = __fadd_rn(ah, al);
+      al = __fsub_rn(al, __fsub_rn(hh, ah));
+      ah = hh;
+    }
+    for (int o = Vmax >> 1; o > 0; o >>= 1) {
+      const float bh = __shfl_xor_sync(0xffffffffu, ah, o);
+      const float bl = __shfl_xor_sync(0xffffffffu, al, o);
+      if (o < V) ff_add(ah, al, bh, bl);
+    }
+    if (leader) {
+      // y = (in - acc) * dinv in float-float
+      float dh = ff_hi(inr), dl = ff_lo(inr);
+      ff_add(dh, dl, -ah, -al);
+      const float p = __fmul_rn(dh, dvr);
+      float pe = __fmaf_rn(dh, dvr, -p);
+      pe = __fmaf_rn(dl, dvr, pe);
+      const float yh = __fadd_rn(p, pe);
+      const float yl = __fsub_rn(pe, __fsub_rn(yh, p));
+      out[row] = ff_pack(yh, yl);
+    }
+    __syncwarp();
+    if (done && lane == 0) red_release_cta(smem_u32(done + level));
+    issue(k + SLOTS - 1);
+  }
+  cp_async_wait<0>();
+}
+
 // mode 0: x += alpha p, r -= alpha q, ||r||^2, z = M^{-1} r, r^T z, z^T q;
 // mode 1: z = M^{-1} r only, then rho = r^T z and p = z (start or restart);
 // mode 2: z = M^{-1} r only.
@@ -217,10 +415,14 @@ __global__ void __launch_bounds__(kSweepWarps * 32) k_pcg_update_staged(TriSolve
   __shared__ int timeout;
   const int b = blockIdx.x;
   const int64_t s0 = M.bp[b], e0 = M.bp[b + 1];
-  const size_t ybytes = align128((size_t)M.max_block * sizeof(TC));
-  volatile TC* yb = reinterpret_cast<volatile TC*>(smem_raw);
-  volatile TC* yf = reinterpret_cast<volatile TC*>(smem_raw + ybytes);
-  const TC S = sentinel(TC(0));
+  constexpr bool FF = std::is_same<TC, ff_tag>::value;
+  using TY = typename std::conditional<FF, unsigned long long, TC>::type;  // y storage in shared memory
+  const size_t ybytes = align128((size_t)M.max_block * sizeof(TY));
+  volatile TY* yb = reinterpret_cast<volatile TY*>(smem_raw);
+  volatile TY* yf = reinterpret_cast<volatile TY*>(smem_raw + ybytes);
+  TY S;
+  if constexpr (FF) S = kFFSentinel;
+  else S = sentinel(TC(0));
   const int w = threadIdx.x >> 5;
   const int W = blockDim.x >> 5;
   unsigned char* rings = smem_raw + 2 * ybytes;
@@ -246,32 +448,44 @@ __global__ void __launch_bounds__(kSweepWarps * 32) k_pcg_update_staged(TriSolve
       x[i] = __fma_rn(a, p[i], x[i]);
       r[i] = ri;
       rr = __fma_rn(ri, ri, rr);
-      yb[i - s0] = (TC)ri;
+      if constexpr (FF) yb[i - s0] = ff_from_double(ri);
+      else yb[i - s0] = (TC)ri;
       yf[i - s0] = S;
     }
   } else {
     for (int64_t i = s0 + threadIdx.x; i < e0; i += blockDim.x) {
       const double ri = r[i];
       rr = __fma_rn(ri, ri, rr);
-      yb[i - s0] = (TC)ri;
+      if constexpr (FF) yb[i - s0] = ff_from_double(ri);
+      else yb[i - s0] = (TC)ri;
       yf[i - s0] = S;
     }
   }
   const double rrb = block_sum(rr, sh);
   __syncthreads();
-  sweep_staged<TS, TC, SLOTS, KREG>(M.fwd_stream, toff_f, ntf, ring, M.slot_bytes, yb, yf, M.unit_lower != 0,
-                                    &timeout, M.sweep_warps, (unsigned)M.backoff_ns, done);
+  if constexpr (FF)
+    sweep_staged_ff<SLOTS, KREG>(M.fwd_stream, toff_f, ntf, ring, M.slot_bytes, yb, yf, M.unit_lower != 0,
+                                 &timeout, M.sweep_warps, (unsigned)M.backoff_ns, done, M.wait_limit);
+  else
+    sweep_staged<TS, TC, SLOTS, KREG>(M.fwd_stream, toff_f, ntf, ring, M.slot_bytes, yb, yf, M.unit_lower != 0,
+                                      &timeout, M.sweep_warps, (unsigned)M.backoff_ns, done, M.wait_limit);
   __syncthreads();
   for (int64_t i = threadIdx.x; i < e0 - s0; i += blockDim.x) yb[i] = S;
   if (done)
     for (int t = threadIdx.x; t < M.max_levels; t += blockDim.x) done[t] = 0;
   __syncthreads();
-  sweep_staged<TS, TC, SLOTS, KREG>(M.bwd_stream, toff_b, ntb, ring, M.slot_bytes, yf, yb, false, &timeout,
-                                    M.sweep_warps, (unsigned)M.backoff_ns, done);
+  if constexpr (FF)
+    sweep_staged_ff<SLOTS, KREG>(M.bwd_stream, toff_b, ntb, ring, M.slot_bytes, yf, yb, false, &timeout,
+                                 M.sweep_warps, (unsigned)M.backoff_ns, done, M.wait_limit);
+  else
+    sweep_staged<TS, TC, SLOTS, KREG>(M.bwd_stream, toff_b, ntb, ring, M.slot_bytes, yf, yb, false, &timeout,
+                                      M.sweep_warps, (unsigned)M.backoff_ns, done, M.wait_limit);
   __syncthreads();
   double rz = 0.0, zq = 0.0;
   for (int64_t i = s0 + threadIdx.x; i < e0; i += blockDim.x) {
-    const double zi = (double)yb[i - s0];
+    double zi;
+    if constexpr (FF) zi = ff_to_double(yb[i - s0]);
+    else zi = (double)yb[i - s0];
     z[i] = zi;
     if (mode == 1) pp[i] = zi;
     rz = __fma_rn(r[i], zi, rz);
@@ -285,7 +499,8 @@ __global__ void __launch_bounds__(kSweepWarps * 32) k_pcg_update_staged(TriSolve
 template <typename TS, typename TC, int SLOTS, int KREG>
 cudaError_t launch_staged(const TriSolve& M, const double* p, const double* q, double* x, double* r, double* z,
                           double* pp, double* part, PcgState* s, int mode, cudaStream_t st) {
-  const size_t need = staged_smem_bytes(M.max_block, sizeof(TC), kSweepWarps, M.slot_bytes, M.slots, M.max_tiles,
+  constexpr size_t kTY = std::is_same<TC, ff_tag>::value ? 8 : sizeof(TC);
+  const size_t need = staged_smem_bytes(M.max_block, kTY, kSweepWarps, M.slot_bytes, M.slots, M.max_tiles,
                                         M.level_wait ? M.max_levels : 0);
   auto kern = k_pcg_update_staged<TS, TC, SLOTS, KREG>;
   SDSL_CUDA_TRY((allow_max_dynamic_smem<k_pcg_update_staged<TS, TC, SLOTS, KREG>>()));
@@ -322,6 +537,7 @@ cudaError_t update_staged(const TriSolve& M, const double* p, const double* q, d
                           double* pp, double* part, PcgState* s, int mode, cudaStream_t st) {
   if (M.prec == 64) return launch_shape<double, double>(M, p, q, x, r, z, pp, part, s, mode, st);
   if (M.apply_prec == 64) return launch_shape<float, double>(M, p, q, x, r, z, pp, part, s, mode, st);
+  if (M.apply_prec == 48) return launch_shape<float, ff_tag>(M, p, q, x, r, z, pp, part, s, mode, st);
   return launch_shape<float, float>(M, p, q, x, r, z, pp, part, s, mode, st);
 }
 

@@ -32,7 +32,7 @@ class sdsl_options(C.Structure):
         ("graph_iters", C.c_int), ("tune", C.c_int), ("profile", C.c_int), ("apply_prec", C.c_int),
         ("flexible", C.c_int), ("solve_kernel", C.c_int), ("spmv_form", C.c_int), ("orthog", C.c_int),
         ("sweep_warps", C.c_int), ("sweep_backoff_ns", C.c_int), ("sweep_lane_entries", C.c_int),
-        ("schur_lu", C.c_int), ("sweep_wait", C.c_int),
+        ("schur_lu", C.c_int), ("sweep_wait", C.c_int), ("wait_limit", C.c_int),
     ]
 
 
@@ -47,7 +47,7 @@ class sdsl_stats(C.Structure):
         ("kernel_ms", C.c_double * 4), ("kernel_launches", C.c_int64 * 4), ("kernel_bytes", C.c_double * 4),
         ("spmv_lanes", C.c_int64), ("solve_lanes", C.c_int64), ("tuned_spmv_lanes", C.c_int64),
         ("product_lanes", C.c_int64 * 2), ("ms_schur", C.c_double), ("ms_dense_lu", C.c_double),
-        ("ms_dense_inverse", C.c_double),
+        ("ms_dense_inverse", C.c_double), ("iters_discarded", C.c_int64),
     ]
 
     def as_dict(self):

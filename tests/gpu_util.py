@@ -47,3 +47,42 @@ def relres(S, x, b):
 def iters_close(gpu, ref):
     """Iteration counts within max(1, 5 %) of the oracle's."""
     return abs(gpu - ref) <= max(1, int(np.ceil(0.05 * ref)))
+
+
+def replay_reuse(prob, thetas, ratio=1.5, maxit=None, keep_x=()):
+    """The preconditioner-reuse rule (Sec. 3.4) replayed on the oracle over a
+    theta sequence: factor at step 0; the first converged solve after a build
+    is the baseline; a converged solve needing more than ratio x the baseline,
+    or a solve that does not converge, requests a rebuild before the next
+    step; a solve that does not converge under a reused preconditioner is
+    rebuilt and repeated at once (from x0 = 0).  Returns one dict per step."""
+    import oracle
+
+    maxit = prob.maxit if maxit is None else maxit
+    out = []
+    state, base, need, since = None, -1, True, 0
+    for k, th in enumerate(thetas):
+        S = oracle.normal_matrix(prob.A, th, prob.rho)
+        rebuilt = 0
+        if need:
+            state = oracle.bj_setup_factor(prob.A, th, prob.rho, prob.block_ptr, prob.tau, prob.delta)
+            base, need, since, rebuilt = -1, False, 0, int(k > 0)
+        r = oracle.pcg_bj(S, state.P, state.F, prob.block_ptr, prob.b, rtol=prob.rtol, maxit=maxit)
+        discarded = 0
+        if r.status != 0 and since > 0:
+            discarded = r.iters
+            state = oracle.bj_setup_factor(prob.A, th, prob.rho, prob.block_ptr, prob.tau, prob.delta)
+            base, since, rebuilt = -1, 0, 1
+            r = oracle.pcg_bj(S, state.P, state.F, prob.block_ptr, prob.b, rtol=prob.rtol, maxit=maxit)
+        since += 1
+        if r.status == 0:
+            if base < 0:
+                base = r.iters
+            elif r.iters > ratio * base:
+                need = True
+        else:
+            need = True
+        out.append(dict(k=k, iters=r.iters, status=r.status, rebuilt=rebuilt, discarded=discarded,
+                        relres=float(np.linalg.norm(prob.b - oracle.spmv(S, r.x)) / np.linalg.norm(prob.b)),
+                        x=r.x if k in keep_x else None))
+    return out

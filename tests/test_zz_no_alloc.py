@@ -1,9 +1,15 @@
-"""The allocation-free normal-equation product against sdsl_spmv, through the
-C ABI.  Collected last on purpose: it must also pass after every other test
-has used the library (and, run alone, in a fresh process)."""
+"""The allocation-free normal-equation product, through the C ABI, against the
+handle API's sdsl_spmv and against the oracle's product with its own S =
+A diag(theta) A^T + rho I.  It exists for callers that cannot allocate
+device memory (a host program whose own pool holds the HBM, or a serving
+loop where an allocation would synchronise the device), so the test also
+checks that calls leave the device's free memory unchanged.  Collected last
+on purpose: it must also pass after every other test has used the library
+(and, run alone, in a fresh process)."""
 import numpy as np
 import pytest
 
+import oracle
 from paper_2604_23979_gb300 import sdsl
 from paper_2604_23979_gb300 import workloads as W
 from tests.gpu_util import rel, setup
@@ -42,6 +48,7 @@ def test_noalloc_matches_spmv_two_calls():
     trp, tci, tv = csr_transpose(A)
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()  # noqa: E731
     d = [dev(a) for a in (A.rowptr, A.col, A.val, trp, tci, tv, prob.theta)]
+    S = oracle.normal_matrix(A, prob.theta, prob.rho)  # the oracle's own S
     h, keep = setup(prob)
     try:
         rng = np.random.default_rng(11)
@@ -61,8 +68,34 @@ def test_noalloc_matches_spmv_two_calls():
                          prob.theta * csr_mv(trp, tci, np.abs(tv), np.abs(xh), n), m) + prob.rho * np.abs(xh)
             assert np.all(np.abs(yh - rh) <= 1e-12 * mag), f"call {call}"
             assert rel(yh, rh) <= 1e-12, f"call {call}"
+            # and the oracle's product with its explicit S
+            oh = oracle.spmv(S, xh)
+            assert np.all(np.abs(yh - oh) <= 1e-12 * mag), f"call {call} vs oracle"
     finally:
         sdsl.sdsl_free(h)
+
+
+def test_noalloc_calls_allocate_nothing():
+    """After a first call (which may load the module and look up the scratch
+    address), further calls leave the device's free memory unchanged."""
+    import torch
+
+    prob = W.config1()
+    A = prob.A
+    m, n, nnz = A.nrows, A.ncols, A.nnz
+    trp, tci, tv = csr_transpose(A)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()  # noqa: E731
+    d = [dev(a) for a in (A.rowptr, A.col, A.val, trp, tci, tv, prob.theta)]
+    x = dev(np.random.default_rng(12).standard_normal(m))
+    y = torch.empty(m, dtype=torch.float64, device="cuda")
+    sdsl.sdsl_normal_spmv_noalloc(m, n, nnz, *d, prob.rho, x, y)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(5):
+        sdsl.sdsl_normal_spmv_noalloc(m, n, nnz, *d, prob.rho, x, y)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0, (free0, free1)
 
 
 def test_noalloc_rejects_oversize():
