@@ -114,8 +114,12 @@ typedef struct {
                                     value it reads is solved), 2 per level (a tile waits until the previous
                                     level of its block is complete, one shared counter per level) */
   int wait_limit;                /* polls after which a wait in those sweeps gives up and the solve returns
-                                    SDSL_ERR_TIMEOUT; 0 = default (2^23 polls, about a second).  Small values
-                                    exist to exercise the timeout path */
+                                    SDSL_ERR_TIMEOUT; 0 = default (2^23 polls, about a second; 1,024 under
+                                    wait_test) */
+  int wait_test;                 /* 1 = exercise the timeout path: every per-level wait of the staged sweeps
+                                    waits for one tile more than its level has, which never arrives, so
+                                    each wait gives up after wait_limit polls (no fault, the context stays
+                                    usable) and the solve returns SDSL_ERR_TIMEOUT.  0 in normal use */
 } sdsl_options;
 
 typedef struct {

@@ -1289,7 +1289,8 @@ sdsl_status factor_impl(sdsl_handle h) {
   M.staged = (bj_method(h) && (h->opt.solve_kernel == 3 || (h->opt.solve_kernel == 0 && fits_staged))) ? 1 : 0;
   M.sweep_warps = h->opt.sweep_warps > 0 ? h->opt.sweep_warps : 16;
   M.backoff_ns = h->opt.sweep_backoff_ns >= 0 ? h->opt.sweep_backoff_ns : 0;
-  M.wait_limit = h->opt.wait_limit > 0 ? h->opt.wait_limit : (1 << 23);
+  M.wait_limit = h->opt.wait_limit > 0 ? h->opt.wait_limit : h->opt.wait_test ? 1024 : (1 << 23);
+  M.wait_pad = h->opt.wait_test ? 1 : 0;
   if (M.staged) {
     bool ok = false;
     TRY(build_vtiles(h, f32, apply, &ok));
@@ -1643,6 +1644,7 @@ sdsl_status sdsl_setup(const sdsl_options* opt, int64_t m, int64_t n, const int6
   if (opt->sweep_wait < 0 || opt->sweep_wait > 2) return fail(SDSL_ERR_ARG, "sweep_wait must be in 0..2");
   if (opt->schur_lu < 0 || opt->schur_lu > 2) return fail(SDSL_ERR_ARG, "schur_lu must be in 0..2");
   if (opt->wait_limit < 0) return fail(SDSL_ERR_ARG, "wait_limit must be >= 0");
+  if (opt->wait_test < 0 || opt->wait_test > 1) return fail(SDSL_ERR_ARG, "wait_test must be 0 or 1");
   if (opt->apply_prec != 0 && opt->apply_prec != 64 && opt->apply_prec != 48 && opt->apply_prec != 32)
     return fail(SDSL_ERR_ARG, "apply_prec must be 0, 32, 48 or 64");
   if (opt->factor_prec == 64 && (opt->apply_prec == 32 || opt->apply_prec == 48))
@@ -1808,6 +1810,7 @@ sdsl_status sdsl_solve(sdsl_handle h, const double* b, double* x, int x0_zero, s
   TRY(sync(h, "solve copy-out"));
   h->stats.rebuilt = rebuilt;
   h->stats.iters_discarded = discarded;
+  h->stats.status = s;  // also for early error returns (e.g. SDSL_ERR_TIMEOUT)
   // Reuse rule, slow branch: the first converged solve after a build sets
   // the baseline; a later converged solve that needs more than ratio times
   // as many iterations requests a rebuild before the next solve.  A solve

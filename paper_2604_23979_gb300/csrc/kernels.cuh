@@ -177,6 +177,7 @@ struct TriSolve {  // block triangular factors on the layout of P
   int sweep_warps;      // warps of the staged solve that take tiles (the rest only stage and reduce)
   int backoff_ns;       // sleep between unsuccessful readiness polls
   int wait_limit;       // polls after which a staged-sweep wait gives up (sets the timeout flag)
+  int wait_pad;         // 1: per-level waits wait for one tile more than exists (timeout-path test)
 };
 
 // Packed level-ordered triangle of one direction (dir 0 = strict lower in

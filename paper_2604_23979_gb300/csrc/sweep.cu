@@ -121,7 +121,7 @@ template <typename TS, typename TC, int SLOTS, int KREG>
 __device__ __forceinline__ void sweep_staged(const unsigned char* __restrict__ stream, const int64_t* toff_s,
                                              int ntile, unsigned char* ring, int slot_bytes, volatile TC* in,
                                              volatile TC* out, bool unit, int* timeout, int W, unsigned backoff,
-                                             int* done, int limit) {
+                                             int* done, int limit, int pad) {
   const int lane = lane_id(), w = threadIdx.x >> 5;
   if (w >= W) return;
   const int nk = ntile > w ? (ntile - w + W - 1) / W : 0;  // tiles of this warp
@@ -201,7 +201,7 @@ __device__ __forceinline__ void sweep_staged(const unsigned char* __restrict__ s
           // every lane polls the same counter (a broadcast acquire load)
           const unsigned cnt = smem_u32(done + level - 1);
           int spins = 0;
-          while (ld_acquire_cta(cnt) < need) {
+          while (ld_acquire_cta(cnt) < need + pad) {
             if (backoff) __nanosleep(backoff);
             if (++spins > limit) { *timeout = 1; break; }
           }
@@ -264,7 +264,7 @@ __device__ __forceinline__ void sweep_staged_ff(const unsigned char* __restrict_
                                                 int ntile, unsigned char* ring, int slot_bytes,
                                                 volatile unsigned long long* in, volatile unsigned long long* out,
                                                 bool unit, int* timeout, int W, unsigned backoff, int* done,
-                                                int limit) {
+                                                int limit, int pad) {
   const int lane = lane_id(), w = threadIdx.x >> 5;
   if (w >= W) return;
   const int nk = ntile > w ? (ntile - w + W - 1) / W : 0;
@@ -328,7 +328,7 @@ __device__ __forceinline__ void sweep_staged_ff(const unsigned char* __restrict_
         if (c == 0 && level > 0) {
           const unsigned cnt_addr = smem_u32(done + level - 1);
           int spins = 0;
-          while (ld_acquire_cta(cnt_addr) < need) {
+          while (ld_acquire_cta(cnt_addr) < need + pad) {
             if (backoff) __nanosleep(backoff);
             if (++spins > limit) { *timeout = 1; break; }
           }
@@ -465,10 +465,10 @@ __global__ void __launch_bounds__(kSweepWarps * 32) k_pcg_update_staged(TriSolve
   __syncthreads();
   if constexpr (FF)
     sweep_staged_ff<SLOTS, KREG>(M.fwd_stream, toff_f, ntf, ring, M.slot_bytes, yb, yf, M.unit_lower != 0,
-                                 &timeout, M.sweep_warps, (unsigned)M.backoff_ns, done, M.wait_limit);
+                                 &timeout, M.sweep_warps, (unsigned)M.backoff_ns, done, M.wait_limit, M.wait_pad);
   else
     sweep_staged<TS, TC, SLOTS, KREG>(M.fwd_stream, toff_f, ntf, ring, M.slot_bytes, yb, yf, M.unit_lower != 0,
-                                      &timeout, M.sweep_warps, (unsigned)M.backoff_ns, done, M.wait_limit);
+                                      &timeout, M.sweep_warps, (unsigned)M.backoff_ns, done, M.wait_limit, M.wait_pad);
   __syncthreads();
   for (int64_t i = threadIdx.x; i < e0 - s0; i += blockDim.x) yb[i] = S;
   if (done)
@@ -476,10 +476,10 @@ __global__ void __launch_bounds__(kSweepWarps * 32) k_pcg_update_staged(TriSolve
   __syncthreads();
   if constexpr (FF)
     sweep_staged_ff<SLOTS, KREG>(M.bwd_stream, toff_b, ntb, ring, M.slot_bytes, yf, yb, false, &timeout,
-                                 M.sweep_warps, (unsigned)M.backoff_ns, done, M.wait_limit);
+                                 M.sweep_warps, (unsigned)M.backoff_ns, done, M.wait_limit, M.wait_pad);
   else
     sweep_staged<TS, TC, SLOTS, KREG>(M.bwd_stream, toff_b, ntb, ring, M.slot_bytes, yf, yb, false, &timeout,
-                                      M.sweep_warps, (unsigned)M.backoff_ns, done, M.wait_limit);
+                                      M.sweep_warps, (unsigned)M.backoff_ns, done, M.wait_limit, M.wait_pad);
   __syncthreads();
   double rz = 0.0, zq = 0.0;
   for (int64_t i = s0 + threadIdx.x; i < e0; i += blockDim.x) {
