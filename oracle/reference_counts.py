@@ -1,10 +1,9 @@
 """Write oracle/reference_counts.json: the oracle's PCG iteration count on the
-full 200k x 500k staircase workload, and its run time.
+full 200k x 500k staircase workload, and its run time, for the record.
 
-The CPU baseline of bench.py times a bounded sample of the oracle (setup,
-factor and a few dozen iterations) and extrapolates to one full solve with
-this count.  The count comes from running the oracle itself (FP64, serial,
-IEEE-deterministic with -ffp-contract=off), never from the CUDA path.
+The count comes from running the oracle itself (FP64, IEEE-deterministic with
+-ffp-contract=off, the same bits with or without threads), never from the
+CUDA path.  The tests and bench.py run their own oracle solves.
 Run:  python -m oracle.reference_counts
 """
 import json

@@ -147,6 +147,7 @@ struct sdsl_handle_s {
   int32_t *lev_off_lo = nullptr, *lev_ptr_lo = nullptr, *lev_rows_lo = nullptr;
   int32_t *lev_off_up = nullptr, *lev_ptr_up = nullptr, *lev_rows_up = nullptr;
   std::vector<int32_t> h_nlev_lo, h_nlev_up;
+  int32_t *row_lev_lo = nullptr, *row_lev_up = nullptr;  // level of every row within its block
   int64_t tot_lo = 0, tot_up = 0;
   // Krylov workspace
   double *b = nullptr, *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *u = nullptr;
@@ -931,7 +932,7 @@ sdsl_status build_vtiles(sdsl_handle h, bool f32, int apply, bool* ok) {
     std::vector<int32_t> trp{0}, rows;
     std::vector<int8_t> logv;
     std::vector<int64_t> toff{0}, tile_ptr;
-    std::vector<int32_t> meta;  // per tile: level within the block, tiles of the previous level
+    std::vector<int32_t> meta;  // per tile: level within the block, tiles of the two levels below
     int64_t max_bytes = 0;
   } plan[2];
   std::vector<int32_t> lptr[2], lrows[2];
@@ -973,7 +974,7 @@ sdsl_status build_vtiles(sdsl_handle h, bool f32, int apply, bool* ok) {
       int64_t L = 0, tiles = 0;
       for (int64_t k = 0; k < nb; ++k) {
         P.tile_ptr[k] = tiles;
-        int32_t prev_tiles = 0;
+        int32_t prev_tiles = 0, prev2_tiles = 0;
         for (int32_t l = 0; l < nl[k]; ++l, ++L) {
           const int64_t level_first = tiles;
           lev.clear();
@@ -994,6 +995,7 @@ sdsl_status build_vtiles(sdsl_handle h, bool f32, int apply, bool* ok) {
             P.max_bytes = std::max(P.max_bytes, bytes);
             P.meta.push_back(l);
             P.meta.push_back(prev_tiles);
+            P.meta.push_back(prev2_tiles);
             ++tiles;
             nr = 0;
             ne = 0;
@@ -1010,6 +1012,7 @@ sdsl_status build_vtiles(sdsl_handle h, bool f32, int apply, bool* ok) {
             ne += len;
           }
           close();
+          prev2_tiles = prev_tiles;
           prev_tiles = (int32_t)(tiles - level_first);
         }
       }
@@ -1072,7 +1075,8 @@ sdsl_status build_vtiles(sdsl_handle h, bool f32, int apply, bool* ok) {
     TRY(to_dev(h, d_tile, P.tile_ptr.data(), nb + 1));
     TRY(to_dev(h, d_meta, P.meta.data(), P.meta.size()));
     TRY_CUDA(vt_fill(dir, ntiles, d_trp, d_rows, d_logv, h->row_block, h->d_bp, h->p_rp, h->p_ci, h->p_diag, h->F,
-                     h->dinv, f32 ? 32 : 64, d_toff, d_meta, stream, h->st));
+                     h->dinv, dir == 0 ? h->row_lev_lo : h->row_lev_up, f32 ? 32 : 64, d_toff, d_meta, stream,
+                     h->st));
     if (dir == 0) { M.fwd_stream = stream; M.fwd_toff = d_toff; M.fwd_tile = d_tile; }
     else { M.bwd_stream = stream; M.bwd_toff = d_toff; M.bwd_tile = d_tile; }
   }
@@ -1110,18 +1114,19 @@ sdsl_status factor_impl(sdsl_handle h) {
   TRY(sync(h, "mirror map"));
   if (bad) return fail(SDSL_ERR_ARG, "the system matrix must have a symmetric sparsity pattern");
   // level sets (lower and upper) of the block triangular solves
-  int32_t *cnt, *lev, *fa, *fb, *nlev_d;
+  int32_t *cnt, *fa, *fb, *nlev_d;
   Arena tmp;
   tmp.st = h->st;
   TRY(tmp.get(&cnt, N));
-  TRY(tmp.get(&lev, N));
+  TRY(h->pc.get(&h->row_lev_lo, N));
+  TRY(h->pc.get(&h->row_lev_up, N));
   TRY(tmp.get(&fa, N));
   TRY(tmp.get(&fb, N));
   TRY(tmp.get(&nlev_d, nb));
-  TRY(build_levels(h, 0, &h->lev_off_lo, &h->lev_ptr_lo, &h->lev_rows_lo, h->h_nlev_lo, &h->tot_lo, cnt, lev, fa, fb,
-                   nlev_d));
-  TRY(build_levels(h, 1, &h->lev_off_up, &h->lev_ptr_up, &h->lev_rows_up, h->h_nlev_up, &h->tot_up, cnt, lev, fa, fb,
-                   nlev_d));
+  TRY(build_levels(h, 0, &h->lev_off_lo, &h->lev_ptr_lo, &h->lev_rows_lo, h->h_nlev_lo, &h->tot_lo, cnt,
+                   h->row_lev_lo, fa, fb, nlev_d));
+  TRY(build_levels(h, 1, &h->lev_off_up, &h->lev_ptr_up, &h->lev_rows_up, h->h_nlev_up, &h->tot_up, cnt,
+                   h->row_lev_up, fa, fb, nlev_d));
   // per-block factorization with the shift-retry rule: a block is factored
   // with diagonal p_ii + alpha p_ii for the first alpha of the ladder whose
   // factor does not break down

@@ -74,10 +74,13 @@ cudaError_t ic0_finish(int64_t n, int64_t nnz, const int64_t* prp, const int64_t
                        double* F, const double* dinv, float* Ff, float* dinvf, cudaStream_t st);
 cudaError_t to_float(int64_t n, const double* a, float* b, cudaStream_t st);
 // Variable-width tiles (see precond.cu): fill the stream from a host-built plan.
+// lev: level of every row within its block for this direction (far entries
+// of a row at level L are those with column level <= L - 2).  tile_meta: 3
+// ints per tile (level, tiles of the level below, tiles two levels below).
 cudaError_t vt_fill(int dir, int64_t ntiles, const int32_t* tile_rows_ptr, const int32_t* plan_rows,
                     const int8_t* plan_logv, const int32_t* row_block, const int64_t* bp, const int64_t* prp,
-                    const int32_t* pci, const int64_t* pdiag, const double* F, const double* dinv, int prec,
-                    const int64_t* toff, const int32_t* tile_meta, unsigned char* stream, cudaStream_t st);
+                    const int32_t* pci, const int64_t* pdiag, const double* F, const double* dinv, const int32_t* lev,
+                    int prec, const int64_t* toff, const int32_t* tile_meta, unsigned char* stream, cudaStream_t st);
 // Dynamic shared memory of the staged solve kernel (sweep.cu): y in both
 // directions, the warps' tile rings, the block's staged tile offsets and
 // its per-level completion counters.

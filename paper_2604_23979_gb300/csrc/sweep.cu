@@ -24,6 +24,7 @@ namespace sdsl {
 namespace {
 
 constexpr int kSweepWarps = 16;
+constexpr int kNear = 4;  // near entries per lane and round of the staged sweeps
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
   return static_cast<unsigned>(__cvta_generic_to_shared(p));
@@ -111,17 +112,153 @@ __device__ __forceinline__ unsigned long long ff_from_double(double d) {
 }
 __device__ __forceinline__ double ff_to_double(unsigned long long v) { return (double)ff_hi(v) + (double)ff_lo(v); }
 
+// Arithmetic of one sweep: the type X of a solved value in shared memory,
+// the type VV of a factor value in registers, and a lane's accumulator (two
+// chains fed alternately by the unrolled slots, for instruction-level
+// parallelism; the slot order is fixed, so results are deterministic).
+template <typename TS, typename TC, bool FF>
+struct SweepArith {  // plain: TC = float or double
+  using X = TC;
+  using VV = TC;
+  struct Acc {
+    TC a0, a1;
+  };
+  static __device__ __forceinline__ X sent() { return sentinel(TC(0)); }
+  static __device__ __forceinline__ bool is_sent(X x) { return is_sentinel(x); }
+  static __device__ __forceinline__ VV val(TS v) { return (TC)v; }
+  static __device__ __forceinline__ void init(Acc& a) { a.a0 = TC(0); a.a1 = TC(0); }
+  static __device__ __forceinline__ void add(Acc& a, int k, VV v, X x) {  // k: unrolled slot
+    if (k & 1) a.a1 = fma(v, x, a.a1);
+    else a.a0 = fma(v, x, a.a0);
+  }
+  // y = (in - (far + near)) * d after the lane-group sum
+  static __device__ __forceinline__ X finish(const Acc& far, const Acc& near, int V, int Vmax, X in, TC d,
+                                             bool leader) {
+    TC acc = (far.a0 + far.a1) + (near.a0 + near.a1);
+    acc = segmented_sum(acc, V, Vmax);
+    return leader ? (in - acc) * d : TC(0);
+  }
+};
+
+template <typename TS, typename TC>
+struct SweepArith<TS, TC, true> {  // float-float (TS = float)
+  using X = unsigned long long;
+  using VV = float;
+  struct Acc {
+    float s0, c0, s1, c1;
+  };
+  static __device__ __forceinline__ X sent() { return kFFSentinel; }
+  static __device__ __forceinline__ bool is_sent(X x) { return x == kFFSentinel; }
+  static __device__ __forceinline__ VV val(float v) { return v; }
+  static __device__ __forceinline__ void init(Acc& a) { a.s0 = a.c0 = a.s1 = a.c1 = 0.f; }
+  static __device__ __forceinline__ void add(Acc& a, int k, VV v, X x) {
+    if (k & 1) dot2_step(v, ff_hi(x), ff_lo(x), a.s1, a.c1);
+    else dot2_step(v, ff_hi(x), ff_lo(x), a.s0, a.c0);
+  }
+  // renormalised pair of an accumulator
+  static __device__ __forceinline__ void pair(const Acc& a, float& h, float& l) {
+    two_sum(a.s0, a.s1, h, l);
+    l = __fadd_rn(l, __fadd_rn(a.c0, a.c1));
+    const float hh = __fadd_rn(h, l);
+    l = __fsub_rn(l, __fsub_rn(hh, h));
+    h = hh;
+  }
+  static __device__ __forceinline__ X finish(const Acc& far, const Acc& near, int V, int Vmax, X in, float d,
+                                             bool leader) {
+    float ah, al, bh, bl;
+    pair(far, ah, al);
+    pair(near, bh, bl);
+    ff_add(ah, al, bh, bl);
+    for (int o = Vmax >> 1; o > 0; o >>= 1) {
+      const float ph = __shfl_xor_sync(0xffffffffu, ah, o);
+      const float pl = __shfl_xor_sync(0xffffffffu, al, o);
+      if (o < V) ff_add(ah, al, ph, pl);
+    }
+    if (!leader) return 0ull;
+    // y = (in - acc) * d in float-float
+    float dh = ff_hi(in), dl = ff_lo(in);
+    ff_add(dh, dl, -ah, -al);
+    const float p = __fmul_rn(dh, d);
+    float pe = __fmaf_rn(dh, d, -p);
+    pe = __fmaf_rn(dl, d, pe);
+    const float yh = __fadd_rn(p, pe);
+    const float yl = __fsub_rn(pe, __fsub_rn(yh, p));
+    return ff_pack(yh, yl);
+  }
+};
+
+// Loads out[jj[k]] for KR slots and, with per-level readiness, waits (once,
+// if `wait`) until done[wl] >= need + pad; values that still held the
+// sentinel when they were loaded are reloaded after the wait.  With per-value
+// readiness (done == nullptr) the warp polls until no loaded value is the
+// sentinel.  Every wait is bounded by `limit` polls (then *timeout = 1).
+template <typename AR, int KR>
+__device__ __forceinline__ void load_ready(const int (&jj)[KR], typename AR::X (&xv)[KR],
+                                           volatile typename AR::X* out, int* done, bool wait, int wl, int need,
+                                           int pad, unsigned backoff, int limit, int* timeout) {
+  using X = typename AR::X;
+  if (done) {
+#pragma unroll
+    for (int k = 0; k < KR; ++k) xv[k] = jj[k] >= 0 ? out[jj[k]] : X(0);
+    if (wait) {
+      const unsigned addr = smem_u32(done + wl);  // every lane polls the same counter
+      int spins = 0;
+      while (ld_acquire_cta(addr) < need + pad) {
+        if (backoff) __nanosleep(backoff);
+        if (++spins > limit) { *timeout = 1; break; }
+      }
+#pragma unroll
+      for (int k = 0; k < KR; ++k)
+        if (jj[k] >= 0 && AR::is_sent(xv[k])) xv[k] = out[jj[k]];
+    }
+    return;
+  }
+  bool ready = true;
+#pragma unroll
+  for (int k = 0; k < KR; ++k) {
+    xv[k] = jj[k] >= 0 ? out[jj[k]] : X(0);
+    if (AR::is_sent(xv[k])) ready = false;
+  }
+  int spins = 0;
+  while (!__all_sync(0xffffffffu, ready)) {
+    if (backoff) __nanosleep(backoff);
+    ready = true;
+#pragma unroll
+    for (int k = 0; k < KR; ++k) {
+      if (jj[k] >= 0 && AR::is_sent(xv[k])) xv[k] = out[jj[k]];
+      if (AR::is_sent(xv[k])) ready = false;
+    }
+    if (++spins > limit) {
+      *timeout = 1;
+      ready = true;
+#pragma unroll
+      for (int k = 0; k < KR; ++k)
+        if (AR::is_sent(xv[k])) xv[k] = X(0);
+    }
+  }
+}
+
 // One sweep of a block.  `in` holds the right-hand side, `out` the solution
-// (sentinel until solved).  Only warps w < W take tiles.  Readiness is per
-// value (`done` null: a tile waits until no value it reads is the sentinel)
-// or per level (a tile waits until every tile of the previous level has
-// counted itself in done[level - 1]; since each of those waited for its own
-// previous level, every lower level is then complete too).
-template <typename TS, typename TC, int SLOTS, int KREG>
+// (sentinel until solved).  Only warps w < W take tiles.  A tile's rows are
+// at one level L; each lane first sums its "far" entries (columns at levels
+// <= L - 2), then its "near" ones (level L - 1).  Readiness is per value
+// (`done` null: a tile waits until no value it reads is the sentinel) or per
+// level: the far part waits until every tile of level L - 2 has counted
+// itself in done[L - 2], the near part until level L - 1 has (since each of
+// those tiles waited for its own level below, every lower level is then
+// complete too).  Far entries make up most of a row and are summed while
+// level L - 1 is still being solved; only the near ones (about one per row)
+// stay on the level-to-level critical path.
+template <typename TS, typename TC, bool FF, int SLOTS, int KREG, int KNEAR>
 __device__ __forceinline__ void sweep_staged(const unsigned char* __restrict__ stream, const int64_t* toff_s,
-                                             int ntile, unsigned char* ring, int slot_bytes, volatile TC* in,
-                                             volatile TC* out, bool unit, int* timeout, int W, unsigned backoff,
-                                             int* done, int limit, int pad) {
+                                             int ntile, unsigned char* ring, int slot_bytes,
+                                             volatile typename SweepArith<TS, TC, FF>::X* in,
+                                             volatile typename SweepArith<TS, TC, FF>::X* out, bool unit,
+                                             int* timeout, int W, unsigned backoff, int* done, int limit, int pad) {
+  using AR = SweepArith<TS, TC, FF>;
+  using X = typename AR::X;
+  using VV = typename AR::VV;
+  using DV = typename std::conditional<FF, float, TC>::type;
   const int lane = lane_id(), w = threadIdx.x >> 5;
   if (w >= W) return;
   const int nk = ntile > w ? (ntile - w + W - 1) / W : 0;  // tiles of this warp
@@ -157,243 +294,75 @@ __device__ __forceinline__ void sweep_staged(const unsigned char* __restrict__ s
     const int nr = reinterpret_cast<const int32_t*>(base)[0];
     const int ne = reinterpret_cast<const int32_t*>(base)[1];
     const int level = reinterpret_cast<const int32_t*>(base)[2];
-    const int need = reinterpret_cast<const int32_t*>(base)[3];
+    const unsigned needs = reinterpret_cast<const uint32_t*>(base)[3];
+    const int need1 = (int)(needs & 0xFFFFu), need2 = (int)(needs >> 16);
     const uint2 rec = reinterpret_cast<const uint2*>(base + 16)[lane];  // this lane's role, one load
     const int row = (int)(rec.x & 0xFFFFu);
     const int first = (int)(rec.x >> 16);
     const int cnt = (int)(rec.y & 0xFFu);
     const int V = 1 << ((rec.y >> 8) & 0xFFu);
-    const int r = (int)((rec.y >> 16) & 0xFFu);
-    const bool leader = ((rec.y >> 24) & 1u) != 0;
+    const int r = (int)((rec.y >> 16) & 0x7Fu);
+    const bool leader = ((rec.y >> 23) & 1u) != 0;
+    const int nfar = (int)(rec.y >> 24);
     const int Vmax = (int)__reduce_max_sync(0xffffffffu, (unsigned)V);
     const TS* dv = reinterpret_cast<const TS*>(base + 16 + 256);
     const uint16_t* cols = reinterpret_cast<const uint16_t*>(base + 16 + 256 + ((nr * (int)sizeof(TS) + 15) & ~15));
     const TS* vals = reinterpret_cast<const TS*>(reinterpret_cast<const unsigned char*>(cols) + ((2 * ne + 15) & ~15));
     // The right-hand side and the inverse diagonal are final before the
     // sweep starts: read them before waiting, off the critical path.
-    const TC inr = leader ? (TC)in[row] : TC(0);
-    const TC dvr = leader && !unit ? (TC)dv[r] : TC(1);
-    // Gather this lane's entries (KREG per round; longer rows take more
-    // warp-uniform rounds), then wait warp-uniformly until every value the
-    // round reads is solved: per-lane spin loops would leave the warp
-    // diverged.  The values read by the poll are the ones used: a value that
-    // is no longer the sentinel is final (written once per sweep).  Two
-    // accumulators halve the dependent FMA chain after the wait.
-    TC acc = TC(0), acc2 = TC(0);
-    const int rounds = __reduce_max_sync(0xffffffffu, (unsigned)((cnt + KREG - 1) / KREG));
-    for (int c = 0; c < rounds; ++c) {
+    const X inr = leader ? in[row] : X(0);
+    const DV dvr = leader && !unit ? (DV)dv[r] : DV(1);
+    typename AR::Acc af, an;
+    AR::init(af);
+    AR::init(an);
+    // far entries [0, nfar) of the lane, KREG per warp-uniform round
+    const int rfar = __reduce_max_sync(0xffffffffu, (unsigned)((nfar + KREG - 1) / KREG));
+    for (int c = 0; c < rfar; ++c) {
       int jj[KREG];
-      TC vv[KREG], xv[KREG];
+      VV vv[KREG];
+      X xv[KREG];
 #pragma unroll
       for (int k2 = 0; k2 < KREG; ++k2) {
         const int idx = c * KREG + k2;
+        const bool ok = idx < nfar;
+        const int e = first + idx * V;
+        jj[k2] = ok ? (int)cols[e] : -1;
+        vv[k2] = ok ? AR::val(vals[e]) : VV(0);
+      }
+      load_ready<AR, KREG>(jj, xv, out, done, c == 0 && level >= 2, level - 2, need2, pad, backoff, limit, timeout);
+#pragma unroll
+      for (int k2 = 0; k2 < KREG; ++k2) AR::add(af, k2, vv[k2], xv[k2]);
+    }
+    // near entries [nfar, cnt), KNEAR per round; the first round waits for
+    // level L - 1 (a tile with no near entry still waits once, so that its
+    // own completion count keeps implying every lower level's)
+    const int rnear = __reduce_max_sync(0xffffffffu, (unsigned)((cnt - nfar + KNEAR - 1) / KNEAR));
+    if (done && level >= 1 && rnear == 0) {
+      int jj[1] = {-1};
+      X xv[1];
+      load_ready<AR, 1>(jj, xv, out, done, true, level - 1, need1, pad, backoff, limit, timeout);
+    }
+    for (int c = 0; c < rnear; ++c) {
+      int jj[KNEAR];
+      VV vv[KNEAR];
+      X xv[KNEAR];
+#pragma unroll
+      for (int k2 = 0; k2 < KNEAR; ++k2) {
+        const int idx = nfar + c * KNEAR + k2;
         const bool ok = idx < cnt;
         const int e = first + idx * V;
         jj[k2] = ok ? (int)cols[e] : -1;
-        vv[k2] = ok ? (TC)vals[e] : TC(0);
+        vv[k2] = ok ? AR::val(vals[e]) : VV(0);
       }
-      if (done) {
-        // Speculative loads before the wait: a value still holding the
-        // sentinel is reloaded after it (only those from the last levels).
+      load_ready<AR, KNEAR>(jj, xv, out, done, c == 0 && level >= 1, level - 1, need1, pad, backoff, limit,
+                            timeout);
 #pragma unroll
-        for (int k2 = 0; k2 < KREG; ++k2) xv[k2] = jj[k2] >= 0 ? (TC)out[jj[k2]] : TC(0);
-        if (c == 0 && level > 0) {
-          // every lane polls the same counter (a broadcast acquire load)
-          const unsigned cnt = smem_u32(done + level - 1);
-          int spins = 0;
-          while (ld_acquire_cta(cnt) < need + pad) {
-            if (backoff) __nanosleep(backoff);
-            if (++spins > limit) { *timeout = 1; break; }
-          }
-        }
-#pragma unroll
-        for (int k2 = 0; k2 < KREG; ++k2)
-          if (jj[k2] >= 0 && is_sentinel(xv[k2])) xv[k2] = (TC)out[jj[k2]];
-#pragma unroll
-        for (int k2 = 0; k2 < KREG; k2 += 2) {
-          acc = fma(vv[k2], xv[k2], acc);
-          acc2 = fma(vv[k2 + 1], xv[k2 + 1], acc2);
-        }
-        continue;
-      }
-      bool ready = true;
-#pragma unroll
-      for (int k2 = 0; k2 < KREG; ++k2) {
-        xv[k2] = jj[k2] >= 0 ? (TC)out[jj[k2]] : TC(0);
-        if (is_sentinel(xv[k2])) ready = false;
-      }
-      int spins = 0;
-      while (!__all_sync(0xffffffffu, ready)) {
-        if (backoff) __nanosleep(backoff);
-        ready = true;
-#pragma unroll
-        for (int k2 = 0; k2 < KREG; ++k2) {
-          if (jj[k2] >= 0 && is_sentinel(xv[k2])) xv[k2] = (TC)out[jj[k2]];
-          if (is_sentinel(xv[k2])) ready = false;
-        }
-        if (++spins > limit) {
-          *timeout = 1;
-          ready = true;
-#pragma unroll
-          for (int k2 = 0; k2 < KREG; ++k2)
-            if (is_sentinel(xv[k2])) xv[k2] = TC(0);
-        }
-      }
-#pragma unroll
-      for (int k2 = 0; k2 < KREG; k2 += 2) {
-        acc = fma(vv[k2], xv[k2], acc);
-        acc2 = fma(vv[k2 + 1], xv[k2 + 1], acc2);
-      }
+      for (int k2 = 0; k2 < KNEAR; ++k2) AR::add(an, k2, vv[k2], xv[k2]);
     }
-    acc = segmented_sum(acc + acc2, V, Vmax);
-    if (leader) out[row] = (inr - acc) * dvr;
+    const X y = AR::finish(af, an, V, Vmax, inr, dvr, leader);
+    if (leader) out[row] = y;
     __syncwarp();  // the slot of tile k-1 is free: refill it with tile k+SLOTS-1
     if (done && lane == 0) red_release_cta(smem_u32(done + level));  // the tile's values before its count
-    issue(k + SLOTS - 1);
-  }
-  cp_async_wait<0>();
-}
-
-// The same sweep in float-float arithmetic: `in` and `out` hold packed
-// (h, l) pairs (64-bit words, so a value and its readiness are published by
-// one aligned store; the sentinel is a pair whose high word is the FP32
-// sentinel, which no arithmetic result has).  Factor values and inverse
-// diagonals are the stored FP32 numbers, exact in this arithmetic.
-template <int SLOTS, int KREG>
-__device__ __forceinline__ void sweep_staged_ff(const unsigned char* __restrict__ stream, const int64_t* toff_s,
-                                                int ntile, unsigned char* ring, int slot_bytes,
-                                                volatile unsigned long long* in, volatile unsigned long long* out,
-                                                bool unit, int* timeout, int W, unsigned backoff, int* done,
-                                                int limit, int pad) {
-  const int lane = lane_id(), w = threadIdx.x >> 5;
-  if (w >= W) return;
-  const int nk = ntile > w ? (ntile - w + W - 1) / W : 0;
-  if (nk == 0) return;
-  auto issue = [&](int k) {
-    if (k < nk) {
-      const int t = w + k * W;
-      const int64_t a = toff_s[t];
-      const int n16 = (int)((toff_s[t + 1] - a) >> 4);
-      if (n16 * 16 <= slot_bytes) {
-        unsigned char* dst = ring + (k % SLOTS) * slot_bytes;
-        const unsigned char* src = stream + a;
-        for (int c = lane; c < n16; c += 32) cp_async16(dst + 16 * c, src + 16 * c);
-      }
-    }
-    cp_async_commit();
-  };
-#pragma unroll
-  for (int d = 0; d < SLOTS - 1; ++d) issue(d);
-  for (int k = 0; k < nk; ++k) {
-    const int t = w + k * W;
-    const int64_t a = toff_s[t];
-    const int bytes = (int)(toff_s[t + 1] - a);
-    cp_async_wait<SLOTS - 2>();
-    __syncwarp();
-    const unsigned char* base = bytes <= slot_bytes ? ring + (k % SLOTS) * slot_bytes : stream + a;
-    const int nr = reinterpret_cast<const int32_t*>(base)[0];
-    const int ne = reinterpret_cast<const int32_t*>(base)[1];
-    const int level = reinterpret_cast<const int32_t*>(base)[2];
-    const int need = reinterpret_cast<const int32_t*>(base)[3];
-    const uint2 rec = reinterpret_cast<const uint2*>(base + 16)[lane];
-    const int row = (int)(rec.x & 0xFFFFu);
-    const int first = (int)(rec.x >> 16);
-    const int cnt = (int)(rec.y & 0xFFu);
-    const int V = 1 << ((rec.y >> 8) & 0xFFu);
-    const int r = (int)((rec.y >> 16) & 0xFFu);
-    const bool leader = ((rec.y >> 24) & 1u) != 0;
-    const int Vmax = (int)__reduce_max_sync(0xffffffffu, (unsigned)V);
-    const float* dv = reinterpret_cast<const float*>(base + 16 + 256);
-    const uint16_t* cols = reinterpret_cast<const uint16_t*>(base + 16 + 256 + ((nr * 4 + 15) & ~15));
-    const float* vals = reinterpret_cast<const float*>(reinterpret_cast<const unsigned char*>(cols) + ((2 * ne + 15) & ~15));
-    const unsigned long long inr = leader ? in[row] : 0ull;
-    const float dvr = leader && !unit ? dv[r] : 1.0f;
-    float s0 = 0.f, c0 = 0.f, s1 = 0.f, c1 = 0.f;  // two Dot2 accumulators
-    const int rounds = __reduce_max_sync(0xffffffffu, (unsigned)((cnt + KREG - 1) / KREG));
-    for (int c = 0; c < rounds; ++c) {
-      int jj[KREG];
-      float vv[KREG];
-      unsigned long long xv[KREG];
-#pragma unroll
-      for (int k2 = 0; k2 < KREG; ++k2) {
-        const int idx = c * KREG + k2;
-        const bool ok = idx < cnt;
-        const int e = first + idx * V;
-        jj[k2] = ok ? (int)cols[e] : -1;
-        vv[k2] = ok ? vals[e] : 0.f;
-      }
-      if (done) {
-#pragma unroll
-        for (int k2 = 0; k2 < KREG; ++k2) xv[k2] = jj[k2] >= 0 ? out[jj[k2]] : 0ull;
-        if (c == 0 && level > 0) {
-          const unsigned cnt_addr = smem_u32(done + level - 1);
-          int spins = 0;
-          while (ld_acquire_cta(cnt_addr) < need + pad) {
-            if (backoff) __nanosleep(backoff);
-            if (++spins > limit) { *timeout = 1; break; }
-          }
-        }
-#pragma unroll
-        for (int k2 = 0; k2 < KREG; ++k2)
-          if (jj[k2] >= 0 && xv[k2] == kFFSentinel) xv[k2] = out[jj[k2]];
-      } else {
-        bool ready = true;
-#pragma unroll
-        for (int k2 = 0; k2 < KREG; ++k2) {
-          xv[k2] = jj[k2] >= 0 ? out[jj[k2]] : 0ull;
-          if (xv[k2] == kFFSentinel) ready = false;
-        }
-        int spins = 0;
-        while (!__all_sync(0xffffffffu, ready)) {
-          if (backoff) __nanosleep(backoff);
-          ready = true;
-#pragma unroll
-          for (int k2 = 0; k2 < KREG; ++k2) {
-            if (jj[k2] >= 0 && xv[k2] == kFFSentinel) xv[k2] = out[jj[k2]];
-            if (xv[k2] == kFFSentinel) ready = false;
-          }
-          if (++spins > limit) {
-            *timeout = 1;
-            ready = true;
-#pragma unroll
-            for (int k2 = 0; k2 < KREG; ++k2)
-              if (xv[k2] == kFFSentinel) xv[k2] = 0ull;
-          }
-        }
-      }
-#pragma unroll
-      for (int k2 = 0; k2 < KREG; k2 += 2) {
-        dot2_step(vv[k2], ff_hi(xv[k2]), ff_lo(xv[k2]), s0, c0);
-        dot2_step(vv[k2 + 1], ff_hi(xv[k2 + 1]), ff_lo(xv[k2 + 1]), s1, c1);
-      }
-    }
-    // this lane's sum as a renormalised pair, then the row's lane group
-    float ah, al;
-    two_sum(s0, s1, ah, al);
-    al = __fadd_rn(al, __fadd_rn(c0, c1));
-    {
-      const float hh = __fadd_rn(ah, al);
-      al = __fsub_rn(al, __fsub_rn(hh, ah));
-      ah = hh;
-    }
-    for (int o = Vmax >> 1; o > 0; o >>= 1) {
-      const float bh = __shfl_xor_sync(0xffffffffu, ah, o);
-      const float bl = __shfl_xor_sync(0xffffffffu, al, o);
-      if (o < V) ff_add(ah, al, bh, bl);
-    }
-    if (leader) {
-      // y = (in - acc) * dinv in float-float
-      float dh = ff_hi(inr), dl = ff_lo(inr);
-      ff_add(dh, dl, -ah, -al);
-      const float p = __fmul_rn(dh, dvr);
-      float pe = __fmaf_rn(dh, dvr, -p);
-      pe = __fmaf_rn(dl, dvr, pe);
-      const float yh = __fadd_rn(p, pe);
-      const float yl = __fsub_rn(pe, __fsub_rn(yh, p));
-      out[row] = ff_pack(yh, yl);
-    }
-    __syncwarp();
-    if (done && lane == 0) red_release_cta(smem_u32(done + level));
     issue(k + SLOTS - 1);
   }
   cp_async_wait<0>();
@@ -463,23 +432,17 @@ __global__ void __launch_bounds__(kSweepWarps * 32) k_pcg_update_staged(TriSolve
   }
   const double rrb = block_sum(rr, sh);
   __syncthreads();
-  if constexpr (FF)
-    sweep_staged_ff<SLOTS, KREG>(M.fwd_stream, toff_f, ntf, ring, M.slot_bytes, yb, yf, M.unit_lower != 0,
-                                 &timeout, M.sweep_warps, (unsigned)M.backoff_ns, done, M.wait_limit, M.wait_pad);
-  else
-    sweep_staged<TS, TC, SLOTS, KREG>(M.fwd_stream, toff_f, ntf, ring, M.slot_bytes, yb, yf, M.unit_lower != 0,
-                                      &timeout, M.sweep_warps, (unsigned)M.backoff_ns, done, M.wait_limit, M.wait_pad);
+  sweep_staged<TS, TC, FF, SLOTS, KREG, kNear>(M.fwd_stream, toff_f, ntf, ring, M.slot_bytes, yb, yf,
+                                               M.unit_lower != 0, &timeout, M.sweep_warps, (unsigned)M.backoff_ns,
+                                               done, M.wait_limit, M.wait_pad);
   __syncthreads();
   for (int64_t i = threadIdx.x; i < e0 - s0; i += blockDim.x) yb[i] = S;
   if (done)
     for (int t = threadIdx.x; t < M.max_levels; t += blockDim.x) done[t] = 0;
   __syncthreads();
-  if constexpr (FF)
-    sweep_staged_ff<SLOTS, KREG>(M.bwd_stream, toff_b, ntb, ring, M.slot_bytes, yf, yb, false, &timeout,
-                                 M.sweep_warps, (unsigned)M.backoff_ns, done, M.wait_limit, M.wait_pad);
-  else
-    sweep_staged<TS, TC, SLOTS, KREG>(M.bwd_stream, toff_b, ntb, ring, M.slot_bytes, yf, yb, false, &timeout,
-                                      M.sweep_warps, (unsigned)M.backoff_ns, done, M.wait_limit, M.wait_pad);
+  sweep_staged<TS, TC, FF, SLOTS, KREG, kNear>(M.bwd_stream, toff_b, ntb, ring, M.slot_bytes, yf, yb, false,
+                                               &timeout, M.sweep_warps, (unsigned)M.backoff_ns, done, M.wait_limit,
+                                               M.wait_pad);
   __syncthreads();
   double rz = 0.0, zq = 0.0;
   for (int64_t i = s0 + threadIdx.x; i < e0; i += blockDim.x) {
