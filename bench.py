@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--spmv-form", type=int, default=0, help="PCG product: 0 auto, 1 explicit S, 2 factored CSR, "
                                                               "3 factored sliced ELL")
     ap.add_argument("--sweep-wait", type=int, default=0, help="staged sweeps: 0 auto, 1 per value, 2 per level")
+    ap.add_argument("--far-gap", type=int, default=0, help="staged sweeps: levels below a row from which its entries "
+                                                            "are summed before its last wait (0 auto)")
     ap.add_argument("--tune", type=int, default=0, help="1: autotune the product kernels' lane widths at factor time")
     ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5"],
                     help="c2: the headline Block-Jacobi solve (default); c3: BBD GMRES(30) on the block-angular "
@@ -243,6 +245,7 @@ def run_ours(args, ws, rank, local):
         o.sweep_lane_entries = args.lane_entries
         o.tune = args.tune
         o.sweep_wait = args.sweep_wait
+        o.sweep_far_gap = args.far_gap
         o.spmv_form = args.spmv_form
         arrs = arrays if arrays is not None else (d_rp, d_ci, d_v, d_th)
         h = sdsl.sdsl_setup(o, A.nrows, A.ncols, *arrs)

@@ -116,6 +116,10 @@ typedef struct {
   int wait_limit;                /* polls after which a wait in those sweeps gives up and the solve returns
                                     SDSL_ERR_TIMEOUT; 0 = default (2^23 polls, about a second; 1,024 under
                                     wait_test) */
+  int sweep_far_gap;             /* tile shape of the staged sweeps: entries whose column lies at least this
+                                    many levels below the row are summed first, behind one wait on a level
+                                    count; the nearer ones are read by the row's first lane last, polling
+                                    the values; 0 = auto (3), else 2..16 */
   int wait_test;                 /* 1 = exercise the timeout path: every per-level wait of the staged sweeps
                                     waits for one tile more than its level has, which never arrives, so
                                     each wait gives up after wait_limit polls (no fault, the context stays

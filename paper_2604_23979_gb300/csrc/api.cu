@@ -923,6 +923,8 @@ sdsl_status build_vtiles(sdsl_handle h, bool f32, int apply, bool* ok) {
   const int tsz = f32 ? 4 : 8;
   const int tc = apply == 32 ? 4 : 8;
   const int E = h->opt.sweep_lane_entries > 0 ? h->opt.sweep_lane_entries : 16;
+  const int gap = h->opt.sweep_far_gap > 0 ? h->opt.sweep_far_gap : 3;
+  M.far_gap = gap;
   const int kWarps = 16;
   *ok = false;
   int64_t maxb = 0;
@@ -945,6 +947,9 @@ sdsl_status build_vtiles(sdsl_handle h, bool f32, int apply, bool* ok) {
     ~Release() { a.release(); }
   } release_tmp{tmp};
   TRY(tmp.get(&d_len, nrows + 1));
+  int* d_bad;
+  TRY(tmp.get(&d_bad, 1));
+  TRY_CUDA(cudaMemsetAsync(d_bad, 0, sizeof(int), h->st));
   for (int dir = 0; dir < 2; ++dir) {
     const int64_t tot = dir == 0 ? h->tot_lo : h->tot_up;
     const int32_t* d_rows = dir == 0 ? h->lev_rows_lo : h->lev_rows_up;
@@ -974,7 +979,7 @@ sdsl_status build_vtiles(sdsl_handle h, bool f32, int apply, bool* ok) {
       int64_t L = 0, tiles = 0;
       for (int64_t k = 0; k < nb; ++k) {
         P.tile_ptr[k] = tiles;
-        int32_t prev_tiles = 0, prev2_tiles = 0;
+        std::vector<int32_t> lt;  // tiles of each level of this block so far
         for (int32_t l = 0; l < nl[k]; ++l, ++L) {
           const int64_t level_first = tiles;
           lev.clear();
@@ -994,8 +999,8 @@ sdsl_status build_vtiles(sdsl_handle h, bool f32, int apply, bool* ok) {
             P.trp.push_back((int32_t)P.rows.size());
             P.max_bytes = std::max(P.max_bytes, bytes);
             P.meta.push_back(l);
-            P.meta.push_back(prev_tiles);
-            P.meta.push_back(prev2_tiles);
+            P.meta.push_back(l >= 1 ? lt[l - 1] : 0);
+            P.meta.push_back(l >= gap ? lt[l - gap] : 0);
             ++tiles;
             nr = 0;
             ne = 0;
@@ -1012,8 +1017,7 @@ sdsl_status build_vtiles(sdsl_handle h, bool f32, int apply, bool* ok) {
             ne += len;
           }
           close();
-          prev2_tiles = prev_tiles;
-          prev_tiles = (int32_t)(tiles - level_first);
+          lt.push_back((int32_t)(tiles - level_first));
         }
       }
       P.tile_ptr[nb] = tiles;
@@ -1076,11 +1080,14 @@ sdsl_status build_vtiles(sdsl_handle h, bool f32, int apply, bool* ok) {
     TRY(to_dev(h, d_meta, P.meta.data(), P.meta.size()));
     TRY_CUDA(vt_fill(dir, ntiles, d_trp, d_rows, d_logv, h->row_block, h->d_bp, h->p_rp, h->p_ci, h->p_diag, h->F,
                      h->dinv, dir == 0 ? h->row_lev_lo : h->row_lev_up, f32 ? 32 : 64, d_toff, d_meta, stream,
-                     h->st));
+                     d_bad, gap, h->st));
     if (dir == 0) { M.fwd_stream = stream; M.fwd_toff = d_toff; M.fwd_tile = d_tile; }
     else { M.bwd_stream = stream; M.bwd_toff = d_toff; M.bwd_tile = d_tile; }
   }
+  int bad = 0;
+  TRY(to_host(h, &bad, d_bad, 1));
   TRY(sync(h, "tile streams"));
+  if (bad) return SDSL_OK;  // a row with more near entries than a lane record holds: another solve kernel
   *ok = true;
   return SDSL_OK;
 }
@@ -1650,6 +1657,8 @@ sdsl_status sdsl_setup(const sdsl_options* opt, int64_t m, int64_t n, const int6
   if (opt->schur_lu < 0 || opt->schur_lu > 2) return fail(SDSL_ERR_ARG, "schur_lu must be in 0..2");
   if (opt->wait_limit < 0) return fail(SDSL_ERR_ARG, "wait_limit must be >= 0");
   if (opt->wait_test < 0 || opt->wait_test > 1) return fail(SDSL_ERR_ARG, "wait_test must be 0 or 1");
+  if (opt->sweep_far_gap < 0 || opt->sweep_far_gap == 1 || opt->sweep_far_gap > 16)
+    return fail(SDSL_ERR_ARG, "sweep_far_gap must be 0 (auto) or in 2..16");
   if (opt->apply_prec != 0 && opt->apply_prec != 64 && opt->apply_prec != 48 && opt->apply_prec != 32)
     return fail(SDSL_ERR_ARG, "apply_prec must be 0, 32, 48 or 64");
   if (opt->factor_prec == 64 && (opt->apply_prec == 32 || opt->apply_prec == 48))

@@ -75,12 +75,14 @@ cudaError_t ic0_finish(int64_t n, int64_t nnz, const int64_t* prp, const int64_t
 cudaError_t to_float(int64_t n, const double* a, float* b, cudaStream_t st);
 // Variable-width tiles (see precond.cu): fill the stream from a host-built plan.
 // lev: level of every row within its block for this direction (far entries
-// of a row at level L are those with column level <= L - 2).  tile_meta: 3
-// ints per tile (level, tiles of the level below, tiles two levels below).
+// of a row at level L have column level <= L - gap, near ones above that).
+// tile_meta: 3 ints per tile (level, tiles of level L - 1, tiles of level
+// L - gap).  *bad = 1 if a row has more than 255 near entries.
 cudaError_t vt_fill(int dir, int64_t ntiles, const int32_t* tile_rows_ptr, const int32_t* plan_rows,
                     const int8_t* plan_logv, const int32_t* row_block, const int64_t* bp, const int64_t* prp,
                     const int32_t* pci, const int64_t* pdiag, const double* F, const double* dinv, const int32_t* lev,
-                    int prec, const int64_t* toff, const int32_t* tile_meta, unsigned char* stream, cudaStream_t st);
+                    int prec, const int64_t* toff, const int32_t* tile_meta, unsigned char* stream, int* bad,
+                    int gap, cudaStream_t st);
 // Dynamic shared memory of the staged solve kernel (sweep.cu): y in both
 // directions, the warps' tile rings, the block's staged tile offsets and
 // its per-level completion counters.
@@ -181,6 +183,7 @@ struct TriSolve {  // block triangular factors on the layout of P
   int backoff_ns;       // sleep between unsuccessful readiness polls
   int wait_limit;       // polls after which a staged-sweep wait gives up (sets the timeout flag)
   int wait_pad;         // 1: per-level waits wait for one tile more than exists (timeout-path test)
+  int far_gap;          // staged tiles: entries at least this many levels below the row are "far"
 };
 
 // Packed level-ordered triangle of one direction (dir 0 = strict lower in

@@ -498,20 +498,22 @@ __device__ __forceinline__ int strict_count(int dir, int64_t i, int64_t s, int64
 // Variable-width tiles.  A tile holds rows of one level L (within its
 // block); row r of the tile gets V_r lanes (a power of two, a planned number
 // of entries per lane), groups packed at V-aligned lane offsets.  A row's
-// strict entries are listed "far" first -- columns whose level is at most
-// L - 2, final once level L - 2 is complete -- then "near" (level L - 1),
-// each group in ascending column order; the row's list is dealt to its V
-// lanes round-robin (lane k gets entries k, k + V, ...).  Layout (16-byte
-// aligned parts):
-//   int32 nr, ne, L, (tiles of level L-1) | (tiles of level L-2) << 16
+// strict in-block entries are split by the level of their column: "near"
+// (levels L - gap + 1 .. L - 1: the values the row waits for last) and "far"
+// (level <= L - gap, usually final long before).  The row's near entries come first, all read by
+// the row's first lane (its leader); then its far entries, dealt to the V
+// lanes round-robin (lane k reads far entries k, k + V, ...).  Each group is
+// in ascending column order.  Layout (16-byte aligned parts):
+//   int32 nr, ne, L, (tiles of level L-1) | (tiles of level L-gap) << 16
 //   lane record x 32 (8 bytes each): uint16 row (block-local; 0xFFFF = idle),
-//     uint16 first (index of the lane's first entry in the tile), uint8 count
-//     (entries of the lane, strided by V), uint8 log2 V, uint8 r | leader << 7
-//     (r = row within the tile, leader = first lane of the row), uint8 far
-//     count of the lane
+//     uint16 first (index of the lane's first far entry in the tile), uint8
+//     far count of the lane, uint8 log2 V, uint8 r | leader << 7 (r = row
+//     within the tile), uint8 near count (leader; its near entries are the
+//     ones just before `first`)
 //   TS dinv[nr] | uint16 col[ne] (block-local) | TS val[ne]
 // A lane reads its whole role with one 8-byte load.  The plan (rows of every
-// tile in packing order and their V) is built on the host; one tile per thread.
+// tile in packing order and their V) is built on the host; one tile per
+// thread.  *bad is set if a row has more than 255 near entries.
 template <typename TS>
 __global__ void k_vt_fill(int dir, int64_t ntiles, const int32_t* __restrict__ tile_rows_ptr,
                           const int32_t* __restrict__ plan_rows, const int8_t* __restrict__ plan_logv,
@@ -520,7 +522,7 @@ __global__ void k_vt_fill(int dir, int64_t ntiles, const int32_t* __restrict__ t
                           const int64_t* __restrict__ pdiag, const double* __restrict__ F,
                           const double* __restrict__ dinv, const int32_t* __restrict__ lev,
                           const int64_t* __restrict__ toff, const int32_t* __restrict__ tile_meta,
-                          unsigned char* __restrict__ stream) {
+                          unsigned char* __restrict__ stream, int* __restrict__ bad, int gap) {
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < ntiles; t += (int64_t)gridDim.x * blockDim.x) {
     unsigned char* base = stream + toff[t];
     const int r0 = tile_rows_ptr[t], nr = tile_rows_ptr[t + 1] - r0;
@@ -540,22 +542,22 @@ __global__ void k_vt_fill(int dir, int64_t ntiles, const int32_t* __restrict__ t
       const int32_t b = rb[i];
       const int64_t s = bp[b], e = bp[b + 1];
       const int len = strict_count(dir, i, s, e, prp, pci, pdiag);
-      // far entries of the row: in-block strict columns two or more levels down
       const int64_t t0 = dir == 0 ? prp[i] : pdiag[i] + 1;
       const int64_t t1 = dir == 0 ? pdiag[i] : prp[i + 1];
       int nfar = 0;
       for (int64_t q = t0; q < t1; ++q) {
         const int32_t j = pci[q];
-        if (j >= s && j < e && lev[j] <= lev[i] - 2) ++nfar;
+        if (j >= s && j < e && lev[j] <= lev[i] - gap) ++nfar;
       }
+      const int nnear = len - nfar;
+      if (nnear > 255) *bad = 1;
       dv[r] = (TS)dinv[i];
       for (int k = 0; k < V; ++k) {
-        const int cnt = k < len ? (len - k + V - 1) / V : 0;
         const int cfar = k < nfar ? (nfar - k + V - 1) / V : 0;
         rec[4 * (lane + k) + 0] = (uint16_t)(i - s);
-        rec[4 * (lane + k) + 1] = (uint16_t)(ne + k);
-        rec[4 * (lane + k) + 2] = (uint16_t)(cnt | (lv << 8));
-        rec[4 * (lane + k) + 3] = (uint16_t)(r | (k == 0 ? 0x80 : 0) | (cfar << 8));
+        rec[4 * (lane + k) + 1] = (uint16_t)(ne + nnear + k);
+        rec[4 * (lane + k) + 2] = (uint16_t)(cfar | (lv << 8));
+        rec[4 * (lane + k) + 3] = (uint16_t)(r | (k == 0 ? 0x80 | ((nnear & 0xFF) << 8) : 0));
       }
       lane += V;
       ne += len;
@@ -573,11 +575,11 @@ __global__ void k_vt_fill(int dir, int64_t ntiles, const int32_t* __restrict__ t
       const int64_t s = bp[b], e = bp[b + 1];
       const int64_t t0 = dir == 0 ? prp[i] : pdiag[i] + 1;
       const int64_t t1 = dir == 0 ? pdiag[i] : prp[i + 1];
-      for (int pass = 0; pass < 2; ++pass) {  // far entries, then near ones
+      for (int pass = 0; pass < 2; ++pass) {  // near entries, then far ones
         for (int64_t q = t0; q < t1; ++q) {
           const int32_t j = pci[q];
           if (j < s || j >= e) continue;
-          if ((lev[j] <= lev[i] - 2) != (pass == 0)) continue;
+          if ((lev[j] <= lev[i] - gap) != (pass == 1)) continue;
           col[at] = (uint16_t)(j - s);
           val[at] = (TS)F[q];
           ++at;
@@ -717,15 +719,16 @@ cudaError_t pack_fill(int dir, int64_t npos, const int32_t* row_block, const int
 cudaError_t vt_fill(int dir, int64_t ntiles, const int32_t* tile_rows_ptr, const int32_t* plan_rows,
                     const int8_t* plan_logv, const int32_t* row_block, const int64_t* bp, const int64_t* prp,
                     const int32_t* pci, const int64_t* pdiag, const double* F, const double* dinv, const int32_t* lev,
-                    int prec, const int64_t* toff, const int32_t* tile_meta, unsigned char* stream, cudaStream_t st) {
+                    int prec, const int64_t* toff, const int32_t* tile_meta, unsigned char* stream, int* bad,
+                    int gap, cudaStream_t st) {
   if (prec == 32) {
     k_vt_fill<float><<<grid_for(ntiles, 128), 128, 0, st>>>(dir, ntiles, tile_rows_ptr, plan_rows, plan_logv,
                                                             row_block, bp, prp, pci, pdiag, F, dinv, lev, toff,
-                                                            tile_meta, stream); count_launch();
+                                                            tile_meta, stream, bad, gap); count_launch();
   } else {
     k_vt_fill<double><<<grid_for(ntiles, 128), 128, 0, st>>>(dir, ntiles, tile_rows_ptr, plan_rows, plan_logv,
                                                              row_block, bp, prp, pci, pdiag, F, dinv, lev, toff,
-                                                             tile_meta, stream); count_launch();
+                                                             tile_meta, stream, bad, gap); count_launch();
   }
   return cudaGetLastError();
 }

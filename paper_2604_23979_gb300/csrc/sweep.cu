@@ -4,15 +4,18 @@
 // One CTA per diagonal block (all blocks are independent work of one launch).
 // The block's rows are grouped by level (Sec. 2.2, level scheduling); the
 // rows of one level are packed into 32-lane tiles, a row taking V lanes.
-// Each tile is a contiguous byte record in HBM:
-//   [16 B header: nr, ne][32 lane records, 8 B each][inverse diagonals, nr]
+// Each tile is a contiguous byte record in HBM (format in precond.cu,
+// k_vt_fill):
+//   [16 B header: nr, ne, level, tiles of the two levels below]
+//   [32 lane records, 8 B each][inverse diagonals, nr]
 //   [block-local columns, ne x u16][values, ne]            (16-byte aligned parts)
-// A lane record is {row (0xFFFF: idle), first entry, entry count | log2 V << 8,
-// row-in-tile | first-lane-of-row << 8}.
+// A row's entries are split into "near" ones (columns one level below the
+// row, read by the row's leader lane) and "far" ones (two or more levels
+// below, dealt round-robin to the row's lanes).
 // Warp w of the CTA takes the block's tiles w, w+W, ... in order; its lanes
 // keep cp.async copies of the next SLOTS-1 tiles in flight into the warp's
 // shared-memory ring while the warp solves the current tile.  y lives in
-// shared memory, initialised to a signalling-NaN sentinel; a tile waits
+// shared memory, initialised to a signalling-NaN sentinel; a tile polls
 // (warp-uniformly, bounded) until every value it reads is no longer the
 // sentinel, so no barrier separates the levels.
 #include <type_traits>
@@ -113,106 +116,108 @@ __device__ __forceinline__ unsigned long long ff_from_double(double d) {
 __device__ __forceinline__ double ff_to_double(unsigned long long v) { return (double)ff_hi(v) + (double)ff_lo(v); }
 
 // Arithmetic of one sweep: the type X of a solved value in shared memory,
-// the type VV of a factor value in registers, and a lane's accumulator (two
-// chains fed alternately by the unrolled slots, for instruction-level
-// parallelism; the slot order is fixed, so results are deterministic).
+// the type VV of a factor value in registers, and a lane's accumulator.  A
+// row's sum starts at -(right-hand side) in its leader lane, so that
+// y = -(sum) * dinv at the end; the far entries feed two chains alternately
+// (instruction-level parallelism; the slot order is fixed, so results are
+// deterministic); the lanes' far sums are added into the leader before the
+// row waits for its near entries, which the leader then adds one by one.
 template <typename TS, typename TC, bool FF>
 struct SweepArith {  // plain: TC = float or double
   using X = TC;
   using VV = TC;
+  using D = TC;
   struct Acc {
     TC a0, a1;
   };
   static __device__ __forceinline__ X sent() { return sentinel(TC(0)); }
   static __device__ __forceinline__ bool is_sent(X x) { return is_sentinel(x); }
   static __device__ __forceinline__ VV val(TS v) { return (TC)v; }
-  static __device__ __forceinline__ void init(Acc& a) { a.a0 = TC(0); a.a1 = TC(0); }
+  static __device__ __forceinline__ void init(Acc& a, X minus_in_of) { a.a0 = -minus_in_of; a.a1 = TC(0); }
   static __device__ __forceinline__ void add(Acc& a, int k, VV v, X x) {  // k: unrolled slot
     if (k & 1) a.a1 = fma(v, x, a.a1);
     else a.a0 = fma(v, x, a.a0);
   }
-  // y = (in - (far + near)) * d after the lane-group sum
-  static __device__ __forceinline__ X finish(const Acc& far, const Acc& near, int V, int Vmax, X in, TC d,
-                                             bool leader) {
-    TC acc = (far.a0 + far.a1) + (near.a0 + near.a1);
-    acc = segmented_sum(acc, V, Vmax);
-    return leader ? (in - acc) * d : TC(0);
+  // far sum of the row's lane group, valid in every lane of the group
+  static __device__ __forceinline__ void gather(Acc& a, int V, int Vmax) {
+    a.a0 = segmented_sum(a.a0 + a.a1, V, Vmax);
+    a.a1 = TC(0);
   }
+  static __device__ __forceinline__ void add_near(Acc& a, VV v, X x) { a.a0 = fma(v, x, a.a0); }
+  static __device__ __forceinline__ X finish(const Acc& a, D d) { return -a.a0 * d; }
 };
 
 template <typename TS, typename TC>
 struct SweepArith<TS, TC, true> {  // float-float (TS = float)
   using X = unsigned long long;
   using VV = float;
+  using D = float;
   struct Acc {
     float s0, c0, s1, c1;
   };
   static __device__ __forceinline__ X sent() { return kFFSentinel; }
   static __device__ __forceinline__ bool is_sent(X x) { return x == kFFSentinel; }
   static __device__ __forceinline__ VV val(float v) { return v; }
-  static __device__ __forceinline__ void init(Acc& a) { a.s0 = a.c0 = a.s1 = a.c1 = 0.f; }
+  static __device__ __forceinline__ void init(Acc& a, X in) {
+    a.s0 = -ff_hi(in);
+    a.c0 = -ff_lo(in);
+    a.s1 = a.c1 = 0.f;
+  }
   static __device__ __forceinline__ void add(Acc& a, int k, VV v, X x) {
     if (k & 1) dot2_step(v, ff_hi(x), ff_lo(x), a.s1, a.c1);
     else dot2_step(v, ff_hi(x), ff_lo(x), a.s0, a.c0);
   }
-  // renormalised pair of an accumulator
-  static __device__ __forceinline__ void pair(const Acc& a, float& h, float& l) {
+  static __device__ __forceinline__ void gather(Acc& a, int V, int Vmax) {
+    float h, l;
     two_sum(a.s0, a.s1, h, l);
     l = __fadd_rn(l, __fadd_rn(a.c0, a.c1));
-    const float hh = __fadd_rn(h, l);
-    l = __fsub_rn(l, __fsub_rn(hh, h));
-    h = hh;
-  }
-  static __device__ __forceinline__ X finish(const Acc& far, const Acc& near, int V, int Vmax, X in, float d,
-                                             bool leader) {
-    float ah, al, bh, bl;
-    pair(far, ah, al);
-    pair(near, bh, bl);
-    ff_add(ah, al, bh, bl);
-    for (int o = Vmax >> 1; o > 0; o >>= 1) {
-      const float ph = __shfl_xor_sync(0xffffffffu, ah, o);
-      const float pl = __shfl_xor_sync(0xffffffffu, al, o);
-      if (o < V) ff_add(ah, al, ph, pl);
+    {
+      const float hh = __fadd_rn(h, l);
+      l = __fsub_rn(l, __fsub_rn(hh, h));
+      h = hh;
     }
-    if (!leader) return 0ull;
-    // y = (in - acc) * d in float-float
-    float dh = ff_hi(in), dl = ff_lo(in);
-    ff_add(dh, dl, -ah, -al);
-    const float p = __fmul_rn(dh, d);
-    float pe = __fmaf_rn(dh, d, -p);
-    pe = __fmaf_rn(dl, d, pe);
+    for (int o = Vmax >> 1; o > 0; o >>= 1) {
+      const float ph = __shfl_xor_sync(0xffffffffu, h, o);
+      const float pl = __shfl_xor_sync(0xffffffffu, l, o);
+      if (o < V) ff_add(h, l, ph, pl);
+    }
+    a.s0 = h;
+    a.c0 = l;
+    a.s1 = a.c1 = 0.f;
+  }
+  static __device__ __forceinline__ void add_near(Acc& a, VV v, X x) { dot2_step(v, ff_hi(x), ff_lo(x), a.s0, a.c0); }
+  // y = -(s0 + c0) * d in float-float
+  static __device__ __forceinline__ X finish(const Acc& a, D d) {
+    float h, l;
+    two_sum(a.s0, a.c0, h, l);  // |c0| can exceed |s0| after cancellation
+    const float p = __fmul_rn(h, d);
+    float pe = __fmaf_rn(h, d, -p);
+    pe = __fmaf_rn(l, d, pe);
     const float yh = __fadd_rn(p, pe);
     const float yl = __fsub_rn(pe, __fsub_rn(yh, p));
-    return ff_pack(yh, yl);
+    return ff_pack(-yh, -yl);
   }
 };
 
-// Loads out[jj[k]] for KR slots and, with per-level readiness, waits (once,
-// if `wait`) until done[wl] >= need + pad; values that still held the
-// sentinel when they were loaded are reloaded after the wait.  With per-value
-// readiness (done == nullptr) the warp polls until no loaded value is the
-// sentinel.  Every wait is bounded by `limit` polls (then *timeout = 1).
+// Bounded wait until done[wl] >= need + pad (one broadcast acquire load per
+// poll for the whole warp).  Sets *timeout and returns when it gives up.
+__device__ __forceinline__ void wait_count(int* done, int wl, int need, int pad, unsigned backoff, int limit,
+                                           int* timeout) {
+  const unsigned addr = smem_u32(done + wl);
+  int spins = 0;
+  while (ld_acquire_cta(addr) < need + pad) {
+    if (backoff) __nanosleep(backoff);
+    if (++spins > limit) { *timeout = 1; break; }
+  }
+}
+
+// Loads out[jj[k]] for KR slots (jj < 0: none) and polls, warp-uniformly and
+// bounded, until no loaded value is the sentinel.  A value that is not the
+// sentinel is final: it is written once per sweep.
 template <typename AR, int KR>
 __device__ __forceinline__ void load_ready(const int (&jj)[KR], typename AR::X (&xv)[KR],
-                                           volatile typename AR::X* out, int* done, bool wait, int wl, int need,
-                                           int pad, unsigned backoff, int limit, int* timeout) {
+                                           volatile typename AR::X* out, unsigned backoff, int limit, int* timeout) {
   using X = typename AR::X;
-  if (done) {
-#pragma unroll
-    for (int k = 0; k < KR; ++k) xv[k] = jj[k] >= 0 ? out[jj[k]] : X(0);
-    if (wait) {
-      const unsigned addr = smem_u32(done + wl);  // every lane polls the same counter
-      int spins = 0;
-      while (ld_acquire_cta(addr) < need + pad) {
-        if (backoff) __nanosleep(backoff);
-        if (++spins > limit) { *timeout = 1; break; }
-      }
-#pragma unroll
-      for (int k = 0; k < KR; ++k)
-        if (jj[k] >= 0 && AR::is_sent(xv[k])) xv[k] = out[jj[k]];
-    }
-    return;
-  }
   bool ready = true;
 #pragma unroll
   for (int k = 0; k < KR; ++k) {
@@ -239,26 +244,31 @@ __device__ __forceinline__ void load_ready(const int (&jj)[KR], typename AR::X (
 }
 
 // One sweep of a block.  `in` holds the right-hand side, `out` the solution
-// (sentinel until solved).  Only warps w < W take tiles.  A tile's rows are
-// at one level L; each lane first sums its "far" entries (columns at levels
-// <= L - 2), then its "near" ones (level L - 1).  Readiness is per value
-// (`done` null: a tile waits until no value it reads is the sentinel) or per
-// level: the far part waits until every tile of level L - 2 has counted
-// itself in done[L - 2], the near part until level L - 1 has (since each of
-// those tiles waited for its own level below, every lower level is then
-// complete too).  Far entries make up most of a row and are summed while
-// level L - 1 is still being solved; only the near ones (about one per row)
-// stay on the level-to-level critical path.
+// (sentinel until solved; an aligned store publishes value and readiness at
+// once).  Only warps w < W take tiles.  A tile's rows are at one level L.
+// Each lane first sums its "far" entries (columns at levels <= L - gap) --
+// with per-level counters (`done`) the warp first waits, with one broadcast
+// poll, until level L - gap is counted complete (a tile counts itself only
+// after its values are stored and its own level below is complete, so this
+// means every level <= L - gap is solved) -- and the lanes' far sums are
+// added into the row's leader.  Only then does the leader load its "near"
+// entries (levels L - gap + 1 .. L - 1), polling the values themselves: one
+// or two per row, the only arithmetic left between a value's store and the
+// next level's.  The gap lets the counts, whose releases trail the values,
+// gate the far part without delaying it.  Readiness
+// is always confirmed on the values, so a value is never used before it is
+// final; the counters spare the waiting warps the value polls.
 template <typename TS, typename TC, bool FF, int SLOTS, int KREG, int KNEAR>
 __device__ __forceinline__ void sweep_staged(const unsigned char* __restrict__ stream, const int64_t* toff_s,
                                              int ntile, unsigned char* ring, int slot_bytes,
                                              volatile typename SweepArith<TS, TC, FF>::X* in,
                                              volatile typename SweepArith<TS, TC, FF>::X* out, bool unit,
-                                             int* timeout, int W, unsigned backoff, int* done, int limit, int pad) {
+                                             int* timeout, int W, unsigned backoff, int* done, int limit, int pad,
+                                             int gap) {
   using AR = SweepArith<TS, TC, FF>;
   using X = typename AR::X;
   using VV = typename AR::VV;
-  using DV = typename std::conditional<FF, float, TC>::type;
+  using D = typename AR::D;
   const int lane = lane_id(), w = threadIdx.x >> 5;
   if (w >= W) return;
   const int nk = ntile > w ? (ntile - w + W - 1) / W : 0;  // tiles of this warp
@@ -295,28 +305,28 @@ __device__ __forceinline__ void sweep_staged(const unsigned char* __restrict__ s
     const int ne = reinterpret_cast<const int32_t*>(base)[1];
     const int level = reinterpret_cast<const int32_t*>(base)[2];
     const unsigned needs = reinterpret_cast<const uint32_t*>(base)[3];
-    const int need1 = (int)(needs & 0xFFFFu), need2 = (int)(needs >> 16);
+    const int need1 = (int)(needs & 0xFFFFu), needg = (int)(needs >> 16);
     const uint2 rec = reinterpret_cast<const uint2*>(base + 16)[lane];  // this lane's role, one load
     const int row = (int)(rec.x & 0xFFFFu);
     const int first = (int)(rec.x >> 16);
-    const int cnt = (int)(rec.y & 0xFFu);
+    const int nfar = (int)(rec.y & 0xFFu);
     const int V = 1 << ((rec.y >> 8) & 0xFFu);
     const int r = (int)((rec.y >> 16) & 0x7Fu);
     const bool leader = ((rec.y >> 23) & 1u) != 0;
-    const int nfar = (int)(rec.y >> 24);
+    const int nnear = (int)(rec.y >> 24);
     const int Vmax = (int)__reduce_max_sync(0xffffffffu, (unsigned)V);
     const TS* dv = reinterpret_cast<const TS*>(base + 16 + 256);
     const uint16_t* cols = reinterpret_cast<const uint16_t*>(base + 16 + 256 + ((nr * (int)sizeof(TS) + 15) & ~15));
     const TS* vals = reinterpret_cast<const TS*>(reinterpret_cast<const unsigned char*>(cols) + ((2 * ne + 15) & ~15));
     // The right-hand side and the inverse diagonal are final before the
-    // sweep starts: read them before waiting, off the critical path.
+    // sweep starts: read them first, off the critical path.
     const X inr = leader ? in[row] : X(0);
-    const DV dvr = leader && !unit ? (DV)dv[r] : DV(1);
-    typename AR::Acc af, an;
-    AR::init(af);
-    AR::init(an);
-    // far entries [0, nfar) of the lane, KREG per warp-uniform round
+    const D dvr = leader && !unit ? (D)dv[r] : D(1);
+    typename AR::Acc acc;
+    AR::init(acc, inr);
+    // far entries of the lane, KREG per warp-uniform round
     const int rfar = __reduce_max_sync(0xffffffffu, (unsigned)((nfar + KREG - 1) / KREG));
+    if (done && level >= gap && rfar > 0) wait_count(done, level - gap, needg, pad, backoff, limit, timeout);
     for (int c = 0; c < rfar; ++c) {
       int jj[KREG];
       VV vv[KREG];
@@ -329,40 +339,42 @@ __device__ __forceinline__ void sweep_staged(const unsigned char* __restrict__ s
         jj[k2] = ok ? (int)cols[e] : -1;
         vv[k2] = ok ? AR::val(vals[e]) : VV(0);
       }
-      load_ready<AR, KREG>(jj, xv, out, done, c == 0 && level >= 2, level - 2, need2, pad, backoff, limit, timeout);
+      load_ready<AR, KREG>(jj, xv, out, backoff, limit, timeout);
 #pragma unroll
-      for (int k2 = 0; k2 < KREG; ++k2) AR::add(af, k2, vv[k2], xv[k2]);
+      for (int k2 = 0; k2 < KREG; ++k2) AR::add(acc, k2, vv[k2], xv[k2]);
     }
-    // near entries [nfar, cnt), KNEAR per round; the first round waits for
-    // level L - 1 (a tile with no near entry still waits once, so that its
-    // own completion count keeps implying every lower level's)
-    const int rnear = __reduce_max_sync(0xffffffffu, (unsigned)((cnt - nfar + KNEAR - 1) / KNEAR));
-    if (done && level >= 1 && rnear == 0) {
-      int jj[1] = {-1};
-      X xv[1];
-      load_ready<AR, 1>(jj, xv, out, done, true, level - 1, need1, pad, backoff, limit, timeout);
-    }
+    AR::gather(acc, V, Vmax);
+    // near entries (leader lanes), KNEAR per round; under the timeout-path
+    // test the tile first waits for a count of level L - 1 that never comes
+    if (pad && done && level >= 1) wait_count(done, level - 1, need1, pad, backoff, limit, timeout);
+    const int near0 = first - nnear;
+    const int rnear = __reduce_max_sync(0xffffffffu, (unsigned)((nnear + KNEAR - 1) / KNEAR));
     for (int c = 0; c < rnear; ++c) {
       int jj[KNEAR];
       VV vv[KNEAR];
       X xv[KNEAR];
 #pragma unroll
       for (int k2 = 0; k2 < KNEAR; ++k2) {
-        const int idx = nfar + c * KNEAR + k2;
-        const bool ok = idx < cnt;
-        const int e = first + idx * V;
-        jj[k2] = ok ? (int)cols[e] : -1;
-        vv[k2] = ok ? AR::val(vals[e]) : VV(0);
+        const int idx = c * KNEAR + k2;
+        const bool ok = idx < nnear;
+        jj[k2] = ok ? (int)cols[near0 + idx] : -1;
+        vv[k2] = ok ? AR::val(vals[near0 + idx]) : VV(0);
       }
-      load_ready<AR, KNEAR>(jj, xv, out, done, c == 0 && level >= 1, level - 1, need1, pad, backoff, limit,
-                            timeout);
+      load_ready<AR, KNEAR>(jj, xv, out, backoff, limit, timeout);
 #pragma unroll
-      for (int k2 = 0; k2 < KNEAR; ++k2) AR::add(an, k2, vv[k2], xv[k2]);
+      for (int k2 = 0; k2 < KNEAR; ++k2)
+        if (jj[k2] >= 0) AR::add_near(acc, vv[k2], xv[k2]);
     }
-    const X y = AR::finish(af, an, V, Vmax, inr, dvr, leader);
-    if (leader) out[row] = y;
+    if (leader) out[row] = AR::finish(acc, dvr);
     __syncwarp();  // the slot of tile k-1 is free: refill it with tile k+SLOTS-1
-    if (done && lane == 0) red_release_cta(smem_u32(done + level));  // the tile's values before its count
+    if (done) {
+      // The tile counts itself in done[L] once its values are stored and
+      // level L - 1 is counted complete, so a complete done[L] means every
+      // level <= L is solved.  The next level's rows read this tile's values
+      // directly, so neither wait nor count is on their path.
+      if (level >= 1) wait_count(done, level - 1, need1, 0, backoff, limit, timeout);
+      if (lane == 0) red_release_cta(smem_u32(done + level));  // the tile's values before its count
+    }
     issue(k + SLOTS - 1);
   }
   cp_async_wait<0>();
@@ -434,7 +446,7 @@ __global__ void __launch_bounds__(kSweepWarps * 32) k_pcg_update_staged(TriSolve
   __syncthreads();
   sweep_staged<TS, TC, FF, SLOTS, KREG, kNear>(M.fwd_stream, toff_f, ntf, ring, M.slot_bytes, yb, yf,
                                                M.unit_lower != 0, &timeout, M.sweep_warps, (unsigned)M.backoff_ns,
-                                               done, M.wait_limit, M.wait_pad);
+                                               done, M.wait_limit, M.wait_pad, M.far_gap);
   __syncthreads();
   for (int64_t i = threadIdx.x; i < e0 - s0; i += blockDim.x) yb[i] = S;
   if (done)
@@ -442,7 +454,7 @@ __global__ void __launch_bounds__(kSweepWarps * 32) k_pcg_update_staged(TriSolve
   __syncthreads();
   sweep_staged<TS, TC, FF, SLOTS, KREG, kNear>(M.bwd_stream, toff_b, ntb, ring, M.slot_bytes, yf, yb, false,
                                                &timeout, M.sweep_warps, (unsigned)M.backoff_ns, done, M.wait_limit,
-                                               M.wait_pad);
+                                               M.wait_pad, M.far_gap);
   __syncthreads();
   double rz = 0.0, zq = 0.0;
   for (int64_t i = s0 + threadIdx.x; i < e0; i += blockDim.x) {

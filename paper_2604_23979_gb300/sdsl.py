@@ -32,7 +32,7 @@ class sdsl_options(C.Structure):
         ("graph_iters", C.c_int), ("tune", C.c_int), ("profile", C.c_int), ("apply_prec", C.c_int),
         ("flexible", C.c_int), ("solve_kernel", C.c_int), ("spmv_form", C.c_int), ("orthog", C.c_int),
         ("sweep_warps", C.c_int), ("sweep_backoff_ns", C.c_int), ("sweep_lane_entries", C.c_int),
-        ("schur_lu", C.c_int), ("sweep_wait", C.c_int), ("wait_limit", C.c_int), ("wait_test", C.c_int),
+        ("schur_lu", C.c_int), ("sweep_wait", C.c_int), ("wait_limit", C.c_int), ("sweep_far_gap", C.c_int), ("wait_test", C.c_int),
     ]
 
 
