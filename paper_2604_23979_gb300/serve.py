@@ -42,6 +42,7 @@ class SolveRecord:
     status: int
     rel_res: float
     x: Optional[np.ndarray] = None
+    rebuilt: int = 0      # 1 if the preconditioner was rebuilt for this solve (reuse rule)
 
 
 @dataclasses.dataclass
@@ -212,7 +213,7 @@ class GpuServer:
                     x = d_x.cpu().numpy() if self.keep_x else None
                     stream.synchronize()
                     recs.append(SolveRecord(start, time.perf_counter() - t0, int(st.iters), int(st.status),
-                                            float(st.rel_res_true), x))
+                                            float(st.rel_res_true), x, int(st.rebuilt)))
             finally:
                 sdsl.sdsl_free(h)
         return recs

@@ -49,7 +49,7 @@ def iters_close(gpu, ref):
     return abs(gpu - ref) <= max(1, int(np.ceil(0.05 * ref)))
 
 
-def replay_reuse(prob, thetas, ratio=1.5, maxit=None, keep_x=()):
+def replay_reuse(prob, thetas, ratio=1.5, maxit=None, keep_x=None):
     """The preconditioner-reuse rule (Sec. 3.4) replayed on the oracle over a
     theta sequence: factor at step 0; the first converged solve after a build
     is the baseline; a converged solve needing more than ratio x the baseline,
@@ -75,14 +75,17 @@ def replay_reuse(prob, thetas, ratio=1.5, maxit=None, keep_x=()):
             base, since, rebuilt = -1, 0, 1
             r = oracle.pcg_bj(S, state.P, state.F, prob.block_ptr, prob.b, rtol=prob.rtol, maxit=maxit)
         since += 1
+        margin = None  # how close this solve came to the ratio threshold (relative)
         if r.status == 0:
             if base < 0:
                 base = r.iters
-            elif r.iters > ratio * base:
-                need = True
+            else:
+                margin = abs(r.iters / (ratio * base) - 1.0)
+                if r.iters > ratio * base:
+                    need = True
         else:
             need = True
-        out.append(dict(k=k, iters=r.iters, status=r.status, rebuilt=rebuilt, discarded=discarded,
+        out.append(dict(k=k, iters=r.iters, status=r.status, rebuilt=rebuilt, discarded=discarded, margin=margin,
                         relres=float(np.linalg.norm(prob.b - oracle.spmv(S, r.x)) / np.linalg.norm(prob.b)),
-                        x=r.x if k in keep_x else None))
+                        x=r.x if keep_x is None or k in keep_x else None))
     return out
