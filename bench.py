@@ -488,13 +488,19 @@ def run_c4(args, local):
                 st = sdsl.sdsl_solve(h, b, x)
                 steps.append(dict(k=k, iters=int(st.iters), status=int(st.status), rebuilt=int(st.rebuilt),
                                   ms_update=upd, ms_factor=st.ms_factor if st.rebuilt else 0.0, ms_solve=st.ms_solve,
-                                  relres=st.rel_res_true))
+                                  relres=st.rel_res_true, discarded=int(st.iters_discarded)))
             wall = time.perf_counter() - t0
         finally:
             sdsl.sdsl_free(h)
         total = first + sum(s["ms_update"] + s["ms_factor"] + s["ms_solve"] for s in steps)
+        conv = [s for s in steps if s["status"] == 0]
         out["forms"][f"f{prec}"] = {
             "ms_per_ipm_step": round(total / len(steps), 2), "rebuilds": sum(s["rebuilt"] for s in steps),
+            "converged_steps": len(conv),
+            "ms_per_converged_step": (round((first + sum(s["ms_update"] + s["ms_factor"] + s["ms_solve"]
+                                                          for s in conv)) / len(conv), 2) if conv else None),
+            "first_unconverged_step": next((s["k"] for s in steps if s["status"] != 0), None),
+            "iters_discarded": sum(s["discarded"] for s in steps),
             "setup_factor_ms": round(first, 1), "wall_s": round(wall, 2),
             "iters": [s["iters"] for s in steps], "unconverged": sum(1 for s in steps if s["status"] != 0),
             "max_relres": max(s["relres"] for s in steps),

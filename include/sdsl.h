@@ -247,6 +247,13 @@ sdsl_status sdsl_export_precond(sdsl_handle h, int64_t* rowptr, int32_t* col, do
 sdsl_status sdsl_export_levels(sdsl_handle h, int which, int32_t* nlev, int64_t* level_ptr, int32_t* level_rows);
 sdsl_status sdsl_export_schur(sdsl_handle h, double* sb);
 
+/* BBD only (Sec. 2.4, the dense border factorization): the LU's pivot rows
+ * (ipiv[k] = row swapped with row k at step k, border-local, border entries)
+ * and its pivots u_kk in FP64 (the blocked LU, schur_lu 0 or 1, chooses and
+ * keeps them in FP64; the unblocked one, schur_lu 2, gives its FP32 u_kk
+ * widened).  Host buffers; either may be NULL. */
+sdsl_status sdsl_export_schur_lu(sdsl_handle h, int32_t* ipiv, double* pivots);
+
 /* y = A x with the handle's system matrix (device pointers, FP64). */
 sdsl_status sdsl_spmv(sdsl_handle h, const double* x, double* y);
 

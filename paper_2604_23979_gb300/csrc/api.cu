@@ -170,6 +170,7 @@ struct sdsl_handle_s {
   double* SB = nullptr;
   float *LU32 = nullptr, *Sinv = nullptr;
   int32_t* ipiv = nullptr;
+  double* udiag = nullptr;  // FP64 pivots of the blocked LU (modes 0, 1)
   double *V = nullptr, *Z = nullptr, *bt = nullptr, *bg = nullptr, *bz = nullptr, *bres = nullptr, *bcor = nullptr;
   double *gpart = nullptr, *gh = nullptr;
   std::vector<int32_t> h_lev_off_lo, h_lev_off_up;
@@ -681,6 +682,7 @@ sdsl_status build_bbd(sdsl_handle h) {
   TRY(h->pc.get(&h->LU32, m * m));
   TRY(h->pc.get(&h->Sinv, m * m));
   TRY(h->pc.get(&h->ipiv, m));
+  TRY(h->pc.get(&h->udiag, m));
   TRY_CUDA(schur_init(m, h->b0, h->p_rp, h->p_ci, h->p_v, h->SB, h->st));
   Arena tmp;
   tmp.st = h->st;
@@ -737,10 +739,15 @@ sdsl_status build_bbd(sdsl_handle h) {
   }
   TRY_CUDA(cudaEventRecord(ev[1], h->st));
   TRY_CUDA(cudaMemsetAsync(h->flag, 0, sizeof(int), h->st));
-  TRY_CUDA(dense_lu_f32(m, h->SB, h->LU32, h->ipiv, h->flag, h->opt.schur_lu, h->st));
+  double* W64;
+  TRY(tmp.get(&W64, (size_t)m * 64));
+  const bool blocked = h->opt.schur_lu != 2;
+  TRY_CUDA(dense_lu_f32(m, h->SB, h->LU32, h->ipiv, blocked ? W64 : nullptr, blocked ? h->udiag : nullptr, h->flag,
+                        h->opt.schur_lu, h->st));
   TRY_CUDA(cudaEventRecord(ev[2], h->st));
   TRY(tmp.get(&work, (size_t)m * ((m + 31) / 32) * 32));
-  TRY_CUDA(dense_lu_inverse(m, h->LU32, h->ipiv, h->Sinv, work, h->opt.schur_lu, h->flag, h->st));
+  TRY_CUDA(dense_lu_inverse(m, h->LU32, h->ipiv, blocked ? h->udiag : nullptr, h->Sinv, work, h->opt.schur_lu,
+                            h->flag, h->st));
   TRY_CUDA(cudaEventRecord(ev[3], h->st));
   int bad = 0;
   TRY(to_host(h, &bad, h->flag, 1));
@@ -1917,6 +1924,26 @@ sdsl_status sdsl_export_schur(sdsl_handle h, double* sb) {
   Scope scope(h);
   if (h->nbord > 0) TRY(to_host(h, sb, h->SB, h->nbord * h->nbord));
   return sync(h, "export schur");
+}
+
+sdsl_status sdsl_export_schur_lu(sdsl_handle h, int32_t* ipiv, double* pivots) {
+  if (!h) return fail(SDSL_ERR_ARG, "handle is NULL");
+  if (h->method != SDSL_BBD_GMRES || !h->factored) return fail(SDSL_ERR_STATE, "no Schur complement (BBD, factored)");
+  Scope scope(h);
+  const int64_t m = h->nbord;
+  if (m == 0) return SDSL_OK;
+  if (ipiv) TRY(to_host(h, ipiv, h->ipiv, m));
+  if (pivots) {
+    if (h->opt.schur_lu != 2) {
+      TRY(to_host(h, pivots, h->udiag, m));
+    } else {  // the unblocked FP32 LU: its diagonal, widened
+      std::vector<float> d(m);
+      for (int64_t k = 0; k < m; ++k) TRY(to_host(h, &d[k], h->LU32 + k * m + k, 1));
+      TRY(sync(h, "export schur lu"));
+      for (int64_t k = 0; k < m; ++k) pivots[k] = d[k];
+    }
+  }
+  return sync(h, "export schur lu");
 }
 
 sdsl_status sdsl_spmv(sdsl_handle h, const double* x, double* y) {

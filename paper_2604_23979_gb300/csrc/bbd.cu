@@ -433,12 +433,12 @@ cudaError_t schur_wave(int njobs, const SchurJob* jobs, int64_t b0, int64_t nb, 
   return cudaGetLastError();
 }
 
-cudaError_t dense_lu_f32(int64_t n, const double* SB, float* LU, int32_t* ipiv, int* status, int mode,
-                         cudaStream_t st) {
+cudaError_t dense_lu_f32(int64_t n, const double* SB, float* LU, int32_t* ipiv, double* W, double* udiag,
+                         int* status, int mode, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
   k_to_f32<<<grid_for(n * n, 256), 256, 0, st>>>(n * n, SB, LU); count_launch();
   SDSL_CUDA_TRY(cudaGetLastError());
-  if (mode != 2) return dense_lu_blocked(n, LU, ipiv, status, mode == 0 ? 1 : 0, st);
+  if (mode != 2) return dense_lu_blocked(n, LU, ipiv, W, udiag, status, mode == 0 ? 1 : 0, st);
   for (int64_t k = 0; k < n; ++k) {
     k_lu_pivot<<<1, 1024, 0, st>>>(n, k, LU, ipiv, status); count_launch();
     SDSL_CUDA_TRY(cudaGetLastError());
@@ -450,11 +450,12 @@ cudaError_t dense_lu_f32(int64_t n, const double* SB, float* LU, int32_t* ipiv, 
   return cudaSuccess;
 }
 
-cudaError_t dense_lu_inverse(int64_t n, const float* LU, const int32_t* ipiv, float* Xinv, float* work, int mode,
-                             int* status, cudaStream_t st) {
+cudaError_t dense_lu_inverse(int64_t n, const float* LU, const int32_t* ipiv, const double* udiag, float* Xinv,
+                             float* work, int mode, int* status, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
   if (mode != 2)
-    return dense_inverse_blocked(n, LU, ipiv, Xinv, reinterpret_cast<int32_t*>(work), status, mode == 0 ? 1 : 0, st);
+    return dense_inverse_blocked(n, LU, ipiv, udiag, Xinv, reinterpret_cast<int32_t*>(work), status,
+                                 mode == 0 ? 1 : 0, st);
   k_lu_inverse<<<(unsigned)((n + 31) / 32), 512, 0, st>>>(n, LU, ipiv, Xinv, work); count_launch();
   return cudaGetLastError();
 }

@@ -1,11 +1,14 @@
 // dense_lu.cu -- blocked LU with partial pivoting of the dense border Schur
 // complement (Sec. 2.4: S_B is dense and factored once per preconditioner
-// build), FP32, with the trailing update on the 5th-generation tensor cores.
+// build): FP32 storage, FP64 panels and pivots, the trailing update on the
+// 5th-generation tensor cores.
 //
 // Right-looking, panels of kNb columns:
-//   panel  (one CTA): for each column, pivot = largest |a_ik| (lowest i on
-//          ties), swap whole rows, l_ik = a_ik / a_kk, rank-1 update of the
-//          panel's remaining columns -- the unblocked algorithm on the panel;
+//   panel  (one CTA, FP64 on a widened copy of the panel): for each column,
+//          pivot = largest |a_ik| (lowest i on ties), swap whole rows,
+//          l_ik = a_ik / a_kk, rank-1 update of the panel's remaining
+//          columns -- the unblocked algorithm on the panel; the pivots a_kk
+//          are kept in FP64;
 //   trsm   U12 = L11^{-1} A12 (unit lower L11, one thread per column);
 //   update A22 -= L21 U12 as a tcgen05.mma GEMM (kind::tf32, accumulator in
 //          tensor memory).  FP32 accuracy from TF32 inputs by splitting each
@@ -83,6 +86,102 @@ __global__ void __launch_bounds__(kPanelThreads) k_lu_panel(int64_t n, int64_t k
         A[i * n + c] = __fmaf_rn(-A[i * n + k], ukc, A[i * n + c]);
     }
     __syncthreads();
+  }
+}
+
+// Panel in FP64 (the factorization's pivots): the panel's columns [k0, k0 +
+// kb) of rows [k0, n) are widened into W (row i - k0, column j at
+// W[(i - k0) * kNb + j]); pivot search (largest |w|, lowest row on ties),
+// scaling by the pivot and the panel's rank-1 updates run in FP64, and the
+// pivots are kept in FP64 (udiag[k]).  Row swaps act on W and, outside the
+// panel's columns, on the FP32 matrix; at the end the panel's values are
+// rounded back into it.  The trailing update (outside) stays FP32.
+__global__ void __launch_bounds__(kPanelThreads) k_lu_panel64(int64_t n, int64_t k0, int kb, float* __restrict__ A,
+                                                              double* __restrict__ W, double* __restrict__ udiag,
+                                                              int32_t* __restrict__ ipiv, int* __restrict__ status) {
+  __shared__ double bv[32];
+  __shared__ int64_t bi[32];
+  __shared__ int64_t piv;
+  const int64_t rows = n - k0;
+  for (int64_t t = threadIdx.x; t < rows * kb; t += blockDim.x) {
+    const int64_t i = t / kb, j = t % kb;
+    W[i * kNb + j] = (double)A[(k0 + i) * n + k0 + j];
+  }
+  __syncthreads();
+  for (int j = 0; j < kb; ++j) {
+    const int64_t k = k0 + j;
+    double best = -1.0;
+    int64_t bidx = j;
+    for (int64_t i = j + threadIdx.x; i < rows; i += blockDim.x) {
+      const double v = fabs(W[i * kNb + j]);
+      if (v > best) { best = v; bidx = i; }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ov = __shfl_xor_sync(0xffffffffu, best, o);
+      const int64_t oi = __shfl_xor_sync(0xffffffffu, bidx, o);
+      if (ov > best || (ov == best && oi < bidx)) { best = ov; bidx = oi; }
+    }
+    if (lane_id() == 0) { bv[threadIdx.x >> 5] = best; bi[threadIdx.x >> 5] = bidx; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double b = -1.0;
+      int64_t p = j;
+      for (unsigned w = 0; w < blockDim.x / 32; ++w)
+        if (bv[w] > b || (bv[w] == b && bi[w] < p)) { b = bv[w]; p = bi[w]; }
+      piv = p;
+      ipiv[k] = (int32_t)(k0 + p);
+      if (!(b > 0.0) || !isfinite(b)) *status = 1;
+    }
+    __syncthreads();
+    const int64_t p = piv;
+    if (p != j) {
+      for (int c = threadIdx.x; c < kb; c += blockDim.x) {
+        const double t = W[j * kNb + c];
+        W[j * kNb + c] = W[p * kNb + c];
+        W[p * kNb + c] = t;
+      }
+      for (int64_t c = threadIdx.x; c < n - kb; c += blockDim.x) {  // columns outside the panel
+        const int64_t cc = c < k0 ? c : c + kb;
+        const float t = A[k * n + cc];
+        A[k * n + cc] = A[(k0 + p) * n + cc];
+        A[(k0 + p) * n + cc] = t;
+      }
+    }
+    __syncthreads();
+    const double pk = W[j * kNb + j];
+    if (threadIdx.x == 0) udiag[k] = pk;
+    for (int64_t i = j + 1 + threadIdx.x; i < rows; i += blockDim.x) W[i * kNb + j] = W[i * kNb + j] / pk;
+    __syncthreads();
+    // rank-1 update, four rows per thread and round: all loads of a round
+    // are issued before its stores (the loop over one array cannot be
+    // reordered by the compiler otherwise)
+    const int rem = kb - j - 1;
+    const int tx = threadIdx.x & (kNb - 1), ty = threadIdx.x / kNb;
+    constexpr int kRs = kPanelThreads / kNb;  // row stride: 16
+    if (tx < rem) {
+      const int c = j + 1 + tx;
+      const double ukc = W[j * kNb + c];
+      for (int64_t i0 = j + 1 + ty; i0 < rows; i0 += 4 * kRs) {
+        double a[4], b[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int64_t i = i0 + u * kRs;
+          a[u] = i < rows ? W[i * kNb + j] : 0.0;
+          b[u] = i < rows ? W[i * kNb + c] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int64_t i = i0 + u * kRs;
+          if (i < rows) W[i * kNb + c] = __fma_rn(-a[u], ukc, b[u]);
+        }
+      }
+    }
+    __syncthreads();
+  }
+  for (int64_t t = threadIdx.x; t < rows * kb; t += blockDim.x) {
+    const int64_t i = t / kb, j = t % kb;
+    A[(k0 + i) * n + k0 + j] = (float)W[i * kNb + j];
   }
 }
 
@@ -344,7 +443,8 @@ __global__ void k_fill_perm(int64_t n, const int32_t* __restrict__ perm, float* 
 // diagonal block of LU at (i0, i0): unit lower (upper = 0) or upper with its
 // diagonal (upper = 1).  One column per thread.
 __global__ void __launch_bounds__(kTrsmThreads) k_trsm_block(int64_t n, const float* __restrict__ LU, int64_t i0,
-                                                            int kb, float* __restrict__ X, int upper) {
+                                                            int kb, float* __restrict__ X, int upper,
+                                                            const double* __restrict__ udiag) {
   __shared__ float T[kNb][kNb + 1];
   __shared__ float xs[kNb][kTrsmThreads];
   for (int t = threadIdx.x; t < kb * kb; t += blockDim.x) T[t / kb][t % kb] = LU[(i0 + t / kb) * n + i0 + t % kb];
@@ -359,7 +459,8 @@ __global__ void __launch_bounds__(kTrsmThreads) k_trsm_block(int64_t n, const fl
     }
   } else {
     for (int j = kb - 1; j >= 0; --j) {
-      const float xj = xs[j][threadIdx.x] / T[j][j];
+      // the pivot in FP64 when the factorization kept it
+      const float xj = udiag ? (float)((double)xs[j][threadIdx.x] / udiag[i0 + j]) : xs[j][threadIdx.x] / T[j][j];
       xs[j][threadIdx.x] = xj;
       for (int i = 0; i < j; ++i) xs[i][threadIdx.x] = __fmaf_rn(-T[i][j], xj, xs[i][threadIdx.x]);
     }
@@ -370,11 +471,16 @@ __global__ void __launch_bounds__(kTrsmThreads) k_trsm_block(int64_t n, const fl
 
 }  // namespace
 
-cudaError_t dense_lu_blocked(int64_t n, float* LU, int32_t* ipiv, int* status, int tensor_cores, cudaStream_t st) {
+cudaError_t dense_lu_blocked(int64_t n, float* LU, int32_t* ipiv, double* W, double* udiag, int* status,
+                             int tensor_cores, cudaStream_t st) {
   if (tensor_cores) SDSL_CUDA_TRY((allow_max_dynamic_smem<k_gemm_sub_tc>()));
   for (int64_t k0 = 0; k0 < n; k0 += kNb) {
     const int kb = (int)std::min<int64_t>(kNb, n - k0);
-    k_lu_panel<<<1, kPanelThreads, 0, st>>>(n, k0, kb, LU, ipiv, status); count_launch();
+    if (W && udiag) {
+      k_lu_panel64<<<1, kPanelThreads, 0, st>>>(n, k0, kb, LU, W, udiag, ipiv, status); count_launch();
+    } else {
+      k_lu_panel<<<1, kPanelThreads, 0, st>>>(n, k0, kb, LU, ipiv, status); count_launch();
+    }
     SDSL_CUDA_TRY(cudaGetLastError());
     const int64_t rest = n - k0 - kb;
     if (rest <= 0) continue;
@@ -397,8 +503,8 @@ cudaError_t dense_lu_blocked(int64_t n, float* LU, int32_t* ipiv, int* status, i
 
 // X = U^{-1} L^{-1} P from the blocked LU: forward block sweep with unit L,
 // then backward with U; the block updates of the remaining rows are GEMMs.
-cudaError_t dense_inverse_blocked(int64_t n, const float* LU, const int32_t* ipiv, float* X, int32_t* perm,
-                                  int* status, int tensor_cores, cudaStream_t st) {
+cudaError_t dense_inverse_blocked(int64_t n, const float* LU, const int32_t* ipiv, const double* udiag, float* X,
+                                  int32_t* perm, int* status, int tensor_cores, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
   if (tensor_cores) SDSL_CUDA_TRY((allow_max_dynamic_smem<k_gemm_sub_tc>()));
   k_perm_identity<<<1, 32, 0, st>>>(n, ipiv, perm); count_launch();
@@ -408,7 +514,7 @@ cudaError_t dense_inverse_blocked(int64_t n, const float* LU, const int32_t* ipi
   const unsigned tgrid = (unsigned)((n + kTrsmThreads - 1) / kTrsmThreads);
   for (int64_t i0 = 0; i0 < n; i0 += kNb) {  // Y = L^{-1} P
     const int kb = (int)std::min<int64_t>(kNb, n - i0);
-    k_trsm_block<<<tgrid, kTrsmThreads, 0, st>>>(n, LU, i0, kb, X, 0); count_launch();
+    k_trsm_block<<<tgrid, kTrsmThreads, 0, st>>>(n, LU, i0, kb, X, 0, nullptr); count_launch();
     SDSL_CUDA_TRY(cudaGetLastError());
     GemmSub g;  // rows below -= L[below, I] Y_I
     g.A = LU + (i0 + kb) * n + i0;
@@ -426,7 +532,7 @@ cudaError_t dense_inverse_blocked(int64_t n, const float* LU, const int32_t* ipi
   for (int64_t b = nblk - 1; b >= 0; --b) {  // X = U^{-1} Y
     const int64_t i0 = b * kNb;
     const int kb = (int)std::min<int64_t>(kNb, n - i0);
-    k_trsm_block<<<tgrid, kTrsmThreads, 0, st>>>(n, LU, i0, kb, X, 1); count_launch();
+    k_trsm_block<<<tgrid, kTrsmThreads, 0, st>>>(n, LU, i0, kb, X, 1, udiag); count_launch();
     SDSL_CUDA_TRY(cudaGetLastError());
     GemmSub g;  // rows above -= U[above, I] X_I
     g.A = LU + i0;

@@ -315,21 +315,25 @@ cudaError_t schur_wave(int njobs, const SchurJob* jobs, int64_t b0, int64_t nb, 
                        const int64_t* pdiag, const int32_t* lev_ptr_lo, const int32_t* lev_rows_lo,
                        const int32_t* lev_ptr_up, const int32_t* lev_rows_up, double* X, double* Cpart, double* SB,
                        cudaStream_t st);
-// FP32 LU with partial pivoting of the FP64 matrix SB (status = 1 on a zero
-// pivot, 2 if a tensor-core update did not complete).  mode 0: blocked with
-// the trailing update on tensor cores, 1: blocked on CUDA cores, 2: unblocked.
-cudaError_t dense_lu_f32(int64_t n, const double* SB, float* LU, int32_t* ipiv, int* status, int mode,
-                         cudaStream_t st);
-// Blocked right-looking LU of the FP32 matrix LU in place (dense_lu.cu).
-cudaError_t dense_lu_blocked(int64_t n, float* LU, int32_t* ipiv, int* status, int tensor_cores, cudaStream_t st);
+// LU with partial pivoting of the FP64 matrix SB, stored in FP32 (status = 1
+// on a zero pivot, 2 if a tensor-core update did not complete).  mode 0:
+// blocked with the trailing update on tensor cores, 1: blocked on CUDA cores
+// (both with FP64 panels: W holds n x 64 doubles, udiag receives the n
+// pivots in FP64), 2: unblocked FP32 (W, udiag unused).
+cudaError_t dense_lu_f32(int64_t n, const double* SB, float* LU, int32_t* ipiv, double* W, double* udiag,
+                         int* status, int mode, cudaStream_t st);
+// Blocked right-looking LU of the FP32 matrix LU in place (dense_lu.cu); FP64
+// panels when W and udiag are given.
+cudaError_t dense_lu_blocked(int64_t n, float* LU, int32_t* ipiv, double* W, double* udiag, int* status,
+                             int tensor_cores, cudaStream_t st);
 // Explicit inverse from the LU factors (work: n * 32 * ceil(n / 32) floats).
 // mode 0: blocked, block updates on tensor cores; 1: blocked on CUDA cores;
 // 2: column tiles swept one row at a time.  status = 2 if a tensor-core
 // update did not complete.
-cudaError_t dense_lu_inverse(int64_t n, const float* LU, const int32_t* ipiv, float* Xinv, float* work, int mode,
-                             int* status, cudaStream_t st);
-cudaError_t dense_inverse_blocked(int64_t n, const float* LU, const int32_t* ipiv, float* X, int32_t* perm,
-                                  int* status, int tensor_cores, cudaStream_t st);
+cudaError_t dense_lu_inverse(int64_t n, const float* LU, const int32_t* ipiv, const double* udiag, float* Xinv,
+                             float* work, int mode, int* status, cudaStream_t st);
+cudaError_t dense_inverse_blocked(int64_t n, const float* LU, const int32_t* ipiv, const double* udiag, float* X,
+                                  int32_t* perm, int* status, int tensor_cores, cudaStream_t st);
 // y = U_k^{-1} L_k^{-1} y on every interior block (in place).
 cudaError_t block_lu_solve(int64_t nblocks, const int64_t* bp, const int64_t* prp, const int32_t* pci,
                            const double* F, const double* dinv, const int64_t* pdiag, const int32_t* lev_off_lo,

@@ -91,6 +91,7 @@ def load():
     L.sdsl_export_precond.argtypes = [H, _VP, _VP, _VP, _VP, _VP]
     L.sdsl_export_levels.argtypes = [H, C.c_int, _VP, _VP, _VP]
     L.sdsl_export_schur.argtypes = [H, _VP]
+    L.sdsl_export_schur_lu.argtypes = [H, _VP, _VP]
     L.sdsl_spmv.argtypes = [H, _VP, _VP]
     L.sdsl_precond_apply.argtypes = [H, _VP, _VP]
     L.sdsl_normal_spmv_noalloc.argtypes = [_I64, _I64, _I64, _VP, _VP, _VP, _VP, _VP, _VP, _VP, C.c_double,
@@ -103,7 +104,7 @@ def load():
     L.sdsl_last_error.restype = C.c_char_p
     for f in ("sdsl_setup", "sdsl_factor", "sdsl_solve", "sdsl_update_diag", "sdsl_free", "sdsl_get_stats",
               "sdsl_get_info", "sdsl_export_system", "sdsl_export_precond", "sdsl_export_levels",
-              "sdsl_export_schur", "sdsl_spmv", "sdsl_precond_apply", "sdsl_normal_spmv_noalloc"):
+              "sdsl_export_schur", "sdsl_export_schur_lu", "sdsl_spmv", "sdsl_precond_apply", "sdsl_normal_spmv_noalloc"):
         getattr(L, f).restype = C.c_int
     _lib = L
     return L
@@ -229,6 +230,14 @@ def sdsl_export_levels(h, which):
 
 def sdsl_kernel_launches() -> int:
     return int(load().sdsl_kernel_launches())
+
+
+def sdsl_export_schur_lu(h, nbord):
+    """(ipiv, pivots) of the border Schur LU (host arrays of nbord entries)."""
+    ipiv = np.zeros(max(nbord, 1), np.int32)
+    piv = np.zeros(max(nbord, 1))
+    _check(load().sdsl_export_schur_lu(h, ipiv.ctypes.data, piv.ctypes.data))
+    return ipiv[:nbord], piv[:nbord]
 
 
 def sdsl_spmv(h, x, y):

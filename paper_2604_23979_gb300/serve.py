@@ -252,12 +252,14 @@ def summarize(results: Sequence[RequestResult], max_concurrency: int = 1) -> dic
     lat = np.array([r.latency_s for r in results])
     solve_lat = np.array([s.done_s - s.start_s for r in results for s in r.solves])
     nsolves = sum(len(r.solves) for r in results)
+    nconv = sum(1 for r in results for s in r.solves if s.status == 0)
     t_first = min(r.arrival_s for r in results)
     t_last = max(r.done_s for r in results)
     span = max(t_last - t_first, 1e-9)
     return {
         "requests": len(results), "solves": nsolves, "span_s": round(span, 3),
         "solves_per_s": round(nsolves / span, 3), "requests_per_s": round(len(results) / span, 3),
+        "converged_solves": nconv, "converged_solves_per_s": round(nconv / span, 3),
         "latency_p50_s": round(float(np.percentile(lat, 50)), 4),
         "latency_p99_s": round(float(np.percentile(lat, 99)), 4),
         "solve_latency_p50_s": round(float(np.percentile(solve_lat, 50)), 4),

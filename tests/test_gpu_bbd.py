@@ -152,6 +152,31 @@ def test_bbd_border_lu_modes(schur_lu):
         sdsl.sdsl_free(h)
 
 
+@pytest.mark.parametrize("schur_lu", [0, 1])
+def test_bbd_border_lu_fp64_pivots(schur_lu):
+    """The blocked border LU chooses its pivots in FP64 and keeps them in
+    FP64: on a 300-row border of a well-conditioned KKT system (distinct
+    pivot candidates) its pivot rows equal those of the oracle's FP64 LU of
+    the oracle's S_B, and its FP64 pivots match the oracle's u_kk to the FP32
+    accuracy of the trailing updates.  (Where theta spans 16 decades, near
+    ties among candidates reorder under that rounding; there the refined
+    apply is what is compared, in test_bbd_border_lu_modes.)"""
+    p = kkt(seed=11, scale=0.01, nblocks=3, nlink=300, link_frac=0.05)
+    ref = oracle_bbd(p)
+    nb = ref["SB"].shape[0]
+    h, keep = gpu_setup(p, schur_lu=schur_lu)
+    try:
+        sdsl.sdsl_factor(h)
+        ipiv, piv = sdsl.sdsl_export_schur_lu(h, nb)
+    finally:
+        sdsl.sdsl_free(h)
+    u = np.diag(ref["lu"])
+    same = ipiv == ref["ipiv"]
+    assert same.all(), (same.mean(), int(np.argmin(same)))
+    assert rel(piv, u) <= 1e-5, rel(piv, u)
+    assert np.all(np.isfinite(piv)) and np.all(piv != 0)
+
+
 @pytest.mark.parametrize("seed", [5, 3])
 def test_bbd_gmres_matches_oracle(seed):
     p = kkt(seed=seed)
