@@ -86,7 +86,14 @@ typedef struct {
   int graph_iters;               /* Krylov iterations captured per CUDA graph launch; 0 = no graphs
                                     (BiCGSTAB captures at most 4 passes: the applies and products of
                                     passes after the converged one still run) */
-  int tune;                      /* 1 = time candidate launch shapes at factor time and keep the fastest */
+  int tune;                      /* 1 (default) = autotune: time candidate launch shapes on the handle's own
+                                    matrix -- the PCG product's form and lanes per row, the staged sweeps'
+                                    tile shape -- and keep the fastest (a candidate must beat the default by
+                                    5 %).  The choice is cached per structure (sizes of A and S, blocks,
+                                    method, precisions) for the life of the process: the first
+                                    factorization of a structure pays the timing, later ones reuse it.
+                                    Options set explicitly (spmv_form, sweep_lane_entries, sweep_far_gap)
+                                    are kept.  0 = the built-in heuristics */
   int profile;                   /* 1 = time every Krylov kernel with CUDA events (no graphs; slower) */
   int apply_prec;                /* arithmetic of the triangular solves with FP32 factors: 32 (FP32),
                                     48 (float-float: pairs of FP32 numbers with error-free products and
@@ -156,6 +163,11 @@ typedef struct {
   double ms_schur;        /* BBD: device time of the border Schur complement assembly (part of ms_factor) */
   double ms_dense_lu;     /* BBD: device time of its dense FP32 LU (part of ms_factor) */
   double ms_dense_inverse; /* BBD: device time of the explicit FP32 inverse from that LU (part of ms_factor) */
+  double ms_tune;          /* host time the autotuner spent in the last factorization (0 when its choice
+                              for this structure was already cached) */
+  int64_t sweep_shape[2];  /* staged sweeps' tile shape in use: entries per lane, far gap */
+  int64_t product_kind;    /* PCG product chosen by the autotuner: 1 explicit S, 2 factored CSR, 3 factored
+                              sliced ELL (0: not tuned) */
   int64_t iters_discarded; /* iterations of a first attempt of the last solve that did not converge under a
                               reused preconditioner and was repeated after a rebuild (0 if none); ms_solve
                               covers both attempts */
@@ -169,7 +181,7 @@ typedef struct {
 
 /* Fill *o with the defaults: BJ-PCG, normal form, tau 1e-3, delta 1e-12,
  * rho 1e-6, FP64 factors, rtol 1e-8, maxit 2000, restart 30, refactor_ratio
- * 1.5, device pointers, default stream, graph_iters 16, tune 0, profile 0,
+ * 1.5, device pointers, default stream, graph_iters 16, tune 1, profile 0,
  * apply_prec 0 (= factor_prec), flexible -1 (auto), solve_kernel 0 (auto), spmv_form 0 (auto),
  * orthog 0 (modified Gram-Schmidt). */
 void sdsl_default_options(sdsl_options* o);

@@ -7,6 +7,10 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <chrono>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <vector>
 
 #include "common.cuh"
@@ -435,41 +439,183 @@ void choose_spmv_plan(sdsl_handle h) {
   set_product_grids(h);
 }
 
-// Autotuner: time the SpMV at every lane width on the handle's own matrix
-// and keep the fastest (ties keep the smaller width).
-sdsl_status tune_spmv(sdsl_handle h) {
+// ------------------------------------------------------------- autotuner
+// Launch shapes picked by timing candidates on the handle's own matrix: the
+// PCG product (explicit S at each lane width; the factored form on CSR, each
+// half at each lane width; the factored form on the sliced ELL copies) and
+// the staged sweeps' tile shape (entries per lane, far gap).  A choice is
+// kept per structure (device, sizes of A and S, blocks, method, precisions)
+// for the life of the process, so the first factorization of a structure
+// pays the timing and later handles and rebuilds of it reuse the choice.  A
+// candidate replaces the default only when it is at least 5 % faster, so
+// close calls keep the same (default) arithmetic order.
+struct TuneKey {
+  int dev, method, fprec, aprec;
+  int64_t N, a_nnz, s_nnz, nb;
+  bool operator<(const TuneKey& o) const {
+    return std::tie(dev, method, fprec, aprec, N, a_nnz, s_nnz, nb) <
+           std::tie(o.dev, o.method, o.fprec, o.aprec, o.N, o.a_nnz, o.s_nnz, o.nb);
+  }
+};
+struct TuneChoice {
+  int product = 0;  // 0 untuned, 1 explicit S, 2 factored CSR, 3 factored sliced ELL
+  int lanes = 0, at_lanes = 0, a_lanes = 0;
+  int E = 0, gap = 0;
+  float ms = 0.f;  // time spent tuning
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, TuneChoice>& tune_cache() {
+  static std::map<TuneKey, TuneChoice> m;
+  return m;
+}
+TuneKey tune_key(sdsl_handle h, int apply) {
+  return TuneKey{h->dev, h->method, h->opt.factor_prec, apply, h->N, h->a_nnz, h->s_nnz, h->nblocks};
+}
+
+// Mean device time of one call of `launch` (after one untimed call).
+template <typename F>
+sdsl_status time_calls(sdsl_handle h, int reps, float* ms, F launch) {
+  TRY_CUDA(launch());
+  cudaEvent_t a, b;
+  TRY_CUDA(cudaEventCreate(&a));
+  TRY_CUDA(cudaEventCreate(&b));
+  cudaEventRecord(a, h->st);
+  for (int i = 0; i < reps; ++i) {
+    cudaError_t e = launch();
+    if (e != cudaSuccess) { cudaEventDestroy(a); cudaEventDestroy(b); return cuda_fail(e, "tuning launch"); }
+  }
+  cudaEventRecord(b, h->st);
+  cudaError_t e = cudaEventSynchronize(b);
+  float t = 0.f;
+  cudaEventElapsedTime(&t, a, b);
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  if (e != cudaSuccess) return cuda_fail(e, "tuning sync");
+  *ms = t / (float)reps;
+  return SDSL_OK;
+}
+
+cudaError_t product(sdsl_handle h, const double* y, double* out);
+
+// Autotuner of the PCG product (see the autotuner notes above):
+// explicit S at every lane width, the factored form on CSR (each half at
+// every lane width), the factored form on the sliced ELL copies.
+sdsl_status tune_product(sdsl_handle h) {
+  const int form = h->opt.spmv_form;
+  const bool can_factored = h->form == SDSL_FORM_NORMAL && bj_method(h);
   TRY_CUDA(cudaMemsetAsync(h->p, 0, sizeof(double) * (size_t)h->N, h->st));
-  if (h->A.factored) {
-    // the two halves of the factored product are independent choices
-    float best_at = 1e30f, best_a = 1e30f;
-    int l_at = h->A.at_lanes, l_a = h->A.a_lanes;
-    for (int l = 1; l <= 32; l <<= 1) {
-      h->A.at_lanes = l;
-      h->A.a_lanes = l;
-      set_product_grids(h);
-      float ms_at = 0.f, ms_a = 0.f;
-      TRY_CUDA(time_factored(h->A, h->p, h->q, 3, &ms_at, &ms_a, h->st));
-      if (ms_at < best_at * 0.98f) { best_at = ms_at; l_at = l; }
-      if (ms_a < best_a * 0.98f) { best_a = ms_a; l_a = l; }
+  const SpmvPlan def = h->A;
+  float def_ms = 1e30f;
+  TRY(time_calls(h, 3, &def_ms, [&]() { return product(h, h->p, h->q); }));
+  float best = def_ms;
+  SpmvPlan best_plan = def;
+  int best_kind = def.factored ? (def.sell ? 3 : 2) : 1;
+  auto consider = [&](const SpmvPlan& P, int kind) -> sdsl_status {
+    h->A = P;
+    float ms = 1e30f;
+    TRY(time_calls(h, 3, &ms, [&]() { return product(h, h->p, h->q); }));
+    if (ms < best) { best = ms; best_plan = P; best_kind = kind; }
+    return SDSL_OK;
+  };
+  if (form == 0 || form == 1) {  // explicit S
+    SpmvPlan P = def;
+    P.factored = 0;
+    P.sell = 0;
+    for (int l = 2; l <= 32; l <<= 1) {
+      P.lanes = l;
+      P.grid = one_wave(h->N, h->sms, product_occupancy(1, l));
+      TRY(consider(P, 1));
     }
-    h->A.at_lanes = l_at;
-    h->A.a_lanes = l_a;
+  }
+  if (can_factored && (form == 0 || form == 2)) {  // factored on CSR: the halves' widths independently
+    SpmvPlan P = def;
+    P.factored = 1;
+    P.sell = 0;
+    P.ncols = h->n;
+    P.a_rp = h->a_rp; P.a_ci = h->a_ci; P.a_v = h->a_v;
+    P.at_rp = h->at_rp; P.at_ci = h->at_ci; P.at_v = h->at_v;
+    P.theta = h->theta;
+    P.rho = h->opt.rho;
+    P.u = h->u;
+    float b_at = 1e30f, b_a = 1e30f;
+    int l_at = 4, l_a = 4;
+    for (int l = 2; l <= 32; l <<= 1) {
+      P.at_lanes = P.a_lanes = l;
+      P.at_grid = one_wave(h->n, h->sms, product_occupancy(2, l));
+      P.grid = one_wave(h->N, h->sms, product_occupancy(3, l));
+      float ms_at = 0.f, ms_a = 0.f;
+      TRY_CUDA(time_factored(P, h->p, h->q, 3, &ms_at, &ms_a, h->st));
+      if (ms_at < b_at) { b_at = ms_at; l_at = l; }
+      if (ms_a < b_a) { b_a = ms_a; l_a = l; }
+    }
+    P.at_lanes = l_at;
+    P.a_lanes = l_a;
+    P.at_grid = one_wave(h->n, h->sms, product_occupancy(2, l_at));
+    P.grid = one_wave(h->N, h->sms, product_occupancy(3, l_a));
+    TRY(consider(P, 2));
+  }
+  if (can_factored && h->sell_ok && (form == 0 || form == 3) && !def.sell) {
+    SpmvPlan P = def;
+    P.factored = 1;
+    P.sell = 1;
+    P.a_sell = h->a_sell;
+    P.at_sell = h->at_sell;
+    P.sell_at_grid = sell_grid_for(h->at_sell.nslices, h->sms * std::min(sell_occupancy(0), 8));
+    P.sell_a_grid = sell_grid_for(h->a_sell.nslices, h->sms * std::min(sell_occupancy(1), 8));
+    P.ncols = h->n;
+    P.a_rp = h->a_rp; P.a_ci = h->a_ci; P.a_v = h->a_v;
+    P.at_rp = h->at_rp; P.at_ci = h->at_ci; P.at_v = h->at_v;
+    P.theta = h->theta;
+    P.rho = h->opt.rho;
+    P.u = h->u;
+    TRY(consider(P, 3));
+  }
+  if (best > 0.95f * def_ms) { best_plan = def; best_kind = def.factored ? (def.sell ? 3 : 2) : 1; }
+  h->A = best_plan;
+  h->stats.tuned_spmv_lanes = best_kind == 1 ? best_plan.lanes : 0;
+  h->stats.product_kind = best_kind;
+  return SDSL_OK;
+}
+
+// The tuned product for this handle's structure: from the cache, or timed
+// now and cached.
+sdsl_status tune_spmv(sdsl_handle h) {
+  const TuneKey key = tune_key(h, h->M.apply_prec);
+  TuneChoice ch{};
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto it = tune_cache().find(key);
+    if (it != tune_cache().end()) ch = it->second;
+  }
+  if (ch.product != 0) {
+    SpmvPlan& A = h->A;
+    if (ch.product == 1) {
+      A.factored = 0;
+      A.sell = 0;
+      A.lanes = ch.lanes;
+    } else {
+      h->opt.spmv_form = ch.product;  // re-plan in that form with the tuned widths
+      choose_spmv_plan(h);
+      if (ch.product == 2) {
+        A.at_lanes = ch.at_lanes;
+        A.a_lanes = ch.a_lanes;
+      }
+    }
     set_product_grids(h);
+    h->stats.product_kind = ch.product;
     return SDSL_OK;
   }
-  float best = 1e30f;
-  int best_l = h->A.lanes;
-  SpmvPlan P = h->A;
-  for (int l = 1; l <= 32; l <<= 1) {
-    P.lanes = l;
-    P.grid = one_wave(h->N, h->sms, product_occupancy(0, l));
-    float ms = 0.f;
-    TRY_CUDA(time_spmv(P, h->p, h->q, 3, &ms, h->st));
-    if (ms < best * 0.98f) { best = ms; best_l = l; }
-  }
-  h->A.lanes = best_l;
-  set_product_grids(h);
-  h->stats.tuned_spmv_lanes = best_l;
+  auto t0 = std::chrono::steady_clock::now();
+  TRY(tune_product(h));
+  const float ms = std::chrono::duration<float, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  h->stats.ms_tune += ms;
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  TuneChoice& c = tune_cache()[key];
+  c.product = h->stats.product_kind;
+  c.lanes = h->A.lanes;
+  c.at_lanes = h->A.at_lanes;
+  c.a_lanes = h->A.a_lanes;
+  c.ms += ms;
   return SDSL_OK;
 }
 
@@ -923,14 +1069,12 @@ sdsl_status gmres_solve(sdsl_handle h) {
 // slots hold the largest tile within the shared-memory budget.
 // Returns SDSL_OK with *ok = false if the staging does not fit in shared
 // memory (the caller then uses another solve kernel).
-sdsl_status build_vtiles(sdsl_handle h, bool f32, int apply, bool* ok) {
+sdsl_status build_vtiles(sdsl_handle h, bool f32, int apply, int E, int gap, Arena& out, bool* ok) {
   TriSolve& M = h->M;
   const int64_t nb = h->nblocks;
   const int64_t nrows = h->h_bp[nb];
   const int tsz = f32 ? 4 : 8;
   const int tc = apply == 32 ? 4 : 8;
-  const int E = h->opt.sweep_lane_entries > 0 ? h->opt.sweep_lane_entries : 16;
-  const int gap = h->opt.sweep_far_gap > 0 ? h->opt.sweep_far_gap : 3;
   M.far_gap = gap;
   const int kWarps = 16;
   *ok = false;
@@ -1072,13 +1216,13 @@ sdsl_status build_vtiles(sdsl_handle h, bool f32, int apply, bool* ok) {
     int64_t *d_toff, *d_tile;
     int32_t* d_meta;
     unsigned char* stream;
-    TRY(h->pc.get(&d_trp, ntiles + 1));
-    TRY(h->pc.get(&d_rows, P.rows.size()));
-    TRY(h->pc.get(&d_logv, P.logv.size()));
-    TRY(h->pc.get(&d_toff, ntiles + 1));
-    TRY(h->pc.get(&d_tile, nb + 1));
+    TRY(out.get(&d_trp, ntiles + 1));
+    TRY(out.get(&d_rows, P.rows.size()));
+    TRY(out.get(&d_logv, P.logv.size()));
+    TRY(out.get(&d_toff, ntiles + 1));
+    TRY(out.get(&d_tile, nb + 1));
     TRY(tmp.get(&d_meta, P.meta.size()));
-    TRY(h->pc.get(&stream, P.toff.back()));
+    TRY(out.get(&stream, P.toff.back()));
     TRY(to_dev(h, d_trp, P.trp.data(), ntiles + 1));
     TRY(to_dev(h, d_rows, P.rows.data(), P.rows.size()));
     TRY(to_dev(h, d_logv, P.logv.data(), P.logv.size()));
@@ -1099,7 +1243,43 @@ sdsl_status build_vtiles(sdsl_handle h, bool f32, int apply, bool* ok) {
   return SDSL_OK;
 }
 
+// Tile shape of the staged sweeps: build each candidate's tile streams in a
+// scratch arena and time the preconditioner apply (3 calls each).
+sdsl_status tune_sweep(sdsl_handle h, bool f32, int apply, int* E_out, int* gap_out) {
+  const int E0 = h->opt.sweep_lane_entries, G0 = h->opt.sweep_far_gap;
+  std::vector<std::pair<int, int>> cand;
+  const int Es[] = {16, 12, 24, 32};
+  const int Gs[] = {3, 2, 4};
+  for (int e : Es)
+    for (int g : Gs)
+      if ((E0 == 0 || e == E0) && (G0 == 0 || g == G0)) cand.emplace_back(e, g);
+  if (cand.empty()) cand.emplace_back(E0 > 0 ? E0 : 16, G0 > 0 ? G0 : 3);
+  TRY_CUDA(cudaMemsetAsync(h->r, 0, sizeof(double) * (size_t)h->N, h->st));
+  float best = 1e30f, def = 1e30f;
+  int bE = cand[0].first, bG = cand[0].second;
+  for (size_t c = 0; c < cand.size(); ++c) {
+    Arena tmp;
+    tmp.st = h->st;
+    bool ok = false;
+    sdsl_status s = build_vtiles(h, f32, apply, cand[c].first, cand[c].second, tmp, &ok);
+    float ms = 1e30f;
+    if (s == SDSL_OK && ok)
+      s = time_calls(h, 3, &ms, [&]() {
+        return precond_apply(h->M, h->r, h->z, nullptr, h->part_blk, h->state, 2, h->st);
+      });
+    tmp.release();
+    TRY(s);
+    if (c == 0) def = ms;
+    if (ms < best) { best = ms; bE = cand[c].first; bG = cand[c].second; }
+  }
+  if (best > 0.95f * def) { bE = cand[0].first; bG = cand[0].second; }
+  *E_out = bE;
+  *gap_out = bG;
+  return SDSL_OK;
+}
+
 sdsl_status factor_impl(sdsl_handle h) {
+  h->stats.ms_tune = 0.0;
   cudaEventRecord(h->ev_a, h->st);
   h->pc.release();
   destroy_graph(h);
@@ -1312,7 +1492,32 @@ sdsl_status factor_impl(sdsl_handle h) {
   M.wait_pad = h->opt.wait_test ? 1 : 0;
   if (M.staged) {
     bool ok = false;
-    TRY(build_vtiles(h, f32, apply, &ok));
+    int E = h->opt.sweep_lane_entries > 0 ? h->opt.sweep_lane_entries : 16;
+    int gap = h->opt.sweep_far_gap > 0 ? h->opt.sweep_far_gap : 3;
+    if (h->opt.tune) {
+      const TuneKey key = tune_key(h, apply);
+      TuneChoice ch{};
+      {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        auto it = tune_cache().find(key);
+        if (it != tune_cache().end()) ch = it->second;
+      }
+      if (ch.E == 0) {
+        auto t0 = std::chrono::steady_clock::now();
+        TRY(tune_sweep(h, f32, apply, &ch.E, &ch.gap));
+        ch.ms += std::chrono::duration<float, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        h->stats.ms_tune += ch.ms;
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        TuneChoice& c = tune_cache()[key];
+        c.E = ch.E;
+        c.gap = ch.gap;
+      }
+      E = ch.E;
+      gap = ch.gap;
+    }
+    h->stats.sweep_shape[0] = E;
+    h->stats.sweep_shape[1] = gap;
+    TRY(build_vtiles(h, f32, apply, E, gap, h->pc, &ok));
     if (!ok) {
       if (h->opt.solve_kernel == 3)
         return fail(SDSL_ERR_ARG, "staged solves need blocks of at most 65,535 rows that fit in shared memory");
@@ -1595,6 +1800,7 @@ void sdsl_default_options(sdsl_options* o) {
   o->refactor_ratio = 1.5;
   o->mem_space = SDSL_MEM_DEVICE;
   o->graph_iters = 16;
+  o->tune = 1;
   o->apply_prec = 0;
   o->flexible = -1;
   o->orthog = 0;

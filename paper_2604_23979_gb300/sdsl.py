@@ -47,7 +47,8 @@ class sdsl_stats(C.Structure):
         ("kernel_ms", C.c_double * 4), ("kernel_launches", C.c_int64 * 4), ("kernel_bytes", C.c_double * 4),
         ("spmv_lanes", C.c_int64), ("solve_lanes", C.c_int64), ("tuned_spmv_lanes", C.c_int64),
         ("product_lanes", C.c_int64 * 2), ("ms_schur", C.c_double), ("ms_dense_lu", C.c_double),
-        ("ms_dense_inverse", C.c_double), ("iters_discarded", C.c_int64),
+        ("ms_dense_inverse", C.c_double), ("ms_tune", C.c_double), ("sweep_shape", C.c_int64 * 2),
+        ("product_kind", C.c_int64), ("iters_discarded", C.c_int64),
     ]
 
     def as_dict(self):
