@@ -1207,7 +1207,25 @@ sdsl_status build_vtiles(sdsl_handle h, bool f32, int apply, int E, int gap, Are
   M.max_tiles = mt;
   M.kreg = E <= 8 ? 8 : 16;
   M.max_levels = (int)maxlev;
-  M.level_wait = h->opt.sweep_wait == 1 ? 0 : 1;  // auto: per-level counters
+  M.level_wait = h->opt.sweep_wait == 1 ? 0 : 1;  // auto: per-level barriers
+  // tiles of every level, in the order of the level offsets (block, level)
+  for (int dir = 0; dir < 2; ++dir) {
+    std::vector<int32_t> lt;
+    const Plan& P = plan[dir];
+    const std::vector<int32_t>& nl = dir == 0 ? h->h_nlev_lo : h->h_nlev_up;
+    int64_t t = 0;
+    for (int64_t k = 0; k < nb; ++k) {
+      for (int32_t l = 0; l < nl[k]; ++l) {
+        int32_t c = 0;
+        while (t < P.tile_ptr[k + 1] && P.meta[3 * t] == l) { ++c; ++t; }
+        lt.push_back(std::max<int32_t>(c, 1));
+      }
+    }
+    int32_t* d_lt;
+    TRY(out.get(&d_lt, lt.size()));
+    TRY(to_dev(h, d_lt, lt.data(), lt.size()));
+    if (dir == 0) M.fwd_ltiles = d_lt; else M.bwd_ltiles = d_lt;
+  }
   for (int dir = 0; dir < 2; ++dir) {
     Plan& P = plan[dir];
     const int64_t ntiles = (int64_t)P.trp.size() - 1;

@@ -184,6 +184,8 @@ struct TriSolve {  // block triangular factors on the layout of P
   int wait_limit;       // polls after which a staged-sweep wait gives up (sets the timeout flag)
   int wait_pad;         // 1: per-level waits wait for one tile more than exists (timeout-path test)
   int far_gap;          // staged tiles: entries at least this many levels below the row are "far"
+  const int32_t* fwd_ltiles;  // staged tiles per level (forward), indexed like lev_off_lo: block b, level l
+  const int32_t* bwd_ltiles;  // at lev_off_[lo|up][b] + l (backward)
 };
 
 // Packed level-ordered triangle of one direction (dir 0 = strict lower in

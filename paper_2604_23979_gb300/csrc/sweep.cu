@@ -39,17 +39,6 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
-// Level completion counters: a release increment by the producing warp (after
-// its lanes' stores, ordered by __syncwarp) and acquire loads by the waiters.
-__device__ __forceinline__ void red_release_cta(unsigned addr) {
-  asm volatile("red.release.cta.shared::cta.add.s32 [%0], 1;" ::"r"(addr) : "memory");
-}
-__device__ __forceinline__ int ld_acquire_cta(unsigned addr) {
-  int v;
-  asm volatile("ld.acquire.cta.shared::cta.s32 %0, [%1];" : "=r"(v) : "r"(addr) : "memory");
-  return v;
-}
-
 __host__ __device__ inline size_t align128(size_t x) { return (x + 127) & ~(size_t)127; }
 
 // Sum within aligned lane groups of size V (a power of two, per lane): every
@@ -199,15 +188,45 @@ struct SweepArith<TS, TC, true> {  // float-float (TS = float)
   }
 };
 
-// Bounded wait until done[wl] >= need + pad (one broadcast acquire load per
-// poll for the whole warp).  Sets *timeout and returns when it gives up.
-__device__ __forceinline__ void wait_count(int* done, int wl, int need, int pad, unsigned backoff, int limit,
-                                           int* timeout) {
-  const unsigned addr = smem_u32(done + wl);
-  int spins = 0;
-  while (ld_acquire_cta(addr) < need + pad) {
-    if (backoff) __nanosleep(backoff);
-    if (++spins > limit) { *timeout = 1; break; }
+// Per-level completion barriers (mbarrier objects in shared memory, one per
+// level of the sweep, expecting one arrival per tile of that level).  A
+// waiting warp parks in mbarrier.try_wait, which suspends it in hardware
+// until the phase completes or a short time window passes, instead of
+// spinning: waiting warps leave the issue slots to the warps that compute.
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_inval(uint64_t* bar) {
+  asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+// One arrival with release semantics: the arriving thread's earlier writes
+// (and, through the warp's __syncwarp, its lanes' stores) are visible to a
+// thread whose wait on the completed phase returns.
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait until level `wl` is complete (every tile of it arrived: the
+// barrier's first phase).  Gives up after `limit` try_waits or about a second
+// (2^31 clocks), sets *timeout and returns.
+__device__ __forceinline__ void wait_level(uint64_t* bars, int wl, int limit, int* timeout) {
+  uint64_t* bar = bars + wl;
+  if (mbar_try_wait(bar, 0u)) return;
+  const long long deadline = clock64() + (1ll << 31);
+  for (int spins = 1;; ++spins) {
+    if (mbar_try_wait(bar, 0u)) return;
+    if (spins > limit || clock64() > deadline) { *timeout = 1; return; }
   }
 }
 
@@ -247,24 +266,23 @@ __device__ __forceinline__ void load_ready(const int (&jj)[KR], typename AR::X (
 // (sentinel until solved; an aligned store publishes value and readiness at
 // once).  Only warps w < W take tiles.  A tile's rows are at one level L.
 // Each lane first sums its "far" entries (columns at levels <= L - gap) --
-// with per-level counters (`done`) the warp first waits, with one broadcast
-// poll, until level L - gap is counted complete (a tile counts itself only
-// after its values are stored and its own level below is complete, so this
-// means every level <= L - gap is solved) -- and the lanes' far sums are
-// added into the row's leader.  Only then does the leader load its "near"
+// with per-level barriers (`done`) the warp first waits, suspended, until
+// level L - gap is complete (a tile arrives only after its values are stored
+// and its own level below is complete, so this means every level <= L - gap
+// is solved) -- and the lanes' far sums are added into the row's leader.  Only then does the leader load its "near"
 // entries (levels L - gap + 1 .. L - 1), polling the values themselves: one
 // or two per row, the only arithmetic left between a value's store and the
-// next level's.  The gap lets the counts, whose releases trail the values,
-// gate the far part without delaying it.  Readiness
+// next level's.  The gap lets the barriers, whose completions trail the
+// values, gate the far part without delaying it.  Readiness
 // is always confirmed on the values, so a value is never used before it is
-// final; the counters spare the waiting warps the value polls.
+// final; the barriers spare the waiting warps the value polls.
 template <typename TS, typename TC, bool FF, int SLOTS, int KREG, int KNEAR>
 __device__ __forceinline__ void sweep_staged(const unsigned char* __restrict__ stream, const int64_t* toff_s,
                                              int ntile, unsigned char* ring, int slot_bytes,
                                              volatile typename SweepArith<TS, TC, FF>::X* in,
                                              volatile typename SweepArith<TS, TC, FF>::X* out, bool unit,
-                                             int* timeout, int W, unsigned backoff, int* done, int limit, int pad,
-                                             int gap) {
+                                             int* timeout, int W, unsigned backoff, uint64_t* done, int limit,
+                                             int pad, int gap) {
   using AR = SweepArith<TS, TC, FF>;
   using X = typename AR::X;
   using VV = typename AR::VV;
@@ -305,7 +323,7 @@ __device__ __forceinline__ void sweep_staged(const unsigned char* __restrict__ s
     const int ne = reinterpret_cast<const int32_t*>(base)[1];
     const int level = reinterpret_cast<const int32_t*>(base)[2];
     const unsigned needs = reinterpret_cast<const uint32_t*>(base)[3];
-    const int need1 = (int)(needs & 0xFFFFu), needg = (int)(needs >> 16);
+    (void)needs;  // tiles of levels L - 1 and L - gap: the barriers carry these counts
     const uint2 rec = reinterpret_cast<const uint2*>(base + 16)[lane];  // this lane's role, one load
     const int row = (int)(rec.x & 0xFFFFu);
     const int first = (int)(rec.x >> 16);
@@ -326,7 +344,7 @@ __device__ __forceinline__ void sweep_staged(const unsigned char* __restrict__ s
     AR::init(acc, inr);
     // far entries of the lane, KREG per warp-uniform round
     const int rfar = __reduce_max_sync(0xffffffffu, (unsigned)((nfar + KREG - 1) / KREG));
-    if (done && level >= gap && rfar > 0) wait_count(done, level - gap, needg, pad, backoff, limit, timeout);
+    if (done && level >= gap && rfar > 0) wait_level(done, level - gap, limit, timeout);
     for (int c = 0; c < rfar; ++c) {
       int jj[KREG];
       VV vv[KREG];
@@ -345,8 +363,9 @@ __device__ __forceinline__ void sweep_staged(const unsigned char* __restrict__ s
     }
     AR::gather(acc, V, Vmax);
     // near entries (leader lanes), KNEAR per round; under the timeout-path
-    // test the tile first waits for a count of level L - 1 that never comes
-    if (pad && done && level >= 1) wait_count(done, level - 1, need1, pad, backoff, limit, timeout);
+    // test the tile first waits for level L - 1, whose barrier then expects
+    // one arrival more than it gets
+    if (pad && done && level >= 1) wait_level(done, level - 1, limit, timeout);
     const int near0 = first - nnear;
     const int rnear = __reduce_max_sync(0xffffffffu, (unsigned)((nnear + KNEAR - 1) / KNEAR));
     for (int c = 0; c < rnear; ++c) {
@@ -368,12 +387,12 @@ __device__ __forceinline__ void sweep_staged(const unsigned char* __restrict__ s
     if (leader) out[row] = AR::finish(acc, dvr);
     __syncwarp();  // the slot of tile k-1 is free: refill it with tile k+SLOTS-1
     if (done) {
-      // The tile counts itself in done[L] once its values are stored and
-      // level L - 1 is counted complete, so a complete done[L] means every
-      // level <= L is solved.  The next level's rows read this tile's values
-      // directly, so neither wait nor count is on their path.
-      if (level >= 1) wait_count(done, level - 1, need1, 0, backoff, limit, timeout);
-      if (lane == 0) red_release_cta(smem_u32(done + level));  // the tile's values before its count
+      // The tile arrives on level L's barrier once its values are stored and
+      // level L - 1 is complete, so a complete level L means every level
+      // <= L is solved.  The next level's rows read this tile's values
+      // directly, so neither wait nor arrival is on their path.
+      if (level >= 1) wait_level(done, level - 1, limit, timeout);
+      if (lane == 0) mbar_arrive(done + level);
     }
     issue(k + SLOTS - 1);
   }
@@ -415,11 +434,14 @@ __global__ void __launch_bounds__(kSweepWarps * 32) k_pcg_update_staged(TriSolve
   const int64_t tb0 = M.bwd_tile[b];
   const int ntb = (int)(M.bwd_tile[b + 1] - tb0);
   int64_t* toff_b = toff_f + ntf + 1;
-  int* done = M.level_wait ? reinterpret_cast<int*>(toff_f + M.max_tiles + 2) : nullptr;
+  uint64_t* done = M.level_wait ? reinterpret_cast<uint64_t*>(toff_f + M.max_tiles + 2) : nullptr;
+  const int lf0 = M.lev_off_lo[b], nlf = M.lev_off_lo[b + 1] - lf0;  // levels of this block, forward
+  const int lb0 = M.lev_off_up[b], nlb = M.lev_off_up[b + 1] - lb0;  // and backward
   for (int t = threadIdx.x; t <= ntf; t += blockDim.x) toff_f[t] = M.fwd_toff[tf0 + t];
   for (int t = threadIdx.x; t <= ntb; t += blockDim.x) toff_b[t] = M.bwd_toff[tb0 + t];
   if (done)
-    for (int t = threadIdx.x; t < M.max_levels; t += blockDim.x) done[t] = 0;
+    for (int t = threadIdx.x; t < nlf; t += blockDim.x)
+      mbar_init(done + t, (unsigned)(M.fwd_ltiles[lf0 + t] + M.wait_pad));
   if (threadIdx.x == 0) timeout = 0;
   double rr = 0.0;
   if (mode == 0) {
@@ -449,8 +471,12 @@ __global__ void __launch_bounds__(kSweepWarps * 32) k_pcg_update_staged(TriSolve
                                                done, M.wait_limit, M.wait_pad, M.far_gap);
   __syncthreads();
   for (int64_t i = threadIdx.x; i < e0 - s0; i += blockDim.x) yb[i] = S;
-  if (done)
-    for (int t = threadIdx.x; t < M.max_levels; t += blockDim.x) done[t] = 0;
+  if (done) {
+    for (int t = threadIdx.x; t < nlf; t += blockDim.x) mbar_inval(done + t);
+    __syncthreads();
+    for (int t = threadIdx.x; t < nlb; t += blockDim.x)
+      mbar_init(done + t, (unsigned)(M.bwd_ltiles[lb0 + t] + M.wait_pad));
+  }
   __syncthreads();
   sweep_staged<TS, TC, FF, SLOTS, KREG, kNear>(M.bwd_stream, toff_b, ntb, ring, M.slot_bytes, yf, yb, false,
                                                &timeout, M.sweep_warps, (unsigned)M.backoff_ns, done, M.wait_limit,
@@ -505,7 +531,7 @@ cudaError_t launch_shape(const TriSolve& M, const double* p, const double* q, do
 size_t staged_smem_bytes(int64_t max_block, size_t tc_size, int warps, int slot_bytes, int slots, int64_t max_tiles,
                          int64_t max_levels) {
   return 2 * align128((size_t)max_block * tc_size) + (size_t)warps * slots * (size_t)slot_bytes +
-         (size_t)(max_tiles + 2) * sizeof(int64_t) + (size_t)max_levels * sizeof(int);
+         (size_t)(max_tiles + 2) * sizeof(int64_t) + (size_t)max_levels * sizeof(uint64_t);
 }
 
 cudaError_t update_staged(const TriSolve& M, const double* p, const double* q, double* x, double* r, double* z,
