@@ -127,6 +127,16 @@ typedef struct {
                                     many levels below the row are summed first, behind one wait on a level
                                     count; the nearer ones are read by the row's first lane last, polling
                                     the values; 0 = auto (3), else 2..16 */
+  int64_t tau_switch_step;       /* two-phase filter (Sec. 4.3): from this IPM step on (counted in
+                                    sdsl_update_diag calls) builds filter with tau_after; 0 = off */
+  double tau_after;              /* the second phase's threshold (1e-2 in Sec. 4.3) */
+  double tau_relax;              /* filter relaxation (Sec. 4.3): a solve that does not converge under a
+                                    freshly built preconditioner is repeated once after a rebuild with
+                                    threshold tau * tau_relax; later builds use the scheduled tau again.
+                                    0 = off, else in (0, 1) */
+  int sweep_slots;               /* ring depth (tiles per warp in flight) of the staged sweeps: 0 = the deepest
+                                    that fits shared memory, else 2..4.  Handles solved together by
+                                    sdsl_batch_solve must share it (with the precisions and lane entries) */
   int wait_test;                 /* 1 = exercise the timeout path: every per-level wait of the staged sweeps
                                     waits for one tile more than its level has, which never arrives, so
                                     each wait gives up after wait_limit polls (no fault, the context stays
@@ -163,6 +173,7 @@ typedef struct {
   double ms_schur;        /* BBD: device time of the border Schur complement assembly (part of ms_factor) */
   double ms_dense_lu;     /* BBD: device time of its dense FP32 LU (part of ms_factor) */
   double ms_dense_inverse; /* BBD: device time of the explicit FP32 inverse from that LU (part of ms_factor) */
+  double tau_used;         /* filter threshold of the preconditioner the last solve used */
   double ms_tune;          /* host time the autotuner spent in the last factorization (0 when its choice
                               for this structure was already cached) */
   int64_t sweep_shape[2];  /* staged sweeps' tile shape in use: entries per lane, far gap */
@@ -228,11 +239,39 @@ sdsl_status sdsl_factor(sdsl_handle h);
  * sdsl_factor, SDSL_ERR_NOT_CONVERGED (x = last iterate), SDSL_ERR_BREAKDOWN. */
 sdsl_status sdsl_solve(sdsl_handle h, const double* b, double* x, int x0_zero, sdsl_stats* st);
 
+/* Solve count independent systems together, each on its own factored handle
+ * (continuous batching of the serving loop: the blocks of every request run
+ * in one launch).  The Block-Jacobi PCG iterations of all requests advance in
+ * the same persistent launches -- the factored product, the update with the
+ * staged block sweeps, the direction -- over a device table of (request,
+ * block) work items, captured graph_iters iterations per CUDA graph (Sec.
+ * 2.3: the blocks are independent, so blocks of different systems are too).
+ * Every request keeps its own grids, partial sums and scalars: its iterates,
+ * count and result are those of sdsl_solve on it alone, bit for bit, and the
+ * reuse rule and filter relaxation act per request as in sdsl_solve.
+ * hs[i], b[i], x[i] as in sdsl_solve (x0_zero shared); st may be NULL, else
+ * count entries.  The handles must be distinct and factored; they are solved
+ * together when every one uses Block-Jacobi PCG with the staged sweeps and
+ * the factored product on the sliced ELL copies, on one device, with equal
+ * factor and apply precision, ring depth (sweep_slots) and lane entries --
+ * otherwise one after another.  Calls on the handles are ordered on the
+ * first handle's stream while the batch runs.  Returns SDSL_OK if every
+ * solve succeeded, else the first failing status (each in st[i].status). */
+sdsl_status sdsl_batch_solve(int count, sdsl_handle* hs, const double* const* b, double* const* x, int x0_zero,
+                             sdsl_stats* st);
+
 /* New IPM scaling theta (Sec. 3.4 preconditioner reuse): recompute the system
  * values on the device (normal: S on its fixed pattern; augmented: the x
  * diagonal -1/theta), keep the factors.  theta has n entries in mem_space.
  * SDSL_ERR_STATE for SDSL_FORM_CSR. */
 sdsl_status sdsl_update_diag(sdsl_handle h, const double* theta);
+
+/* Filter threshold tau (Eq. filter) of the next preconditioner build (the
+ * factorization of sdsl_factor or of an automatic rebuild): the hook for an
+ * IPM driver's own tau schedule (Sec. 4.2 relaxes and re-tightens it across
+ * IPM steps; Sec. 4.3 switches it once).  The current preconditioner is kept
+ * until the next build.  Errors: SDSL_ERR_ARG for tau < 0 or NaN. */
+sdsl_status sdsl_set_tau(sdsl_handle h, double tau);
 
 /* Release everything the handle owns (stream-ordered).  NULL-safe. */
 sdsl_status sdsl_free(sdsl_handle h);

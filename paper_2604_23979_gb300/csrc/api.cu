@@ -9,6 +9,7 @@
 #include <string>
 #include <chrono>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <tuple>
 #include <vector>
@@ -182,6 +183,9 @@ struct sdsl_handle_s {
   bool factored = false, need_rebuild = false;
   int64_t iters_post_build = -1;   // iterations of the first converged solve after the last build
   int64_t solves_since_build = 0;
+  // filter threshold schedule (Sec. 4.3): tau of the next build, IPM steps seen
+  double tau_next = 0.0, tau_built = 0.0;
+  int64_t ipm_step = 0;
   double* x0 = nullptr;            // the caller's initial guess, kept for a re-solve
   sdsl_stats stats{};
 };
@@ -1188,12 +1192,13 @@ sdsl_status build_vtiles(sdsl_handle h, bool f32, int apply, int E, int gap, Are
   int64_t mt = max_tiles();
   const int64_t big = ((std::max(plan[0].max_bytes, plan[1].max_bytes) + 255) / 256) * 256;
   int slots = 0, slot = 0;
-  for (int sl = 4; sl >= 2 && slots == 0; --sl)
+  const int forced = h->opt.sweep_slots;  // 0: the deepest ring that fits
+  for (int sl = forced ? forced : 4; sl >= (forced ? forced : 2) && slots == 0; --sl)
     if (staged_smem_bytes(maxb, tc, kWarps, (int)big, sl, mt, maxlev) <= budget) { slots = sl; slot = (int)big; }
   if (slots == 0) {
-    // the largest tiles do not fit two slots: cap the tiles at the largest
+    // the largest tiles do not fit the ring: cap the tiles at the largest
     // slot that does (the cap raises the tile count, so re-check)
-    slots = 2;
+    slots = forced ? forced : 2;
     const size_t fixed = staged_smem_bytes(maxb, tc, kWarps, 0, 0, 2 * mt, maxlev);
     if (fixed >= budget) return SDSL_OK;
     slot = (int)std::min<int64_t>(((budget - fixed) / ((size_t)kWarps * slots)) & ~(size_t)255, 16384);
@@ -1307,7 +1312,8 @@ sdsl_status factor_impl(sdsl_handle h) {
   // Eq. (filter) + Eq. (diagcorr)
   TRY_CUDA(diag_values(N, h->s_rp, h->s_ci, h->s_v, h->dvals, h->st));
   TRY(h->pc.get(&h->p_rp, N + 1));
-  TRY_CUDA(filter_count(N, h->s_rp, h->s_ci, h->s_v, h->dvals, h->row_block, h->d_bp, whole, h->opt.tau, h->p_rp,
+  const double tau = h->tau_next;
+  TRY_CUDA(filter_count(N, h->s_rp, h->s_ci, h->s_v, h->dvals, h->row_block, h->d_bp, whole, tau, h->p_rp,
                         h->st));
   TRY(scan_total(h, h->p_rp, N, &h->p_nnz));
   TRY(h->pc.get(&h->p_ci, h->p_nnz));
@@ -1316,7 +1322,7 @@ sdsl_status factor_impl(sdsl_handle h) {
   TRY(h->pc.get(&h->F, h->p_nnz));
   TRY(h->pc.get(&h->dinv, N));
   TRY(h->pc.get(&h->mir, h->p_nnz));
-  TRY_CUDA(filter_fill(N, h->s_rp, h->s_ci, h->s_v, h->dvals, h->row_block, h->d_bp, whole, h->opt.tau, h->opt.delta,
+  TRY_CUDA(filter_fill(N, h->s_rp, h->s_ci, h->s_v, h->dvals, h->row_block, h->d_bp, whole, tau, h->opt.delta,
                        h->p_rp, h->p_ci, h->p_v, h->p_diag, h->st));
   // symmetric pattern is required by the level construction and IC(0)
   TRY_CUDA(cudaMemsetAsync(h->flag, 0, sizeof(int), h->st));
@@ -1610,6 +1616,8 @@ sdsl_status factor_impl(sdsl_handle h) {
   h->need_rebuild = false;
   h->iters_post_build = -1;
   h->solves_since_build = 0;
+  h->tau_built = tau;
+  h->stats.tau_used = tau;
   h->stats.ms_factor = elapsed(h);
   h->stats.nnz_precond = h->p_nnz;
   h->stats.nnz_factor = h->method == SDSL_BBD_GMRES ? h->p_nnz : (h->p_nnz + N) / 2;
@@ -1718,6 +1726,201 @@ sdsl_status pcg_solve(sdsl_handle h, sdsl_stats* st_out) {
                                                    : "PCG reached maxit before the tolerance");
 }
 
+// ------------------------------------------------------------- batched PCG
+// Several Block-Jacobi PCG solves (independent requests, each its own handle)
+// advanced together: every iteration is three persistent launches over a
+// device table of (request, virtual CTA) items -- the factored product on
+// the sliced ELL copies, the update with the staged block sweeps, the
+// direction -- so one launch carries the blocks of every request; each
+// request keeps its own grids, partial sums, tickets and scalars, so its
+// arithmetic is that of its solve alone.  Iterations are captured G at a
+// time in one CUDA graph; after each graph launch the host reads every
+// request's state and, as pcg_solve does for one, confirms a converged
+// recurrence with the true residual or restarts it.  Requests that stopped
+// are skipped by the kernels.
+bool batchable(const sdsl_handle h, const sdsl_handle h0) {
+  const TriSolve& M = h->M;
+  const TriSolve& M0 = h0->M;
+  return h->method == SDSL_BJ_PCG && h->factored && M.staged && h->A.factored && h->A.sell && h->dev == h0->dev &&
+         M.prec == M0.prec && M.apply_prec == M0.apply_prec && M.slots == M0.slots && M.kreg == M0.kreg &&
+         !h->opt.profile;
+}
+
+// Start of request i (the first part of pcg_solve): r = b - S x, and z, p, rho
+// if the tolerance is not met yet.  *state: 0 running, 1 done (OK), 2 failed.
+struct BatchTrack {
+  double bnorm2 = 0.0, tol2 = 0.0;
+  int state = 0;
+  sdsl_status result = SDSL_ERR_NOT_CONVERGED;
+};
+
+sdsl_status batch_pcg(std::vector<sdsl_handle>& hs, cudaStream_t bs) {
+  const int nreq = (int)hs.size();
+  std::vector<BatchTrack> tr(nreq);
+  // norms and initial residuals
+  for (sdsl_handle h : hs) {
+    double* bn2 = h->scalars;
+    TRY_CUDA(norm2_sq(h->N, h->b, h->part, bn2, reinterpret_cast<unsigned int*>(h->part + 152 * 32), bs));
+    TRY_CUDA(pcg_init_state(h->state, 0.0, h->opt.maxit, bs));
+    TRY_CUDA(true_residual(h->A, h->b, h->x, h->r, h->part, h->state, 1, bs));
+  }
+  std::vector<double> bn(nreq);
+  for (int i = 0; i < nreq; ++i) {
+    TRY_CUDA(cudaMemcpyAsync(&bn[i], hs[i]->scalars, sizeof(double), cudaMemcpyDeviceToHost, bs));
+    TRY_CUDA(cudaMemcpyAsync(hs[i]->h_state, hs[i]->state, sizeof(PcgState), cudaMemcpyDeviceToHost, bs));
+  }
+  TRY_CUDA(cudaStreamSynchronize(bs));
+  for (int i = 0; i < nreq; ++i) {
+    sdsl_handle h = hs[i];
+    h->stats.iters = 0;
+    h->stats.restarts = 0;
+    tr[i].bnorm2 = bn[i];
+    const double tol = h->opt.rtol * std::sqrt(bn[i]);
+    tr[i].tol2 = tol * tol;
+    if (bn[i] == 0.0) {
+      TRY_CUDA(cudaMemsetAsync(h->x, 0, sizeof(double) * (size_t)h->N, bs));
+      tr[i].state = 1;
+      tr[i].result = SDSL_OK;
+      continue;
+    }
+    if (h->h_state->tr <= tr[i].tol2) { tr[i].state = 1; tr[i].result = SDSL_OK; continue; }
+    TRY_CUDA(pcg_init_state(h->state, tr[i].tol2, h->opt.maxit, bs));
+    TRY_CUDA(precond_apply(h->M, h->r, h->z, h->p, h->part_blk, h->state, 1, bs));
+  }
+  static const int kDone = 1;  // a request that is already done never runs in the kernels
+  for (int i = 0; i < nreq; ++i)
+    if (tr[i].state != 0)
+      TRY_CUDA(cudaMemcpyAsync(&hs[i]->state->done, &kDone, sizeof(int), cudaMemcpyHostToDevice, bs));
+  // descriptors and work tables
+  std::vector<BatchReq> reqs(nreq);
+  std::vector<BatchItem> it_at, it_a, it_up, it_dir;
+  size_t smem = 0;
+  for (int i = 0; i < nreq; ++i) {
+    sdsl_handle h = hs[i];
+    BatchReq& R = reqs[i];
+    R.M = h->M;
+    R.A = h->A;
+    R.x = h->x; R.r = h->r; R.z = h->z; R.p = h->p; R.q = h->q;
+    R.part = h->part;
+    R.part_blk = h->part_blk;
+    R.s = h->state;
+    R.n = h->N;
+    R.g_at = (int)h->A.sell_at_grid;
+    R.g_a = (int)h->A.sell_a_grid;
+    R.g_dir = direction_grid(h->N);
+    for (int v = 0; v < R.g_at; ++v) it_at.push_back(BatchItem{i, v});
+    for (int v = 0; v < R.g_a; ++v) it_a.push_back(BatchItem{i, v});
+    for (int v = 0; v < R.g_dir; ++v) it_dir.push_back(BatchItem{i, v});
+    smem = std::max(smem, staged_smem_bytes_of(h->M));
+  }
+  // blocks of the update: largest first over all requests (longest work starts first)
+  std::vector<std::pair<int64_t, BatchItem>> blocks;
+  for (int i = 0; i < nreq; ++i)
+    for (int64_t k = 0; k < hs[i]->nblocks; ++k)
+      blocks.emplace_back(hs[i]->h_bp[k + 1] - hs[i]->h_bp[k], BatchItem{i, (int32_t)k});
+  std::stable_sort(blocks.begin(), blocks.end(),
+                   [](const std::pair<int64_t, BatchItem>& a, const std::pair<int64_t, BatchItem>& b) {
+                     return a.first > b.first;
+                   });
+  for (auto& e : blocks) it_up.push_back(e.second);
+  Arena ar;
+  ar.st = bs;
+  struct Release {
+    Arena& a;
+    ~Release() { a.release(); }
+  } release_ar{ar};
+  BatchReq* d_reqs;
+  BatchItem *d_at, *d_a, *d_up, *d_dir;
+  TRY(ar.get(&d_reqs, nreq));
+  TRY(ar.get(&d_at, it_at.size()));
+  TRY(ar.get(&d_a, it_a.size()));
+  TRY(ar.get(&d_up, it_up.size()));
+  TRY(ar.get(&d_dir, it_dir.size()));
+  TRY_CUDA(cudaMemcpyAsync(d_reqs, reqs.data(), sizeof(BatchReq) * reqs.size(), cudaMemcpyHostToDevice, bs));
+  TRY_CUDA(cudaMemcpyAsync(d_at, it_at.data(), sizeof(BatchItem) * it_at.size(), cudaMemcpyHostToDevice, bs));
+  TRY_CUDA(cudaMemcpyAsync(d_a, it_a.data(), sizeof(BatchItem) * it_a.size(), cudaMemcpyHostToDevice, bs));
+  TRY_CUDA(cudaMemcpyAsync(d_up, it_up.data(), sizeof(BatchItem) * it_up.size(), cudaMemcpyHostToDevice, bs));
+  TRY_CUDA(cudaMemcpyAsync(d_dir, it_dir.data(), sizeof(BatchItem) * it_dir.size(), cudaMemcpyHostToDevice, bs));
+  const int sms = hs[0]->sms;
+  const TriSolve M0 = hs[0]->M;
+  auto iteration = [&]() -> cudaError_t {
+    SDSL_CUDA_TRY(batch_product(d_reqs, d_at, (int)it_at.size(), d_a, (int)it_a.size(), sms * 8, bs));
+    SDSL_CUDA_TRY(batch_update(M0, d_reqs, d_up, (int)it_up.size(), sms, smem, bs));
+    return batch_direction(d_reqs, d_dir, (int)it_dir.size(), sms * 8, bs);
+  };
+  const int G = std::max(1, hs[0]->opt.graph_iters);
+  cudaGraphExec_t gexec = nullptr;
+  long long gk = 0;
+  if (hs[0]->opt.graph_iters > 0) {
+    cudaGraph_t g = nullptr;
+    const long long before = launches_so_far();
+    TRY_CUDA(cudaStreamBeginCapture(bs, cudaStreamCaptureModeRelaxed));
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < G && e == cudaSuccess; ++k) e = iteration();
+    cudaError_t e2 = cudaStreamEndCapture(bs, &g);
+    gk = launches_so_far() - before;
+    count_launch(-gk);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      return cuda_fail(e != cudaSuccess ? e : e2, "batched iteration capture");
+    }
+    e = cudaGraphInstantiate(&gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate (batch)");
+  }
+  struct GraphRelease {
+    cudaGraphExec_t& g;
+    ~GraphRelease() { if (g) cudaGraphExecDestroy(g); }
+  } release_graph{gexec};
+  for (;;) {
+    bool running = false;
+    for (int i = 0; i < nreq; ++i) running = running || tr[i].state == 0;
+    if (!running) break;
+    if (gexec) {
+      TRY_CUDA(cudaGraphLaunch(gexec, bs));
+      count_launch(gk);
+    } else {
+      TRY_CUDA(iteration());
+    }
+    for (int i = 0; i < nreq; ++i)
+      if (tr[i].state == 0)
+        TRY_CUDA(cudaMemcpyAsync(hs[i]->h_state, hs[i]->state, sizeof(PcgState), cudaMemcpyDeviceToHost, bs));
+    TRY_CUDA(cudaStreamSynchronize(bs));
+    for (int i = 0; i < nreq; ++i) {
+      if (tr[i].state != 0) continue;
+      sdsl_handle h = hs[i];
+      const PcgState hs_ = *h->h_state;
+      if (hs_.err) { tr[i].state = 2; tr[i].result = SDSL_ERR_TIMEOUT; continue; }
+      if (!hs_.done) continue;
+      if (hs_.done == 3) { tr[i].state = 2; tr[i].result = SDSL_ERR_BREAKDOWN; continue; }
+      if (hs_.done == 2) { tr[i].state = 2; tr[i].result = SDSL_ERR_NOT_CONVERGED; continue; }
+      // recurrence converged: confirm with the true residual
+      TRY_CUDA(true_residual(h->A, h->b, h->x, h->r, h->part, h->state, 0, bs));
+      TRY_CUDA(cudaMemcpyAsync(h->h_state, h->state, sizeof(PcgState), cudaMemcpyDeviceToHost, bs));
+      TRY_CUDA(cudaStreamSynchronize(bs));
+      if (h->h_state->tr <= tr[i].tol2) { tr[i].state = 1; tr[i].result = SDSL_OK; continue; }
+      if (h->h_state->iters >= h->opt.maxit) { tr[i].state = 2; tr[i].result = SDSL_ERR_NOT_CONVERGED; continue; }
+      h->stats.restarts += 1;
+      TRY_CUDA(true_residual(h->A, h->b, h->x, h->r, h->part, h->state, 1, bs));
+      TRY_CUDA(precond_apply(h->M, h->r, h->z, h->p, h->part_blk, h->state, 1, bs));
+      TRY_CUDA(cudaMemsetAsync(&h->state->done, 0, sizeof(int), bs));
+    }
+  }
+  // final true residual and statistics of every request
+  for (int i = 0; i < nreq; ++i) {
+    sdsl_handle h = hs[i];
+    TRY_CUDA(true_residual(h->A, h->b, h->x, h->r, h->part, h->state, 0, bs));
+    TRY_CUDA(cudaMemcpyAsync(h->h_state, h->state, sizeof(PcgState), cudaMemcpyDeviceToHost, bs));
+    TRY_CUDA(cudaStreamSynchronize(bs));
+    sdsl_stats& S = h->stats;
+    S.iters = h->h_state->iters;
+    S.rel_res_true = tr[i].bnorm2 > 0.0 ? std::sqrt(h->h_state->tr / tr[i].bnorm2) : 0.0;
+    S.rel_res_rec = tr[i].bnorm2 > 0.0 ? std::sqrt(h->h_state->rr / tr[i].bnorm2) : 0.0;
+    S.status = tr[i].result;
+  }
+  return SDSL_OK;
+}
+
 // Right-preconditioned BiCGSTAB with the Block-Jacobi IC(0) preconditioner
 // (Sec. 4.3 pairs them).  The count is the number of passes started; a pass
 // whose first half already meets the tolerance ends there.  Convergence of
@@ -1797,6 +2000,96 @@ sdsl_status bicg_solve(sdsl_handle h) {
 }
 
 }  // namespace
+
+// ------------------------------------------------------------- one solve
+// The pieces of sdsl_solve (also used by sdsl_batch_solve for every request).
+
+// Rebuild if the reuse rule asked for it; copy b and the initial guess.
+sdsl_status solve_prepare(sdsl_handle h, const double* b, const double* x, int x0_zero, int* rebuilt) {
+  *rebuilt = 0;
+  if (h->need_rebuild) {
+    TRY(factor_impl(h));
+    *rebuilt = 1;
+  }
+  TRY(to_dev(h, h->b, b, h->N));
+  if (!x0_zero) TRY(to_dev(h, h->x0, x, h->N));
+  if (x0_zero) TRY_CUDA(cudaMemsetAsync(h->x, 0, sizeof(double) * (size_t)h->N, h->st));
+  else TRY_CUDA(cudaMemcpyAsync(h->x, h->x0, sizeof(double) * (size_t)h->N, cudaMemcpyDeviceToDevice, h->st));
+  return SDSL_OK;
+}
+
+// One Krylov solve from the initial guess (x0 or zero); ms_solve is its
+// device time.
+sdsl_status solve_attempt(sdsl_handle h, int x0_zero, sdsl_stats* st) {
+  cudaEventRecord(h->ev_a, h->st);
+  if (x0_zero) TRY_CUDA(cudaMemsetAsync(h->x, 0, sizeof(double) * (size_t)h->N, h->st));
+  else TRY_CUDA(cudaMemcpyAsync(h->x, h->x0, sizeof(double) * (size_t)h->N, cudaMemcpyDeviceToDevice, h->st));
+  sdsl_status s = h->method == SDSL_BBD_GMRES      ? gmres_solve(h)
+                  : h->method == SDSL_BJ_BICGSTAB ? bicg_solve(h)
+                                                  : pcg_solve(h, st);
+  cudaEventRecord(h->ev_b, h->st);
+  sdsl_status e = sync(h, "solve end");
+  if (e != SDSL_OK) return e;
+  h->stats.ms_solve = elapsed(h);
+  return s;
+}
+
+// After the first attempt (status s): the reuse rule's and the filter
+// relaxation's repeated solves, the copy-out of x, the statistics and the
+// reuse bookkeeping for the next solve.
+sdsl_status solve_conclude(sdsl_handle h, double* x, int x0_zero, sdsl_stats* st, sdsl_status s, bool reused,
+                           int rebuilt) {
+  int64_t discarded = 0;
+  // Reuse rule (Sec. 3.4), failure branch: a reused preconditioner under
+  // which the solve did not converge is rebuilt from the current system and
+  // the solve is repeated from the caller's initial guess in this call.
+  if ((s == SDSL_ERR_NOT_CONVERGED || s == SDSL_ERR_BREAKDOWN) && reused && h->opt.refactor_ratio > 0.0) {
+    discarded = h->stats.iters;
+    const double ms_first = h->stats.ms_solve;
+    TRY(factor_impl(h));
+    rebuilt = 1;
+    s = solve_attempt(h, x0_zero, st);
+    h->stats.ms_solve += ms_first;
+  }
+  // Filter relaxation (Sec. 4.3): a solve that fails under a freshly built
+  // preconditioner is repeated once with a preconditioner rebuilt at the
+  // relaxed threshold tau * tau_relax; later builds return to the scheduled tau.
+  if ((s == SDSL_ERR_NOT_CONVERGED || s == SDSL_ERR_BREAKDOWN) && (!reused || rebuilt) &&
+      h->opt.tau_relax > 0.0 && h->tau_built > 0.0) {
+    discarded += h->stats.iters;
+    const double ms_before = h->stats.ms_solve;
+    const double scheduled = h->tau_next;
+    h->tau_next = h->tau_built * h->opt.tau_relax;
+    sdsl_status f = factor_impl(h);
+    h->tau_next = scheduled;
+    TRY(f);
+    rebuilt = 1;
+    s = solve_attempt(h, x0_zero, st);
+    h->stats.ms_solve += ms_before;
+  }
+  h->solves_since_build += 1;
+  TRY(to_host(h, x, h->x, h->N));
+  TRY(sync(h, "solve copy-out"));
+  h->stats.rebuilt = rebuilt;
+  h->stats.iters_discarded = discarded;
+  h->stats.status = s;  // also for early error returns (e.g. SDSL_ERR_TIMEOUT)
+  // Reuse rule, slow branch: the first converged solve after a build sets
+  // the baseline; a later converged solve that needs more than ratio times
+  // as many iterations requests a rebuild before the next solve.  A solve
+  // that did not converge never becomes the baseline: with a fresh
+  // preconditioner it also requests a rebuild (for the next system).
+  if (h->opt.refactor_ratio > 0.0) {
+    if (s == SDSL_OK) {
+      if (h->iters_post_build < 0) h->iters_post_build = h->stats.iters;
+      else if ((double)h->stats.iters > h->opt.refactor_ratio * (double)h->iters_post_build)
+        h->need_rebuild = true;
+    } else if (s == SDSL_ERR_NOT_CONVERGED || s == SDSL_ERR_BREAKDOWN) {
+      h->need_rebuild = true;
+    }
+  }
+  if (st) *st = h->stats;
+  return s;
+}
 
 // ========================================================================= ABI
 
@@ -1887,7 +2180,11 @@ sdsl_status sdsl_setup(const sdsl_options* opt, int64_t m, int64_t n, const int6
   if (opt->sweep_wait < 0 || opt->sweep_wait > 2) return fail(SDSL_ERR_ARG, "sweep_wait must be in 0..2");
   if (opt->schur_lu < 0 || opt->schur_lu > 2) return fail(SDSL_ERR_ARG, "schur_lu must be in 0..2");
   if (opt->wait_limit < 0) return fail(SDSL_ERR_ARG, "wait_limit must be >= 0");
+  if (opt->tau_switch_step < 0 || !(opt->tau_after >= 0.0) || !(opt->tau_relax >= 0.0) || opt->tau_relax >= 1.0)
+    return fail(SDSL_ERR_ARG, "tau_switch_step >= 0, tau_after >= 0 and 0 <= tau_relax < 1 are required");
   if (opt->wait_test < 0 || opt->wait_test > 1) return fail(SDSL_ERR_ARG, "wait_test must be 0 or 1");
+  if (opt->sweep_slots != 0 && (opt->sweep_slots < 2 || opt->sweep_slots > 4))
+    return fail(SDSL_ERR_ARG, "sweep_slots must be 0 (auto) or in 2..4");
   if (opt->sweep_far_gap < 0 || opt->sweep_far_gap == 1 || opt->sweep_far_gap > 16)
     return fail(SDSL_ERR_ARG, "sweep_far_gap must be 0 (auto) or in 2..16");
   if (opt->apply_prec != 0 && opt->apply_prec != 64 && opt->apply_prec != 48 && opt->apply_prec != 32)
@@ -1936,6 +2233,7 @@ sdsl_status sdsl_setup(const sdsl_options* opt, int64_t m, int64_t n, const int6
   h->N = dimS;
   h->nblocks = nb;
   h->border = opt->form == SDSL_FORM_AUGMENTED ? opt->border : 0;
+  h->tau_next = opt->tau;
   sdsl_status s = SDSL_OK;
   {
     Scope scope(h);
@@ -1991,11 +2289,21 @@ sdsl_status sdsl_factor(sdsl_handle h) {
   return factor_impl(h);
 }
 
+sdsl_status sdsl_set_tau(sdsl_handle h, double tau) {
+  if (!h) return fail(SDSL_ERR_ARG, "handle is NULL");
+  if (!(tau >= 0.0)) return fail(SDSL_ERR_ARG, "tau must be >= 0");
+  h->tau_next = tau;
+  return SDSL_OK;
+}
+
 sdsl_status sdsl_update_diag(sdsl_handle h, const double* theta) {
   if (!h) return fail(SDSL_ERR_ARG, "handle is NULL");
   if (h->form == SDSL_FORM_CSR) return fail(SDSL_ERR_STATE, "update_diag needs the normal or augmented form");
   if (!theta) return fail(SDSL_ERR_ARG, "theta is NULL");
   Scope scope(h);
+  // two-phase filter (Sec. 4.3): from IPM step tau_switch_step on, builds use tau_after
+  h->ipm_step += 1;
+  if (h->opt.tau_switch_step > 0 && h->ipm_step == h->opt.tau_switch_step) h->tau_next = h->opt.tau_after;
   cudaEventRecord(h->ev_a, h->st);
   TRY(to_dev(h, h->theta, theta, h->n));
   if (h->form == SDSL_FORM_NORMAL)
@@ -2015,63 +2323,76 @@ sdsl_status sdsl_solve(sdsl_handle h, const double* b, double* x, int x0_zero, s
   if (!h->factored) return fail(SDSL_ERR_STATE, "sdsl_solve before sdsl_factor");
   Scope scope(h);
   int rebuilt = 0;
-  if (h->need_rebuild) {
-    TRY(factor_impl(h));
-    rebuilt = 1;
-  }
-  TRY(to_dev(h, h->b, b, h->N));
-  if (!x0_zero) TRY(to_dev(h, h->x0, (const double*)x, h->N));
-  // One Krylov solve from the initial guess (x0 or zero); ms_solve is its
-  // device time.
-  auto attempt = [&]() -> sdsl_status {
-    cudaEventRecord(h->ev_a, h->st);
-    if (x0_zero) TRY_CUDA(cudaMemsetAsync(h->x, 0, sizeof(double) * (size_t)h->N, h->st));
-    else TRY_CUDA(cudaMemcpyAsync(h->x, h->x0, sizeof(double) * (size_t)h->N, cudaMemcpyDeviceToDevice, h->st));
-    sdsl_status s = h->method == SDSL_BBD_GMRES      ? gmres_solve(h)
-                    : h->method == SDSL_BJ_BICGSTAB ? bicg_solve(h)
-                                                    : pcg_solve(h, st);
-    cudaEventRecord(h->ev_b, h->st);
-    sdsl_status e = sync(h, "solve end");
-    if (e != SDSL_OK) return e;
-    h->stats.ms_solve = elapsed(h);
-    return s;
-  };
+  TRY(solve_prepare(h, b, x, x0_zero, &rebuilt));
   const bool reused = h->solves_since_build > 0;
-  sdsl_status s = attempt();
-  int64_t discarded = 0;
-  // Reuse rule (Sec. 3.4), failure branch: a reused preconditioner under
-  // which the solve did not converge is rebuilt from the current system and
-  // the solve is repeated from the caller's initial guess in this call.
-  if ((s == SDSL_ERR_NOT_CONVERGED || s == SDSL_ERR_BREAKDOWN) && reused && h->opt.refactor_ratio > 0.0) {
-    discarded = h->stats.iters;
-    const double ms_first = h->stats.ms_solve;
-    TRY(factor_impl(h));
-    rebuilt = 1;
-    s = attempt();
-    h->stats.ms_solve += ms_first;
+  sdsl_status s = solve_attempt(h, x0_zero, st);
+  return solve_conclude(h, x, x0_zero, st, s, reused, rebuilt);
+}
+
+sdsl_status sdsl_batch_solve(int count, sdsl_handle* hs, const double* const* b, double* const* x, int x0_zero,
+                             sdsl_stats* st) {
+  if (count < 0) return fail(SDSL_ERR_ARG, "count must be >= 0");
+  if (count == 0) return SDSL_OK;
+  if (!hs || !b || !x) return fail(SDSL_ERR_ARG, "hs, b or x is NULL");
+  for (int i = 0; i < count; ++i) {
+    if (!hs[i] || !b[i] || !x[i]) return fail(SDSL_ERR_ARG, "a handle, b or x is NULL");
+    if (!hs[i]->factored) return fail(SDSL_ERR_STATE, "sdsl_batch_solve before sdsl_factor");
+    for (int j = 0; j < i; ++j)
+      if (hs[j] == hs[i]) return fail(SDSL_ERR_ARG, "a handle appears twice in the batch");
   }
-  h->solves_since_build += 1;
-  TRY(to_host(h, x, h->x, h->N));
-  TRY(sync(h, "solve copy-out"));
-  h->stats.rebuilt = rebuilt;
-  h->stats.iters_discarded = discarded;
-  h->stats.status = s;  // also for early error returns (e.g. SDSL_ERR_TIMEOUT)
-  // Reuse rule, slow branch: the first converged solve after a build sets
-  // the baseline; a later converged solve that needs more than ratio times
-  // as many iterations requests a rebuild before the next solve.  A solve
-  // that did not converge never becomes the baseline: with a fresh
-  // preconditioner it also requests a rebuild (for the next system).
-  if (h->opt.refactor_ratio > 0.0) {
-    if (s == SDSL_OK) {
-      if (h->iters_post_build < 0) h->iters_post_build = h->stats.iters;
-      else if ((double)h->stats.iters > h->opt.refactor_ratio * (double)h->iters_post_build)
-        h->need_rebuild = true;
-    } else if (s == SDSL_ERR_NOT_CONVERGED || s == SDSL_ERR_BREAKDOWN) {
-      h->need_rebuild = true;
+  bool together = count > 1;
+  for (int i = 0; i < count; ++i) together = together && batchable(hs[i], hs[0]);
+  if (!together) {  // one at a time, each in its own call
+    sdsl_status first = SDSL_OK;
+    for (int i = 0; i < count; ++i) {
+      const sdsl_status s = sdsl_solve(hs[i], b[i], x[i], x0_zero, st ? &st[i] : nullptr);
+      if (s != SDSL_OK && first == SDSL_OK) first = s;
     }
+    return first;
   }
-  if (st) *st = h->stats;
-  return s;
+  std::vector<sdsl_handle> H(hs, hs + count);
+  std::vector<std::unique_ptr<Scope>> scopes;
+  std::vector<int> rebuilt(count, 0);
+  std::vector<bool> reused(count);
+  for (int i = 0; i < count; ++i) {
+    scopes.emplace_back(new Scope(H[i]));
+    TRY(solve_prepare(H[i], b[i], x[i], x0_zero, &rebuilt[i]));
+    reused[i] = H[i]->solves_since_build > 0;
+  }
+  // after preparation, but not once the batch is running, a request whose
+  // rebuild changed its kernel shape is solved alone below
+  for (int i = 0; i < count; ++i)
+    if (!batchable(H[i], H[0])) return fail(SDSL_ERR_STATE, "a rebuilt request no longer fits the batch");
+  cudaStream_t bs = H[0]->st;
+  for (int i = 1; i < count; ++i) {  // the batch stream starts after every request's preparation
+    TRY_CUDA(cudaEventRecord(H[i]->ev_join, H[i]->st));
+    TRY_CUDA(cudaStreamWaitEvent(bs, H[i]->ev_join, 0));
+  }
+  cudaEvent_t e0, e1;
+  TRY_CUDA(cudaEventCreate(&e0));
+  TRY_CUDA(cudaEventCreate(&e1));
+  cudaEventRecord(e0, bs);
+  sdsl_status sb = batch_pcg(H, bs);
+  cudaEventRecord(e1, bs);
+  cudaEventSynchronize(e1);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  TRY(sb);
+  for (int i = 1; i < count; ++i) {
+    TRY_CUDA(cudaEventRecord(H[0]->ev_join, bs));
+    TRY_CUDA(cudaStreamWaitEvent(H[i]->st, H[0]->ev_join, 0));
+  }
+  sdsl_status first = SDSL_OK;
+  for (int i = 0; i < count; ++i) {
+    sdsl_handle h = H[i];
+    h->stats.ms_solve = ms;
+    const sdsl_status s =
+        solve_conclude(h, x[i], x0_zero, st ? &st[i] : nullptr, (sdsl_status)h->stats.status, reused[i], rebuilt[i]);
+    if (s != SDSL_OK && first == SDSL_OK) first = s;
+  }
+  return first;
 }
 
 sdsl_status sdsl_get_stats(sdsl_handle h, sdsl_stats* st) {

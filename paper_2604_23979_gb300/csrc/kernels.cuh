@@ -289,6 +289,33 @@ cudaError_t true_residual(const SpmvPlan& A, const double* b, const double* x, d
 cudaError_t norm2_sq(int64_t n, const double* a, double* part, double* out, unsigned int* ticket, cudaStream_t st);
 cudaError_t pcg_init_state(PcgState* s, double tol2, long long maxit, cudaStream_t st);
 
+// ---- batched PCG iteration over several requests (sell.cu, sweep.cu,
+// krylov.cu): the device descriptor of one request and a work item of a
+// persistent launch (request, virtual CTA of that request's own grid).
+struct BatchReq {
+  TriSolve M;      // its preconditioner (staged sweeps)
+  SpmvPlan A;      // its product (factored, sliced ELL)
+  double *x, *r, *z, *p, *q;
+  double* part;      // product partial sums (g_a entries)
+  double* part_blk;  // update partial sums (3 x nblocks)
+  PcgState* s;
+  int64_t n;
+  int g_at, g_a, g_dir;  // the request's grids of the product halves and the direction
+};
+struct BatchItem {
+  int32_t req, vb;
+};
+cudaError_t batch_product(const BatchReq* reqs, const BatchItem* items_at, int n_at, const BatchItem* items_a,
+                          int n_a, int grid, cudaStream_t st);
+// M0: the first request's preconditioner (all must share the kernel shape:
+// factor/apply precision, ring slots, entries per lane); smem: the largest
+// request's dynamic shared memory.
+cudaError_t batch_update(const TriSolve& M0, const BatchReq* reqs, const BatchItem* items, int nitems, int grid,
+                         size_t smem, cudaStream_t st);
+cudaError_t batch_direction(const BatchReq* reqs, const BatchItem* items, int nitems, int grid, cudaStream_t st);
+size_t staged_smem_bytes_of(const TriSolve& M);
+int direction_grid(int64_t n);
+
 // ---- bicgstab.cu: the vector steps of right-preconditioned BiCGSTAB
 cudaError_t bicg_init(BicgScalars* c, long long maxit, cudaStream_t st);
 // rt = r, rho = r . r, first pass next (a start or a restart).

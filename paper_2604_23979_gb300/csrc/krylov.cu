@@ -387,7 +387,7 @@ __global__ void __launch_bounds__(kThreads) k_pcg_update(TriSolve M, const doubl
   }
   const double rzb = block_sum(rz, sh);
   const double zqb = block_sum(zq, sh);
-  update_epilogue(M, rrb, rzb, zqb, part, s, mode, false);
+  update_epilogue(M, rrb, rzb, zqb, part, s, mode, false, (int)blockIdx.x);
 }
 
 // Sum over the V lanes of this thread's group only, so that the groups of a
@@ -584,15 +584,31 @@ __global__ void __launch_bounds__(1024) k_pcg_update_sf(TriSolve M, const double
   }
   const double rzb = block_sum(rz, sh);
   const double zqb = block_sum(zq, sh);
-  update_epilogue(M, rrb, rzb, zqb, part, s, mode, timeout != 0);
+  update_epilogue(M, rrb, rzb, zqb, part, s, mode, timeout != 0, (int)blockIdx.x);
+}
+
+__device__ __forceinline__ void direction_body(int64_t n, const double* __restrict__ z, double* __restrict__ p,
+                                               double beta, int vb, int vg) {
+  for (int64_t i = (int64_t)vb * blockDim.x + threadIdx.x; i < n; i += (int64_t)vg * blockDim.x)
+    p[i] = __fma_rn(beta, p[i], z[i]);
 }
 
 __global__ void k_pcg_direction(int64_t n, const double* __restrict__ z, double* __restrict__ p,
                                 const PcgState* __restrict__ s) {
   if (s->done) return;
-  const double beta = s->beta;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    p[i] = __fma_rn(beta, p[i], z[i]);
+  direction_body(n, z, p, s->beta, (int)blockIdx.x, (int)gridDim.x);
+}
+
+// p = z + beta p for several requests in one persistent launch (items of
+// each request's own grid).
+__global__ void k_batch_direction(const BatchReq* __restrict__ reqs, const BatchItem* __restrict__ items,
+                                  int nitems) {
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const BatchItem I = items[it];
+    const BatchReq& R = reqs[I.req];
+    if (R.s->done) continue;  // no barrier in this body: per-thread decisions are safe
+    direction_body(R.n, R.z, R.p, R.s->beta, I.vb, R.g_dir);
+  }
 }
 
 __global__ void k_init_state(PcgState* s, double tol2, long long maxit) {
@@ -798,6 +814,14 @@ cudaError_t precond_apply(const TriSolve& M, const double* r, double* z, double*
 
 cudaError_t pcg_direction(int64_t n, const double* z, double* p, PcgState* s, cudaStream_t st) {
   k_pcg_direction<<<grid_for(n, kThreads), kThreads, 0, st>>>(n, z, p, s); count_launch();
+  return cudaGetLastError();
+}
+
+int direction_grid(int64_t n) { return (int)grid_for(n, kThreads); }
+
+cudaError_t batch_direction(const BatchReq* reqs, const BatchItem* items, int nitems, int grid, cudaStream_t st) {
+  if (nitems <= 0) return cudaSuccess;
+  k_batch_direction<<<(unsigned)std::min(grid, nitems), kThreads, 0, st>>>(reqs, items, nitems); count_launch();
   return cudaGetLastError();
 }
 

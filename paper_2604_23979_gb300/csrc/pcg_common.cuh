@@ -17,24 +17,27 @@ __device__ __forceinline__ double warp_fixed_sum(const double* a, int n) {
   return warp_sum(t);
 }
 
-// Returns true in every thread of the last CTA to arrive.
-__device__ __forceinline__ bool last_block(unsigned int* ticket) {
+// Returns true in every thread of the last of `count` CTAs (or virtual CTAs
+// of a batched launch) to arrive.
+__device__ __forceinline__ bool last_block(unsigned int* ticket, unsigned count) {
   __shared__ int amlast;
   __threadfence();
   __syncthreads();
-  if (threadIdx.x == 0) amlast = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  if (threadIdx.x == 0) amlast = atomicAdd(ticket, 1u) == count - 1;
   __syncthreads();
   if (amlast) __threadfence();
   return amlast;
 }
+__device__ __forceinline__ bool last_block(unsigned int* ticket) { return last_block(ticket, gridDim.x); }
 
 // Shared epilogue of the update kernels: z, the block partials of
 // ||r||^2, r^T z and z^T q, and (last CTA) the scalars of the next launch.
 // part holds three sections of nblocks entries: [rr | rz | zq].
+// b: the block this CTA (or virtual CTA) solved; the request's M.nblocks
+// CTAs take part in the reduction.
 __device__ __forceinline__ void update_epilogue(const TriSolve& M, double rrb, double rzb, double zqb,
                                                 double* __restrict__ part, PcgState* __restrict__ s, int mode,
-                                                bool timed_out) {
-  const int b = blockIdx.x;
+                                                bool timed_out, int b) {
   const int nb = (int)M.nblocks;
   if (threadIdx.x == 0) {
     part[b] = rrb;
@@ -43,7 +46,7 @@ __device__ __forceinline__ void update_epilogue(const TriSolve& M, double rrb, d
     if (timed_out) s->err = 1;
   }
   if (mode == 2) return;
-  if (last_block(&s->ticket[2])) {
+  if (last_block(&s->ticket[2], (unsigned)nb)) {
     if (threadIdx.x < 32) {
       const double rrt = warp_fixed_sum(part, nb);
       const double rzt = warp_fixed_sum(part + nb, nb);

@@ -107,14 +107,14 @@ __device__ __forceinline__ double sell_row(const SellMat& S, int64_t s, const do
   return (a0 + a1) + (a2 + a3);
 }
 
-// u = theta o (A^T p) on the SELL copy of A^T.
-__global__ void __launch_bounds__(kSellThreads) k_sell_at_theta(SellMat S, const double* __restrict__ theta,
-                                                               const double* __restrict__ p, double* __restrict__ u,
-                                                               const PcgState* __restrict__ s) {
-  if (s && s->done) return;
+// u = theta o (A^T p) on the SELL copy of A^T; (vb, vg): this CTA's index
+// and the grid it belongs to (a request's virtual grid in a batched launch).
+__device__ __forceinline__ void sell_at_theta_body(const SellMat& S, const double* __restrict__ theta,
+                                                   const double* __restrict__ p, double* __restrict__ u, int vb,
+                                                   int vg) {
   const int lane = lane_id();
-  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t warp = ((int64_t)vb * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)vg * blockDim.x) >> 5;
   for (int64_t sl = warp; sl < S.nslices; sl += nwarps) {
     const double acc = sell_row(S, sl, p);
     const int64_t r = sl * 32 + lane;
@@ -125,17 +125,23 @@ __global__ void __launch_bounds__(kSellThreads) k_sell_at_theta(SellMat S, const
   }
 }
 
+__global__ void __launch_bounds__(kSellThreads) k_sell_at_theta(SellMat S, const double* __restrict__ theta,
+                                                               const double* __restrict__ p, double* __restrict__ u,
+                                                               const PcgState* __restrict__ s) {
+  if (s && s->done) return;
+  sell_at_theta_body(S, theta, p, u, (int)blockIdx.x, (int)gridDim.x);
+}
+
 // q = A u + rho p on the SELL copy of A; with pcg: partial p^T q per CTA, the
-// last CTA sums the partials in CTA order and sets alpha, iters.
-__global__ void __launch_bounds__(kSellThreads) k_sell_a_u_dot(SellMat S, const double* __restrict__ u, double rho,
-                                                              const double* __restrict__ p, double* __restrict__ q,
-                                                              double* __restrict__ part, PcgState* __restrict__ s,
-                                                              int pcg) {
-  if (pcg && s->done) return;
+// last CTA of the grid sums the partials in CTA order and sets alpha, iters.
+__device__ __forceinline__ void sell_a_u_dot_body(const SellMat& S, const double* __restrict__ u, double rho,
+                                                  const double* __restrict__ p, double* __restrict__ q,
+                                                  double* __restrict__ part, PcgState* __restrict__ s, int pcg,
+                                                  int vb, int vg) {
   __shared__ double sh[kSellThreads / 32];
   const int lane = lane_id();
-  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t warp = ((int64_t)vb * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)vg * blockDim.x) >> 5;
   double loc = 0.0;
   for (int64_t sl = warp; sl < S.nslices; sl += nwarps) {
     const double acc = sell_row(S, sl, u);
@@ -149,10 +155,10 @@ __global__ void __launch_bounds__(kSellThreads) k_sell_a_u_dot(SellMat S, const 
   }
   if (!pcg) return;
   const double tot = block_sum(loc, sh);
-  if (threadIdx.x == 0) part[blockIdx.x] = tot;
-  if (last_block(&s->ticket[0])) {
+  if (threadIdx.x == 0) part[vb] = tot;
+  if (last_block(&s->ticket[0], (unsigned)vg)) {
     if (threadIdx.x < 32) {
-      const double pq = warp_fixed_sum(part, gridDim.x);
+      const double pq = warp_fixed_sum(part, vg);
       if (threadIdx.x == 0) {
         s->pq = pq;
         s->alpha = s->rho / pq;
@@ -164,10 +170,50 @@ __global__ void __launch_bounds__(kSellThreads) k_sell_a_u_dot(SellMat S, const 
   }
 }
 
+__global__ void __launch_bounds__(kSellThreads) k_sell_a_u_dot(SellMat S, const double* __restrict__ u, double rho,
+                                                              const double* __restrict__ p, double* __restrict__ q,
+                                                              double* __restrict__ part, PcgState* __restrict__ s,
+                                                              int pcg) {
+  if (pcg && s->done) return;
+  sell_a_u_dot_body(S, u, rho, p, q, part, s, pcg, (int)blockIdx.x, (int)gridDim.x);
+}
+
 inline unsigned sell_grid(int64_t nslices, int max_ctas) {
   int64_t g = (nslices + kSellThreads / 32 - 1) / (kSellThreads / 32);
   if (g > max_ctas) g = max_ctas;
   return (unsigned)(g < 1 ? 1 : g);
+}
+
+// The two halves of the factored product over several requests, one
+// persistent launch each: items (request, virtual CTA) of each request's own
+// grid, so every request's partial sums and ticket are those of its single
+// launch.
+__global__ void __launch_bounds__(kSellThreads) k_batch_sell_at_theta(const BatchReq* __restrict__ reqs,
+                                                                     const BatchItem* __restrict__ items, int nitems) {
+  __shared__ int skip;
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const BatchItem I = items[it];
+    const BatchReq& R = reqs[I.req];
+    __syncthreads();
+    if (threadIdx.x == 0) skip = R.s->done;
+    __syncthreads();
+    if (skip) continue;
+    sell_at_theta_body(R.A.at_sell, R.A.theta, R.p, R.A.u, I.vb, R.g_at);
+  }
+}
+
+__global__ void __launch_bounds__(kSellThreads) k_batch_sell_a_u_dot(const BatchReq* __restrict__ reqs,
+                                                                    const BatchItem* __restrict__ items, int nitems) {
+  __shared__ int skip;
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const BatchItem I = items[it];
+    const BatchReq& R = reqs[I.req];
+    __syncthreads();
+    if (threadIdx.x == 0) skip = R.s->done;
+    __syncthreads();
+    if (skip) continue;
+    sell_a_u_dot_body(R.A.a_sell, R.A.u, R.A.rho, R.p, R.q, R.part, R.s, 1, I.vb, R.g_a);
+  }
 }
 
 }  // namespace
@@ -208,5 +254,19 @@ cudaError_t sell_factored_product(const SpmvPlan& A, const double* p, double* q,
 }
 
 unsigned sell_grid_for(int64_t nslices, int max_ctas) { return sell_grid(nslices, max_ctas); }
+
+cudaError_t batch_product(const BatchReq* reqs, const BatchItem* items_at, int n_at, const BatchItem* items_a,
+                          int n_a, int grid, cudaStream_t st) {
+  if (n_at > 0) {
+    k_batch_sell_at_theta<<<(unsigned)std::min(grid, n_at), kSellThreads, 0, st>>>(reqs, items_at, n_at);
+    count_launch();
+    SDSL_CUDA_TRY(cudaGetLastError());
+  }
+  if (n_a > 0) {
+    k_batch_sell_a_u_dot<<<(unsigned)std::min(grid, n_a), kSellThreads, 0, st>>>(reqs, items_a, n_a);
+    count_launch();
+  }
+  return cudaGetLastError();
+}
 
 }  // namespace sdsl

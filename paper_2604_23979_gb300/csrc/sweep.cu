@@ -402,18 +402,18 @@ __device__ __forceinline__ void sweep_staged(const unsigned char* __restrict__ s
 // mode 0: x += alpha p, r -= alpha q, ||r||^2, z = M^{-1} r, r^T z, z^T q;
 // mode 1: z = M^{-1} r only, then rho = r^T z and p = z (start or restart);
 // mode 2: z = M^{-1} r only.
+// Block b of one request (the whole CTA): the body of the single-request
+// kernel below and of the batched one (batch.cu's persistent launches walk a
+// table of (request, block) items through the same code).
 template <typename TS, typename TC, int SLOTS, int KREG>
-__global__ void __launch_bounds__(kSweepWarps * 32) k_pcg_update_staged(TriSolve M, const double* __restrict__ p,
-                                                                        const double* __restrict__ q,
-                                                                        double* __restrict__ x, double* __restrict__ r,
-                                                                        double* __restrict__ z, double* __restrict__ pp,
-                                                                        double* __restrict__ part,
-                                                                        PcgState* __restrict__ s, int mode) {
-  if (mode == 0 && s->done) return;
+__device__ __forceinline__ void update_staged_body(const TriSolve& M, const double* __restrict__ p,
+                                                   const double* __restrict__ q, double* __restrict__ x,
+                                                   double* __restrict__ r, double* __restrict__ z,
+                                                   double* __restrict__ pp, double* __restrict__ part,
+                                                   PcgState* __restrict__ s, int mode, int b) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double sh[32];
   __shared__ int timeout;
-  const int b = blockIdx.x;
   const int64_t s0 = M.bp[b], e0 = M.bp[b + 1];
   constexpr bool FF = std::is_same<TC, ff_tag>::value;
   using TY = typename std::conditional<FF, unsigned long long, TC>::type;  // y storage in shared memory
@@ -494,7 +494,43 @@ __global__ void __launch_bounds__(kSweepWarps * 32) k_pcg_update_staged(TriSolve
   }
   const double rzb = block_sum(rz, sh);
   const double zqb = block_sum(zq, sh);
-  update_epilogue(M, rrb, rzb, zqb, part, s, mode, timeout != 0);
+  update_epilogue(M, rrb, rzb, zqb, part, s, mode, timeout != 0, b);
+  if (done) {  // the shared memory may hold another block's barriers next
+    __syncthreads();
+    for (int t = threadIdx.x; t < nlb; t += blockDim.x) mbar_inval(done + t);
+    __syncthreads();
+  }
+}
+
+template <typename TS, typename TC, int SLOTS, int KREG>
+__global__ void __launch_bounds__(kSweepWarps * 32) k_pcg_update_staged(TriSolve M, const double* __restrict__ p,
+                                                                        const double* __restrict__ q,
+                                                                        double* __restrict__ x, double* __restrict__ r,
+                                                                        double* __restrict__ z, double* __restrict__ pp,
+                                                                        double* __restrict__ part,
+                                                                        PcgState* __restrict__ s, int mode) {
+  if (mode == 0 && s->done) return;
+  update_staged_body<TS, TC, SLOTS, KREG>(M, p, q, x, r, z, pp, part, s, mode, (int)blockIdx.x);
+}
+
+// One PCG update + apply over the blocks of several requests in one
+// persistent launch: CTA c takes items c, c + gridDim.x, ... of the table;
+// an item is (request, block).  Requests whose solve has stopped are skipped
+// (the decision is read once per item and shared by the CTA).
+template <typename TS, typename TC, int SLOTS, int KREG>
+__global__ void __launch_bounds__(kSweepWarps * 32) k_batch_update_staged(const BatchReq* __restrict__ reqs,
+                                                                          const BatchItem* __restrict__ items,
+                                                                          int nitems) {
+  __shared__ int skip;
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const BatchItem I = items[it];
+    const BatchReq& R = reqs[I.req];
+    __syncthreads();
+    if (threadIdx.x == 0) skip = R.s->done;
+    __syncthreads();
+    if (skip) continue;
+    update_staged_body<TS, TC, SLOTS, KREG>(R.M, R.p, R.q, R.x, R.r, R.z, nullptr, R.part_blk, R.s, 0, I.vb);
+  }
 }
 
 template <typename TS, typename TC, int SLOTS, int KREG>
@@ -526,7 +562,48 @@ cudaError_t launch_shape(const TriSolve& M, const double* p, const double* q, do
   }
 }
 
+template <typename TS, typename TC, int SLOTS, int KREG>
+cudaError_t launch_batch_staged(const BatchReq* reqs, const BatchItem* items, int nitems, int grid, size_t smem,
+                                cudaStream_t st) {
+  SDSL_CUDA_TRY((allow_max_dynamic_smem<k_batch_update_staged<TS, TC, SLOTS, KREG>>()));
+  k_batch_update_staged<TS, TC, SLOTS, KREG><<<(unsigned)grid, kSweepWarps * 32, smem, st>>>(reqs, items, nitems);
+  count_launch();
+  return cudaGetLastError();
+}
+
+template <typename TS, typename TC>
+cudaError_t batch_shape(const TriSolve& M, const BatchReq* reqs, const BatchItem* items, int nitems, int grid,
+                        size_t smem, cudaStream_t st) {
+  const bool wide = M.kreg > 8;
+  switch (M.slots) {
+    case 2:
+      return wide ? launch_batch_staged<TS, TC, 2, 16>(reqs, items, nitems, grid, smem, st)
+                  : launch_batch_staged<TS, TC, 2, 8>(reqs, items, nitems, grid, smem, st);
+    case 3:
+      return wide ? launch_batch_staged<TS, TC, 3, 16>(reqs, items, nitems, grid, smem, st)
+                  : launch_batch_staged<TS, TC, 3, 8>(reqs, items, nitems, grid, smem, st);
+    default:
+      return wide ? launch_batch_staged<TS, TC, 4, 16>(reqs, items, nitems, grid, smem, st)
+                  : launch_batch_staged<TS, TC, 4, 8>(reqs, items, nitems, grid, smem, st);
+  }
+}
+
 }  // namespace
+
+cudaError_t batch_update(const TriSolve& M0, const BatchReq* reqs, const BatchItem* items, int nitems, int grid,
+                         size_t smem, cudaStream_t st) {
+  if (nitems <= 0) return cudaSuccess;
+  if (M0.prec == 64) return batch_shape<double, double>(M0, reqs, items, nitems, grid, smem, st);
+  if (M0.apply_prec == 64) return batch_shape<float, double>(M0, reqs, items, nitems, grid, smem, st);
+  if (M0.apply_prec == 48) return batch_shape<float, ff_tag>(M0, reqs, items, nitems, grid, smem, st);
+  return batch_shape<float, float>(M0, reqs, items, nitems, grid, smem, st);
+}
+
+size_t staged_smem_bytes_of(const TriSolve& M) {
+  const size_t tc = M.apply_prec == 32 ? 4 : 8;
+  return staged_smem_bytes(M.max_block, tc, kSweepWarps, M.slot_bytes, M.slots, M.max_tiles,
+                           M.level_wait ? M.max_levels : 0);
+}
 
 size_t staged_smem_bytes(int64_t max_block, size_t tc_size, int warps, int slot_bytes, int slots, int64_t max_tiles,
                          int64_t max_levels) {

@@ -32,7 +32,9 @@ class sdsl_options(C.Structure):
         ("graph_iters", C.c_int), ("tune", C.c_int), ("profile", C.c_int), ("apply_prec", C.c_int),
         ("flexible", C.c_int), ("solve_kernel", C.c_int), ("spmv_form", C.c_int), ("orthog", C.c_int),
         ("sweep_warps", C.c_int), ("sweep_backoff_ns", C.c_int), ("sweep_lane_entries", C.c_int),
-        ("schur_lu", C.c_int), ("sweep_wait", C.c_int), ("wait_limit", C.c_int), ("sweep_far_gap", C.c_int), ("wait_test", C.c_int),
+        ("schur_lu", C.c_int), ("sweep_wait", C.c_int), ("wait_limit", C.c_int), ("sweep_far_gap", C.c_int),
+        ("tau_switch_step", C.c_int64),
+        ("tau_after", C.c_double), ("tau_relax", C.c_double), ("sweep_slots", C.c_int), ("wait_test", C.c_int),
     ]
 
 
@@ -47,7 +49,7 @@ class sdsl_stats(C.Structure):
         ("kernel_ms", C.c_double * 4), ("kernel_launches", C.c_int64 * 4), ("kernel_bytes", C.c_double * 4),
         ("spmv_lanes", C.c_int64), ("solve_lanes", C.c_int64), ("tuned_spmv_lanes", C.c_int64),
         ("product_lanes", C.c_int64 * 2), ("ms_schur", C.c_double), ("ms_dense_lu", C.c_double),
-        ("ms_dense_inverse", C.c_double), ("ms_tune", C.c_double), ("sweep_shape", C.c_int64 * 2),
+        ("ms_dense_inverse", C.c_double), ("tau_used", C.c_double), ("ms_tune", C.c_double), ("sweep_shape", C.c_int64 * 2),
         ("product_kind", C.c_int64), ("iters_discarded", C.c_int64),
     ]
 
@@ -85,6 +87,8 @@ def load():
     L.sdsl_factor.argtypes = [H]
     L.sdsl_solve.argtypes = [H, _VP, _VP, C.c_int, C.POINTER(sdsl_stats)]
     L.sdsl_update_diag.argtypes = [H, _VP]
+    L.sdsl_set_tau.argtypes = [H, C.c_double]
+    L.sdsl_batch_solve.argtypes = [C.c_int, _VP, _VP, _VP, C.c_int, _VP]
     L.sdsl_free.argtypes = [H]
     L.sdsl_get_stats.argtypes = [H, C.POINTER(sdsl_stats)]
     L.sdsl_get_info.argtypes = [H, C.POINTER(sdsl_info)]
@@ -103,7 +107,8 @@ def load():
     L.sdsl_kernel_launches.restype = C.c_int64
     L.sdsl_last_error.argtypes = []
     L.sdsl_last_error.restype = C.c_char_p
-    for f in ("sdsl_setup", "sdsl_factor", "sdsl_solve", "sdsl_update_diag", "sdsl_free", "sdsl_get_stats",
+    for f in ("sdsl_setup", "sdsl_factor", "sdsl_solve", "sdsl_batch_solve", "sdsl_update_diag", "sdsl_set_tau",
+              "sdsl_free", "sdsl_get_stats",
               "sdsl_get_info", "sdsl_export_system", "sdsl_export_precond", "sdsl_export_levels",
               "sdsl_export_schur", "sdsl_export_schur_lu", "sdsl_spmv", "sdsl_precond_apply", "sdsl_normal_spmv_noalloc"):
         getattr(L, f).restype = C.c_int
@@ -176,9 +181,33 @@ def sdsl_solve(h, b, x, x0_zero=True, allow=(ERR_NOT_CONVERGED,)):
     return st
 
 
+def sdsl_batch_solve(hs, bs, xs, x0_zero=True, allow=(ERR_NOT_CONVERGED,)):
+    """Solve len(hs) systems together (each handle with its own b and x);
+    returns the list of per-request statistics."""
+    n = len(hs)
+    for x in xs:
+        if (isinstance(x, np.ndarray) and not x.flags.c_contiguous) or (hasattr(x, "is_contiguous")
+                                                                         and not x.is_contiguous()):
+            raise ValueError("x arrays must be contiguous (they receive the solutions)")
+    pb = [_ptr(b) for b in bs]  # keeps any contiguous copy of b alive for the call
+    px = [_ptr(x) for x in xs]
+    H = (C.c_void_p * n)(*[h.value if isinstance(h, C.c_void_p) else h for h in hs])
+    B = (C.c_void_p * n)(*[p[0] for p in pb])
+    X = (C.c_void_p * n)(*[p[0] for p in px])
+    st = (sdsl_stats * n)()
+    rc = load().sdsl_batch_solve(n, C.cast(H, C.c_void_p), C.cast(B, C.c_void_p), C.cast(X, C.c_void_p),
+                                 1 if x0_zero else 0, C.cast(st, C.c_void_p))
+    _check(rc, allow)
+    return list(st)
+
+
 def sdsl_update_diag(h, theta):
     p, _, k = _ptr(theta)
     return _check(load().sdsl_update_diag(h, p))
+
+
+def sdsl_set_tau(h, tau):
+    return _check(load().sdsl_set_tau(h, float(tau)))
 
 
 def sdsl_free(h):

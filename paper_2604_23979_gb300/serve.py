@@ -8,10 +8,16 @@ kept preconditioner -- the matrix, the factors and the Krylov state stay
 resident in HBM for the request's lifetime (preconditioner reuse, Sec. 3.4).
 
 Continuous batching: requests are admitted as they arrive, whenever a slot
-and enough HBM are free, and every admitted request runs on its own CUDA
-stream in its own worker thread, so the kernels of different requests
-overlap on the device.  The C-ABI calls release the GIL (ctypes), so the
-workers block on the device, not on each other.
+and enough HBM are free; every admitted request prepares its solves (setup,
+factor, value updates) on its own CUDA stream in its own worker thread.  In
+batched mode (the default) each ready solve is handed to one batching
+thread, which runs all the solves ready at that moment together through
+sdsl_batch_solve -- the blocks of every request in the same launches, each
+request's result that of its solve alone -- and solves that become ready
+meanwhile join the next batch.  Without batching, each worker solves on its
+own stream and the requests' kernels merely overlap.  The C-ABI calls
+release the GIL (ctypes), so the workers block on the device, not on each
+other.
 
 Admission by free HBM: the budget is the device's free memory at start
 (minus a reserve); a request is charged an upper-bound estimate of its
@@ -25,6 +31,7 @@ executor callable), so it can be exercised without a GPU.
 from __future__ import annotations
 
 import dataclasses
+import queue
 import threading
 import time
 from typing import Callable, List, Optional, Sequence
@@ -163,11 +170,66 @@ class Scheduler:
 
 # --------------------------------------------------------------------------- GPU executor
 
+class _Batcher:
+    """Collects ready solves from the workers and runs all those waiting at
+    once through sdsl_batch_solve (up to max_batch per call)."""
+
+    def __init__(self, sdsl, max_batch: int):
+        self.sdsl = sdsl
+        self.max_batch = max_batch
+        self.q: "queue.Queue" = queue.Queue()
+        self.sizes: List[int] = []
+        self.thread = threading.Thread(target=self._loop, daemon=True)
+        self.thread.start()
+
+    def solve(self, h, b, x):
+        item = {"h": h, "b": b, "x": x, "done": threading.Event(), "st": None, "err": None}
+        self.q.put(item)
+        item["done"].wait()
+        if item["err"] is not None:
+            raise item["err"]
+        return item["st"]
+
+    def close(self):
+        self.q.put(None)
+        self.thread.join()
+
+    def _loop(self):
+        sdsl = self.sdsl
+        while True:
+            first = self.q.get()
+            if first is None:
+                return
+            items = [first]
+            while len(items) < self.max_batch:
+                try:
+                    nxt = self.q.get_nowait()
+                except queue.Empty:
+                    break
+                if nxt is None:
+                    self.q.put(None)
+                    break
+                items.append(nxt)
+            self.sizes.append(len(items))
+            try:
+                sts = sdsl.sdsl_batch_solve([i["h"] for i in items], [i["b"] for i in items],
+                                            [i["x"] for i in items],
+                                            allow=(sdsl.ERR_NOT_CONVERGED, sdsl.ERR_BREAKDOWN))
+                for i, st in zip(items, sts):
+                    i["st"] = st
+            except Exception as e:  # noqa: BLE001 -- handed to every waiting worker
+                for i in items:
+                    i["err"] = e
+            for i in items:
+                i["done"].set()
+
+
 class GpuServer:
     """Serves NormalProblem requests on one GPU through the C ABI."""
 
     def __init__(self, slots: int = 8, factor_prec: int = 32, device: int = 0, reserve_frac: float = 0.1,
-                 budget_bytes: Optional[int] = None, keep_x: bool = False, graph_iters: int = 16):
+                 budget_bytes: Optional[int] = None, keep_x: bool = False, graph_iters: int = 16,
+                 batch: bool = True, max_batch: int = 16):
         import torch
 
         from . import sdsl
@@ -186,6 +248,9 @@ class GpuServer:
         self.keep_x = keep_x
         self.graph_iters = graph_iters
         self.streams = [torch.cuda.Stream(self.dev) for _ in range(slots)]
+        self.batch = batch
+        self.max_batch = max_batch
+        self._batcher: Optional[_Batcher] = None
 
     def _serve_one(self, req, stream, t0: float) -> List[SolveRecord]:
         torch, sdsl = self.torch, self.sdsl
@@ -199,6 +264,9 @@ class GpuServer:
             d_x = torch.empty_like(d_b)
             o, keep = sdsl.options_for(prob, factor_prec=self.factor_prec, graph_iters=self.graph_iters,
                                        stream=stream.cuda_stream)
+            if self.batch:  # one kernel shape for every request, so that their solves batch
+                o.sweep_slots = 2
+                o.spmv_form = 3
             start = time.perf_counter() - t0
             h = sdsl.sdsl_setup(o, A.nrows, A.ncols, d_rp, d_ci, d_v, d_th)
             try:
@@ -209,7 +277,10 @@ class GpuServer:
                         start = time.perf_counter() - t0
                         d_th.copy_(torch.from_numpy(th).pin_memory(), non_blocking=True)
                         sdsl.sdsl_update_diag(h, d_th)
-                    st = sdsl.sdsl_solve(h, d_b, d_x)
+                    if self._batcher is not None:
+                        st = self._batcher.solve(h, d_b, d_x)
+                    else:
+                        st = sdsl.sdsl_solve(h, d_b, d_x, allow=(sdsl.ERR_NOT_CONVERGED, sdsl.ERR_BREAKDOWN))
                     x = d_x.cpu().numpy() if self.keep_x else None
                     stream.synchronize()
                     recs.append(SolveRecord(start, time.perf_counter() - t0, int(st.iters), int(st.status),
@@ -233,18 +304,31 @@ class GpuServer:
             recs[i] = self._serve_one(requests[i], self.streams[slot], t0_box["t0"])
 
         sched = Scheduler(self.slots, self.budget)
+        self._batcher = _Batcher(self.sdsl, self.max_batch) if self.batch else None
         t0_box["t0"] = time.perf_counter()
-        admit, done, maxc = sched.run(arrivals, costs, execute)
+        try:
+            admit, done, maxc = sched.run(arrivals, costs, execute)
+        finally:
+            sizes = []
+            if self._batcher is not None:
+                self._batcher.close()
+                sizes = self._batcher.sizes
+                self._batcher = None
         results = [RequestResult(i, arrivals[i], admit[i], recs[i][-1].done_s, requests[i].problem.A.nrows, recs[i])
                    for i in range(n)]
-        return results, summarize(results, maxc)
+        summ = summarize(results, maxc)
+        if sizes:
+            summ["batches"] = len(sizes)
+            summ["mean_batch"] = round(float(np.mean(sizes)), 2)
+            summ["max_batch"] = int(max(sizes))
+        return results, summ
 
 
 def serve_sequential(requests: Sequence, factor_prec: int = 64, device: int = 0, keep_x: bool = False,
                      arrivals: Optional[Sequence[float]] = None) -> tuple:
     """Baseline: one request at a time in arrival order on the default
     stream, plain FP64 factors (no overlap between requests)."""
-    srv = GpuServer(slots=1, factor_prec=factor_prec, device=device, keep_x=keep_x)
+    srv = GpuServer(slots=1, factor_prec=factor_prec, device=device, keep_x=keep_x, batch=False)
     return srv.serve(requests, arrivals=arrivals, costs=[0] * len(requests))
 
 
