@@ -68,6 +68,9 @@ def parse():
     ap.add_argument("--rates", default="200", help="c5: comma-separated Poisson rates (requests/s) to sweep")
     ap.add_argument("--slots", type=int, default=8, help="c5: concurrent requests at most")
     ap.add_argument("--m-hi", type=int, default=500000, help="c5: largest request size m")
+    ap.add_argument("--batchers", default="0,1,2,4", help="c5: batching modes to run: 0 = no batching (each "
+                                                           "request on its own stream), k = k batches of "
+                                                           "slots/k requests")
     return ap.parse_args()
 
 
@@ -557,8 +560,17 @@ def run_c5(args, local):
     base = None
     for k, rate in enumerate(rates):
         arrivals = list(np.cumsum(np.random.default_rng(5).exponential(1.0 / rate, args.count)))
-        _, summ = serve.GpuServer(slots=args.slots, factor_prec=32).serve(reqs, arrivals=arrivals)
-        entry = {"served": summ}
+        entry = {}
+        summ = None
+        for nb in [int(v) for v in args.batchers.split(",")]:
+            srv = serve.GpuServer(slots=args.slots, factor_prec=32, batch=nb > 0, batchers=max(nb, 1),
+                                  max_batch=max(1, args.slots // max(nb, 1)))
+            _, sm = srv.serve(reqs, arrivals=arrivals)
+            entry["no_batching" if nb == 0 else f"batched_{nb}x{max(1, args.slots // nb)}"] = sm
+            if summ is None or sm["solves_per_s"] > summ["solves_per_s"]:
+                summ, best = sm, ("no_batching" if nb == 0 else f"batched_{nb}x{max(1, args.slots // nb)}")
+        entry["served"] = summ
+        entry["served_mode"] = best
         if k == len(rates) - 1:  # the sequential plain-FP64 loop once, at the highest offered load
             _, base = serve.serve_sequential(reqs, factor_prec=64, arrivals=arrivals)
             entry["sequential_fp64"] = base

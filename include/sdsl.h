@@ -39,6 +39,7 @@ extern "C" {
 #endif
 
 typedef struct sdsl_handle_s* sdsl_handle;
+typedef struct sdsl_batch_s* sdsl_batch;
 
 typedef enum {
   SDSL_OK = 0,
@@ -239,23 +240,41 @@ sdsl_status sdsl_factor(sdsl_handle h);
  * sdsl_factor, SDSL_ERR_NOT_CONVERGED (x = last iterate), SDSL_ERR_BREAKDOWN. */
 sdsl_status sdsl_solve(sdsl_handle h, const double* b, double* x, int x0_zero, sdsl_stats* st);
 
+/* Continuous batching of independent solves (the serving loop): a batch
+ * holds requests -- factored handles with their b and x -- whose Block-Jacobi
+ * PCG iterations advance together in the same persistent launches (the
+ * factored product, the update with the staged block sweeps, the direction)
+ * over a device table of (request, block) items, graph_iters iterations per
+ * CUDA graph (Sec. 2.3: the blocks are independent, so blocks of different
+ * systems are too).  Every request keeps its own grids, partial sums and
+ * scalars, so its iterates, count and result are those of sdsl_solve on it
+ * alone, bit for bit; the reuse rule and the filter relaxation act per
+ * request as in sdsl_solve.  Requests join with sdsl_batch_add and leave when
+ * their solve ends: sdsl_batch_step launches the batch until at least one
+ * request has finished (or max_graphs graph launches), then hands back up to
+ * cap finished handles (done_h) with their statistics (done_st, may be NULL)
+ * -- x holds the result on the handle's stream -- and they leave the batch;
+ * requests still running stay.  The launch tables and graph are rebuilt when
+ * the membership changes.  A handle fits a batch when it uses Block-Jacobi
+ * PCG with the staged sweeps and the factored product on the sliced ELL
+ * copies, on the batch's device, with the factor and apply precision, ring
+ * depth (sweep_slots) and lane entries of the batch's other members
+ * (SDSL_ERR_ARG otherwise).  While a handle is in a batch, make no other
+ * call on it.  One thread drives a batch; sdsl_batch_free abandons members
+ * still running (their x is not written). */
+sdsl_status sdsl_batch_create(int graph_iters, sdsl_batch* out);
+sdsl_status sdsl_batch_add(sdsl_batch batch, sdsl_handle h, const double* b, double* x, int x0_zero);
+sdsl_status sdsl_batch_step(sdsl_batch batch, int max_graphs, sdsl_handle* done_h, sdsl_stats* done_st, int cap,
+                            int* ndone);
+int sdsl_batch_size(sdsl_batch batch);
+sdsl_status sdsl_batch_free(sdsl_batch batch);
+
 /* Solve count independent systems together, each on its own factored handle
- * (continuous batching of the serving loop: the blocks of every request run
- * in one launch).  The Block-Jacobi PCG iterations of all requests advance in
- * the same persistent launches -- the factored product, the update with the
- * staged block sweeps, the direction -- over a device table of (request,
- * block) work items, captured graph_iters iterations per CUDA graph (Sec.
- * 2.3: the blocks are independent, so blocks of different systems are too).
- * Every request keeps its own grids, partial sums and scalars: its iterates,
- * count and result are those of sdsl_solve on it alone, bit for bit, and the
- * reuse rule and filter relaxation act per request as in sdsl_solve.
- * hs[i], b[i], x[i] as in sdsl_solve (x0_zero shared); st may be NULL, else
- * count entries.  The handles must be distinct and factored; they are solved
- * together when every one uses Block-Jacobi PCG with the staged sweeps and
- * the factored product on the sliced ELL copies, on one device, with equal
- * factor and apply precision, ring depth (sweep_slots) and lane entries --
- * otherwise one after another.  Calls on the handles are ordered on the
- * first handle's stream while the batch runs.  Returns SDSL_OK if every
+ * (a batch of sdsl_batch_create / _add / _step until all have finished, with
+ * the first handle's graph_iters).  hs[i], b[i], x[i] as in sdsl_solve
+ * (x0_zero shared); st may be NULL, else count entries.  The handles must be
+ * distinct and factored; they are solved together when every one fits one
+ * batch (see above), otherwise one after another.  Returns SDSL_OK if every
  * solve succeeded, else the first failing status (each in st[i].status). */
 sdsl_status sdsl_batch_solve(int count, sdsl_handle* hs, const double* const* b, double* const* x, int x0_zero,
                              sdsl_stats* st);

@@ -1746,58 +1746,95 @@ bool batchable(const sdsl_handle h, const sdsl_handle h0) {
          !h->opt.profile;
 }
 
-// Start of request i (the first part of pcg_solve): r = b - S x, and z, p, rho
-// if the tolerance is not met yet.  *state: 0 running, 1 done (OK), 2 failed.
 struct BatchTrack {
   double bnorm2 = 0.0, tol2 = 0.0;
-  int state = 0;
+  int state = 0;  // 0 running, 1 finished
   sdsl_status result = SDSL_ERR_NOT_CONVERGED;
 };
 
-sdsl_status batch_pcg(std::vector<sdsl_handle>& hs, cudaStream_t bs) {
-  const int nreq = (int)hs.size();
-  std::vector<BatchTrack> tr(nreq);
-  // norms and initial residuals
-  for (sdsl_handle h : hs) {
-    double* bn2 = h->scalars;
-    TRY_CUDA(norm2_sq(h->N, h->b, h->part, bn2, reinterpret_cast<unsigned int*>(h->part + 152 * 32), bs));
-    TRY_CUDA(pcg_init_state(h->state, 0.0, h->opt.maxit, bs));
-    TRY_CUDA(true_residual(h->A, h->b, h->x, h->r, h->part, h->state, 1, bs));
-  }
-  std::vector<double> bn(nreq);
-  for (int i = 0; i < nreq; ++i) {
-    TRY_CUDA(cudaMemcpyAsync(&bn[i], hs[i]->scalars, sizeof(double), cudaMemcpyDeviceToHost, bs));
-    TRY_CUDA(cudaMemcpyAsync(hs[i]->h_state, hs[i]->state, sizeof(PcgState), cudaMemcpyDeviceToHost, bs));
-  }
-  TRY_CUDA(cudaStreamSynchronize(bs));
-  for (int i = 0; i < nreq; ++i) {
-    sdsl_handle h = hs[i];
-    h->stats.iters = 0;
-    h->stats.restarts = 0;
-    tr[i].bnorm2 = bn[i];
-    const double tol = h->opt.rtol * std::sqrt(bn[i]);
-    tr[i].tol2 = tol * tol;
-    if (bn[i] == 0.0) {
-      TRY_CUDA(cudaMemsetAsync(h->x, 0, sizeof(double) * (size_t)h->N, bs));
-      tr[i].state = 1;
-      tr[i].result = SDSL_OK;
-      continue;
-    }
-    if (h->h_state->tr <= tr[i].tol2) { tr[i].state = 1; tr[i].result = SDSL_OK; continue; }
-    TRY_CUDA(pcg_init_state(h->state, tr[i].tol2, h->opt.maxit, bs));
-    TRY_CUDA(precond_apply(h->M, h->r, h->z, h->p, h->part_blk, h->state, 1, bs));
-  }
-  static const int kDone = 1;  // a request that is already done never runs in the kernels
-  for (int i = 0; i < nreq; ++i)
-    if (tr[i].state != 0)
-      TRY_CUDA(cudaMemcpyAsync(&hs[i]->state->done, &kDone, sizeof(int), cudaMemcpyHostToDevice, bs));
-  // descriptors and work tables
-  std::vector<BatchReq> reqs(nreq);
-  std::vector<BatchItem> it_at, it_a, it_up, it_dir;
+}  // namespace
+
+// A continuous batch: requests join (sdsl_batch_add) and leave (when their
+// solve ends, reported by sdsl_batch_step) between graph launches.
+struct sdsl_batch_s {
+  struct Member {
+    sdsl_handle h;
+    const double* b;
+    double* x;
+    int x0_zero, rebuilt;
+    bool reused;
+    BatchTrack tr;
+    cudaEvent_t t0;  // when the member joined (its solve time runs from there)
+  };
+  int dev = 0, sms = 152;
+  cudaStream_t st = nullptr;
+  std::vector<Member> members;
+  Arena ar;
+  cudaGraphExec_t graph = nullptr;
+  long long graph_kernels = 0;
+  bool dirty = true;
+  int graph_iters = 16;
+  // the launch tables of the current members
+  BatchReq* d_reqs = nullptr;
+  BatchItem *d_at = nullptr, *d_a = nullptr, *d_up = nullptr, *d_dir = nullptr;
+  int n_at = 0, n_a = 0, n_up = 0, n_dir = 0;
   size_t smem = 0;
-  for (int i = 0; i < nreq; ++i) {
-    sdsl_handle h = hs[i];
-    BatchReq& R = reqs[i];
+  TriSolve M0{};
+};
+
+namespace {
+
+// Begin a member's solve on the batch stream (the first part of pcg_solve):
+// ||b||, r = b - S x, and -- unless the tolerance is met already -- z, p, rho.
+sdsl_status batch_begin(sdsl_batch B, sdsl_batch_s::Member& mb) {
+  sdsl_handle h = mb.h;
+  const cudaStream_t bs = B->st;
+  double* bn2 = h->scalars;
+  TRY_CUDA(norm2_sq(h->N, h->b, h->part, bn2, reinterpret_cast<unsigned int*>(h->part + 152 * 32), bs));
+  TRY_CUDA(pcg_init_state(h->state, 0.0, h->opt.maxit, bs));
+  TRY_CUDA(true_residual(h->A, h->b, h->x, h->r, h->part, h->state, 1, bs));
+  double bn = 0.0;
+  TRY_CUDA(cudaMemcpyAsync(&bn, bn2, sizeof(double), cudaMemcpyDeviceToHost, bs));
+  TRY_CUDA(cudaMemcpyAsync(h->h_state, h->state, sizeof(PcgState), cudaMemcpyDeviceToHost, bs));
+  TRY_CUDA(cudaStreamSynchronize(bs));
+  h->stats.iters = 0;
+  h->stats.restarts = 0;
+  mb.tr.bnorm2 = bn;
+  const double tol = h->opt.rtol * std::sqrt(bn);
+  mb.tr.tol2 = tol * tol;
+  static const int kDone = 1;  // a finished member never runs in the kernels
+  if (bn == 0.0 || h->h_state->tr <= mb.tr.tol2) {
+    if (bn == 0.0) TRY_CUDA(cudaMemsetAsync(h->x, 0, sizeof(double) * (size_t)h->N, bs));
+    TRY_CUDA(cudaMemcpyAsync(&h->state->done, &kDone, sizeof(int), cudaMemcpyHostToDevice, bs));
+    mb.tr.state = 1;
+    mb.tr.result = SDSL_OK;
+    return SDSL_OK;
+  }
+  TRY_CUDA(pcg_init_state(h->state, mb.tr.tol2, h->opt.maxit, bs));
+  TRY_CUDA(precond_apply(h->M, h->r, h->z, h->p, h->part_blk, h->state, 1, bs));
+  return SDSL_OK;
+}
+
+// One batched PCG iteration over the current tables (three launches).
+cudaError_t batch_iteration(sdsl_batch B) {
+  SDSL_CUDA_TRY(batch_product(B->d_reqs, B->d_at, B->n_at, B->d_a, B->n_a, B->sms * 8, B->st));
+  SDSL_CUDA_TRY(batch_update(B->M0, B->d_reqs, B->d_up, B->n_up, B->sms, B->smem, B->st));
+  return batch_direction(B->d_reqs, B->d_dir, B->n_dir, B->sms * 8, B->st);
+}
+
+// The launch tables and graph of the running members.
+sdsl_status batch_plan(sdsl_batch B) {
+  if (B->graph) { cudaGraphExecDestroy(B->graph); B->graph = nullptr; }
+  B->ar.release();
+  std::vector<BatchReq> reqs;
+  std::vector<BatchItem> it_at, it_a, it_up, it_dir;
+  std::vector<std::pair<int64_t, BatchItem>> blocks;
+  B->smem = 0;
+  for (auto& mb : B->members) {
+    if (mb.tr.state != 0) continue;
+    sdsl_handle h = mb.h;
+    const int i = (int)reqs.size();
+    BatchReq R{};
     R.M = h->M;
     R.A = h->A;
     R.x = h->x; R.r = h->r; R.z = h->z; R.p = h->p; R.q = h->q;
@@ -1808,116 +1845,54 @@ sdsl_status batch_pcg(std::vector<sdsl_handle>& hs, cudaStream_t bs) {
     R.g_at = (int)h->A.sell_at_grid;
     R.g_a = (int)h->A.sell_a_grid;
     R.g_dir = direction_grid(h->N);
+    reqs.push_back(R);
     for (int v = 0; v < R.g_at; ++v) it_at.push_back(BatchItem{i, v});
     for (int v = 0; v < R.g_a; ++v) it_a.push_back(BatchItem{i, v});
     for (int v = 0; v < R.g_dir; ++v) it_dir.push_back(BatchItem{i, v});
-    smem = std::max(smem, staged_smem_bytes_of(h->M));
+    for (int64_t k = 0; k < h->nblocks; ++k)
+      blocks.emplace_back(h->h_bp[k + 1] - h->h_bp[k], BatchItem{i, (int32_t)k});
+    B->smem = std::max(B->smem, staged_smem_bytes_of(h->M));
+    B->M0 = h->M;
   }
-  // blocks of the update: largest first over all requests (longest work starts first)
-  std::vector<std::pair<int64_t, BatchItem>> blocks;
-  for (int i = 0; i < nreq; ++i)
-    for (int64_t k = 0; k < hs[i]->nblocks; ++k)
-      blocks.emplace_back(hs[i]->h_bp[k + 1] - hs[i]->h_bp[k], BatchItem{i, (int32_t)k});
+  B->dirty = false;
+  B->n_at = (int)it_at.size();
+  B->n_a = (int)it_a.size();
+  B->n_dir = (int)it_dir.size();
+  B->n_up = (int)blocks.size();
+  if (reqs.empty()) return SDSL_OK;
+  // blocks of the update: largest first over all members (longest work starts first)
   std::stable_sort(blocks.begin(), blocks.end(),
-                   [](const std::pair<int64_t, BatchItem>& a, const std::pair<int64_t, BatchItem>& b) {
-                     return a.first > b.first;
+                   [](const std::pair<int64_t, BatchItem>& x, const std::pair<int64_t, BatchItem>& y) {
+                     return x.first > y.first;
                    });
   for (auto& e : blocks) it_up.push_back(e.second);
-  Arena ar;
-  ar.st = bs;
-  struct Release {
-    Arena& a;
-    ~Release() { a.release(); }
-  } release_ar{ar};
-  BatchReq* d_reqs;
-  BatchItem *d_at, *d_a, *d_up, *d_dir;
-  TRY(ar.get(&d_reqs, nreq));
-  TRY(ar.get(&d_at, it_at.size()));
-  TRY(ar.get(&d_a, it_a.size()));
-  TRY(ar.get(&d_up, it_up.size()));
-  TRY(ar.get(&d_dir, it_dir.size()));
-  TRY_CUDA(cudaMemcpyAsync(d_reqs, reqs.data(), sizeof(BatchReq) * reqs.size(), cudaMemcpyHostToDevice, bs));
-  TRY_CUDA(cudaMemcpyAsync(d_at, it_at.data(), sizeof(BatchItem) * it_at.size(), cudaMemcpyHostToDevice, bs));
-  TRY_CUDA(cudaMemcpyAsync(d_a, it_a.data(), sizeof(BatchItem) * it_a.size(), cudaMemcpyHostToDevice, bs));
-  TRY_CUDA(cudaMemcpyAsync(d_up, it_up.data(), sizeof(BatchItem) * it_up.size(), cudaMemcpyHostToDevice, bs));
-  TRY_CUDA(cudaMemcpyAsync(d_dir, it_dir.data(), sizeof(BatchItem) * it_dir.size(), cudaMemcpyHostToDevice, bs));
-  const int sms = hs[0]->sms;
-  const TriSolve M0 = hs[0]->M;
-  auto iteration = [&]() -> cudaError_t {
-    SDSL_CUDA_TRY(batch_product(d_reqs, d_at, (int)it_at.size(), d_a, (int)it_a.size(), sms * 8, bs));
-    SDSL_CUDA_TRY(batch_update(M0, d_reqs, d_up, (int)it_up.size(), sms, smem, bs));
-    return batch_direction(d_reqs, d_dir, (int)it_dir.size(), sms * 8, bs);
-  };
-  const int G = std::max(1, hs[0]->opt.graph_iters);
-  cudaGraphExec_t gexec = nullptr;
-  long long gk = 0;
-  if (hs[0]->opt.graph_iters > 0) {
-    cudaGraph_t g = nullptr;
-    const long long before = launches_so_far();
-    TRY_CUDA(cudaStreamBeginCapture(bs, cudaStreamCaptureModeRelaxed));
-    cudaError_t e = cudaSuccess;
-    for (int k = 0; k < G && e == cudaSuccess; ++k) e = iteration();
-    cudaError_t e2 = cudaStreamEndCapture(bs, &g);
-    gk = launches_so_far() - before;
-    count_launch(-gk);
-    if (e != cudaSuccess || e2 != cudaSuccess) {
-      if (g) cudaGraphDestroy(g);
-      return cuda_fail(e != cudaSuccess ? e : e2, "batched iteration capture");
-    }
-    e = cudaGraphInstantiate(&gexec, g, 0);
-    cudaGraphDestroy(g);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate (batch)");
+  const cudaStream_t bs = B->st;
+  TRY(B->ar.get(&B->d_reqs, reqs.size()));
+  TRY(B->ar.get(&B->d_at, it_at.size()));
+  TRY(B->ar.get(&B->d_a, it_a.size()));
+  TRY(B->ar.get(&B->d_up, it_up.size()));
+  TRY(B->ar.get(&B->d_dir, it_dir.size()));
+  TRY_CUDA(cudaMemcpyAsync(B->d_reqs, reqs.data(), sizeof(BatchReq) * reqs.size(), cudaMemcpyHostToDevice, bs));
+  TRY_CUDA(cudaMemcpyAsync(B->d_at, it_at.data(), sizeof(BatchItem) * it_at.size(), cudaMemcpyHostToDevice, bs));
+  TRY_CUDA(cudaMemcpyAsync(B->d_a, it_a.data(), sizeof(BatchItem) * it_a.size(), cudaMemcpyHostToDevice, bs));
+  TRY_CUDA(cudaMemcpyAsync(B->d_up, it_up.data(), sizeof(BatchItem) * it_up.size(), cudaMemcpyHostToDevice, bs));
+  TRY_CUDA(cudaMemcpyAsync(B->d_dir, it_dir.data(), sizeof(BatchItem) * it_dir.size(), cudaMemcpyHostToDevice, bs));
+  if (B->graph_iters <= 0) return SDSL_OK;
+  cudaGraph_t g = nullptr;
+  const long long before = launches_so_far();
+  TRY_CUDA(cudaStreamBeginCapture(bs, cudaStreamCaptureModeRelaxed));
+  cudaError_t e = cudaSuccess;
+  for (int k = 0; k < B->graph_iters && e == cudaSuccess; ++k) e = batch_iteration(B);
+  cudaError_t e2 = cudaStreamEndCapture(bs, &g);
+  B->graph_kernels = launches_so_far() - before;
+  count_launch(-B->graph_kernels);  // captured, not executed: counted per graph launch
+  if (e != cudaSuccess || e2 != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return cuda_fail(e != cudaSuccess ? e : e2, "batched iteration capture");
   }
-  struct GraphRelease {
-    cudaGraphExec_t& g;
-    ~GraphRelease() { if (g) cudaGraphExecDestroy(g); }
-  } release_graph{gexec};
-  for (;;) {
-    bool running = false;
-    for (int i = 0; i < nreq; ++i) running = running || tr[i].state == 0;
-    if (!running) break;
-    if (gexec) {
-      TRY_CUDA(cudaGraphLaunch(gexec, bs));
-      count_launch(gk);
-    } else {
-      TRY_CUDA(iteration());
-    }
-    for (int i = 0; i < nreq; ++i)
-      if (tr[i].state == 0)
-        TRY_CUDA(cudaMemcpyAsync(hs[i]->h_state, hs[i]->state, sizeof(PcgState), cudaMemcpyDeviceToHost, bs));
-    TRY_CUDA(cudaStreamSynchronize(bs));
-    for (int i = 0; i < nreq; ++i) {
-      if (tr[i].state != 0) continue;
-      sdsl_handle h = hs[i];
-      const PcgState hs_ = *h->h_state;
-      if (hs_.err) { tr[i].state = 2; tr[i].result = SDSL_ERR_TIMEOUT; continue; }
-      if (!hs_.done) continue;
-      if (hs_.done == 3) { tr[i].state = 2; tr[i].result = SDSL_ERR_BREAKDOWN; continue; }
-      if (hs_.done == 2) { tr[i].state = 2; tr[i].result = SDSL_ERR_NOT_CONVERGED; continue; }
-      // recurrence converged: confirm with the true residual
-      TRY_CUDA(true_residual(h->A, h->b, h->x, h->r, h->part, h->state, 0, bs));
-      TRY_CUDA(cudaMemcpyAsync(h->h_state, h->state, sizeof(PcgState), cudaMemcpyDeviceToHost, bs));
-      TRY_CUDA(cudaStreamSynchronize(bs));
-      if (h->h_state->tr <= tr[i].tol2) { tr[i].state = 1; tr[i].result = SDSL_OK; continue; }
-      if (h->h_state->iters >= h->opt.maxit) { tr[i].state = 2; tr[i].result = SDSL_ERR_NOT_CONVERGED; continue; }
-      h->stats.restarts += 1;
-      TRY_CUDA(true_residual(h->A, h->b, h->x, h->r, h->part, h->state, 1, bs));
-      TRY_CUDA(precond_apply(h->M, h->r, h->z, h->p, h->part_blk, h->state, 1, bs));
-      TRY_CUDA(cudaMemsetAsync(&h->state->done, 0, sizeof(int), bs));
-    }
-  }
-  // final true residual and statistics of every request
-  for (int i = 0; i < nreq; ++i) {
-    sdsl_handle h = hs[i];
-    TRY_CUDA(true_residual(h->A, h->b, h->x, h->r, h->part, h->state, 0, bs));
-    TRY_CUDA(cudaMemcpyAsync(h->h_state, h->state, sizeof(PcgState), cudaMemcpyDeviceToHost, bs));
-    TRY_CUDA(cudaStreamSynchronize(bs));
-    sdsl_stats& S = h->stats;
-    S.iters = h->h_state->iters;
-    S.rel_res_true = tr[i].bnorm2 > 0.0 ? std::sqrt(h->h_state->tr / tr[i].bnorm2) : 0.0;
-    S.rel_res_rec = tr[i].bnorm2 > 0.0 ? std::sqrt(h->h_state->rr / tr[i].bnorm2) : 0.0;
-    S.status = tr[i].result;
-  }
+  e = cudaGraphInstantiate(&B->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate (batch)");
   return SDSL_OK;
 }
 
@@ -2329,6 +2304,157 @@ sdsl_status sdsl_solve(sdsl_handle h, const double* b, double* x, int x0_zero, s
   return solve_conclude(h, x, x0_zero, st, s, reused, rebuilt);
 }
 
+sdsl_status sdsl_batch_create(int graph_iters, sdsl_batch* out) {
+  if (!out) return fail(SDSL_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (graph_iters < 0) return fail(SDSL_ERR_ARG, "graph_iters must be >= 0");
+  sdsl_batch B = new sdsl_batch_s();
+  cudaGetDevice(&B->dev);
+  cudaDeviceGetAttribute(&B->sms, cudaDevAttrMultiProcessorCount, B->dev);
+  B->graph_iters = graph_iters;
+  if (cudaStreamCreateWithFlags(&B->st, cudaStreamNonBlocking) != cudaSuccess) {
+    delete B;
+    return fail(SDSL_ERR_CUDA, "stream creation failed");
+  }
+  B->ar.st = B->st;
+  *out = B;
+  return SDSL_OK;
+}
+
+int sdsl_batch_size(sdsl_batch B) { return B ? (int)B->members.size() : 0; }
+
+sdsl_status sdsl_batch_add(sdsl_batch B, sdsl_handle h, const double* b, double* x, int x0_zero) {
+  if (!B || !h || !b || !x) return fail(SDSL_ERR_ARG, "NULL argument");
+  if (!h->factored) return fail(SDSL_ERR_STATE, "sdsl_batch_add before sdsl_factor");
+  for (auto& mb : B->members)
+    if (mb.h == h) return fail(SDSL_ERR_ARG, "the handle is already in the batch");
+  sdsl_handle h0 = B->members.empty() ? h : B->members.front().h;
+  if (!batchable(h, h0) || h->dev != B->dev)
+    return fail(SDSL_ERR_ARG, "the handle does not fit the batch's kernel shape");
+  cudaEventRecord(h->ev_join, h->user);  // after the caller's earlier work on its stream
+  cudaStreamWaitEvent(h->st, h->ev_join, 0);
+  sdsl_batch_s::Member mb{};
+  mb.h = h;
+  mb.b = b;
+  mb.x = x;
+  mb.x0_zero = x0_zero;
+  TRY(solve_prepare(h, b, x, x0_zero, &mb.rebuilt));
+  mb.reused = h->solves_since_build > 0;
+  if (!batchable(h, h0)) return fail(SDSL_ERR_STATE, "a rebuild changed the handle's kernel shape");
+  TRY_CUDA(cudaEventRecord(h->ev_join, h->st));
+  TRY_CUDA(cudaStreamWaitEvent(B->st, h->ev_join, 0));
+  TRY_CUDA(cudaEventCreate(&mb.t0));
+  cudaEventRecord(mb.t0, B->st);
+  sdsl_status s = batch_begin(B, mb);
+  if (s != SDSL_OK) {
+    cudaEventDestroy(mb.t0);
+    return s;
+  }
+  B->members.push_back(mb);
+  B->dirty = true;
+  return SDSL_OK;
+}
+
+sdsl_status sdsl_batch_step(sdsl_batch B, int max_graphs, sdsl_handle* done_h, sdsl_stats* done_st, int cap,
+                            int* ndone) {
+  if (!B || !ndone || (cap > 0 && !done_h)) return fail(SDSL_ERR_ARG, "NULL argument");
+  *ndone = 0;
+  if (B->members.empty()) return SDSL_OK;
+  const cudaStream_t bs = B->st;
+  auto running = [&]() {
+    for (auto& mb : B->members)
+      if (mb.tr.state == 0) return true;
+    return false;
+  };
+  auto any_finished = [&]() {
+    for (auto& mb : B->members)
+      if (mb.tr.state != 0) return true;
+    return false;
+  };
+  for (int g = 0; g < std::max(1, max_graphs) && running() && !any_finished(); ++g) {
+    if (B->dirty) TRY(batch_plan(B));
+    if (B->graph) {
+      TRY_CUDA(cudaGraphLaunch(B->graph, bs));
+      count_launch(B->graph_kernels);
+    } else {
+      for (int k = 0; k < 8; ++k) TRY_CUDA(batch_iteration(B));
+    }
+    for (auto& mb : B->members)
+      if (mb.tr.state == 0)
+        TRY_CUDA(cudaMemcpyAsync(mb.h->h_state, mb.h->state, sizeof(PcgState), cudaMemcpyDeviceToHost, bs));
+    TRY_CUDA(cudaStreamSynchronize(bs));
+    for (auto& mb : B->members) {
+      if (mb.tr.state != 0) continue;
+      sdsl_handle h = mb.h;
+      const PcgState hs_ = *h->h_state;
+      BatchTrack& tr = mb.tr;
+      if (hs_.err) { tr.state = 1; tr.result = SDSL_ERR_TIMEOUT; continue; }
+      if (!hs_.done) continue;
+      if (hs_.done == 3) { tr.state = 1; tr.result = SDSL_ERR_BREAKDOWN; continue; }
+      if (hs_.done == 2) { tr.state = 1; tr.result = SDSL_ERR_NOT_CONVERGED; continue; }
+      // recurrence converged: confirm with the true residual, or restart
+      TRY_CUDA(true_residual(h->A, h->b, h->x, h->r, h->part, h->state, 0, bs));
+      TRY_CUDA(cudaMemcpyAsync(h->h_state, h->state, sizeof(PcgState), cudaMemcpyDeviceToHost, bs));
+      TRY_CUDA(cudaStreamSynchronize(bs));
+      if (h->h_state->tr <= tr.tol2) { tr.state = 1; tr.result = SDSL_OK; continue; }
+      if (h->h_state->iters >= h->opt.maxit) { tr.state = 1; tr.result = SDSL_ERR_NOT_CONVERGED; continue; }
+      h->stats.restarts += 1;
+      TRY_CUDA(true_residual(h->A, h->b, h->x, h->r, h->part, h->state, 1, bs));
+      TRY_CUDA(precond_apply(h->M, h->r, h->z, h->p, h->part_blk, h->state, 1, bs));
+      TRY_CUDA(cudaMemsetAsync(&h->state->done, 0, sizeof(int), bs));
+    }
+  }
+  // report finished members (up to cap): statistics, the reuse rule's and
+  // relaxation's repeats on the member's own stream, x copied out
+  std::vector<sdsl_batch_s::Member> keep;
+  for (auto& mb : B->members) {
+    if (mb.tr.state == 0 || *ndone >= cap) {
+      keep.push_back(mb);
+      continue;
+    }
+    sdsl_handle h = mb.h;
+    TRY_CUDA(true_residual(h->A, h->b, h->x, h->r, h->part, h->state, 0, bs));  // final FP64 true residual
+    TRY_CUDA(cudaMemcpyAsync(h->h_state, h->state, sizeof(PcgState), cudaMemcpyDeviceToHost, bs));
+    cudaEvent_t t1;
+    TRY_CUDA(cudaEventCreate(&t1));
+    cudaEventRecord(t1, bs);
+    TRY_CUDA(cudaStreamSynchronize(bs));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, mb.t0, t1);
+    cudaEventDestroy(t1);
+    cudaEventDestroy(mb.t0);
+    sdsl_stats& S = h->stats;
+    S.iters = h->h_state->iters;
+    S.rel_res_true = mb.tr.bnorm2 > 0.0 ? std::sqrt(h->h_state->tr / mb.tr.bnorm2) : 0.0;
+    S.rel_res_rec = mb.tr.bnorm2 > 0.0 ? std::sqrt(h->h_state->rr / mb.tr.bnorm2) : 0.0;
+    S.status = mb.tr.result;
+    S.ms_solve = ms;
+    TRY_CUDA(cudaEventRecord(h->ev_join, bs));
+    TRY_CUDA(cudaStreamWaitEvent(h->st, h->ev_join, 0));
+    sdsl_stats out{};
+    solve_conclude(h, mb.x, mb.x0_zero, &out, mb.tr.result, mb.reused, mb.rebuilt);
+    cudaEventRecord(h->ev_join, h->st);  // the caller's stream sees the result
+    cudaStreamWaitEvent(h->user, h->ev_join, 0);
+    done_h[*ndone] = h;
+    if (done_st) done_st[*ndone] = out;
+    *ndone += 1;
+    B->dirty = true;
+  }
+  B->members.swap(keep);
+  return SDSL_OK;
+}
+
+sdsl_status sdsl_batch_free(sdsl_batch B) {
+  if (!B) return SDSL_OK;
+  for (auto& mb : B->members) cudaEventDestroy(mb.t0);
+  if (B->graph) cudaGraphExecDestroy(B->graph);
+  B->ar.release();
+  cudaStreamSynchronize(B->st);
+  cudaStreamDestroy(B->st);
+  delete B;
+  return SDSL_OK;
+}
+
 sdsl_status sdsl_batch_solve(int count, sdsl_handle* hs, const double* const* b, double* const* x, int x0_zero,
                              sdsl_stats* st) {
   if (count < 0) return fail(SDSL_ERR_ARG, "count must be >= 0");
@@ -2342,57 +2468,36 @@ sdsl_status sdsl_batch_solve(int count, sdsl_handle* hs, const double* const* b,
   }
   bool together = count > 1;
   for (int i = 0; i < count; ++i) together = together && batchable(hs[i], hs[0]);
+  sdsl_status first = SDSL_OK;
   if (!together) {  // one at a time, each in its own call
-    sdsl_status first = SDSL_OK;
     for (int i = 0; i < count; ++i) {
       const sdsl_status s = sdsl_solve(hs[i], b[i], x[i], x0_zero, st ? &st[i] : nullptr);
       if (s != SDSL_OK && first == SDSL_OK) first = s;
     }
     return first;
   }
-  std::vector<sdsl_handle> H(hs, hs + count);
-  std::vector<std::unique_ptr<Scope>> scopes;
-  std::vector<int> rebuilt(count, 0);
-  std::vector<bool> reused(count);
-  for (int i = 0; i < count; ++i) {
-    scopes.emplace_back(new Scope(H[i]));
-    TRY(solve_prepare(H[i], b[i], x[i], x0_zero, &rebuilt[i]));
-    reused[i] = H[i]->solves_since_build > 0;
+  sdsl_batch B = nullptr;
+  TRY(sdsl_batch_create(hs[0]->opt.graph_iters, &B));
+  struct Free {
+    sdsl_batch b;
+    ~Free() { sdsl_batch_free(b); }
+  } free_b{B};
+  for (int i = 0; i < count; ++i) TRY(sdsl_batch_add(B, hs[i], b[i], x[i], x0_zero));
+  std::vector<sdsl_handle> dh(count);
+  std::vector<sdsl_stats> ds(count);
+  while (sdsl_batch_size(B) > 0) {
+    int nd = 0;
+    TRY(sdsl_batch_step(B, 1 << 30, dh.data(), ds.data(), count, &nd));
+    for (int k = 0; k < nd; ++k) {
+      for (int i = 0; i < count; ++i)
+        if (hs[i] == dh[k]) {
+          if (st) st[i] = ds[k];
+          if (ds[k].status != SDSL_OK && first == SDSL_OK) first = (sdsl_status)ds[k].status;
+        }
+    }
   }
-  // after preparation, but not once the batch is running, a request whose
-  // rebuild changed its kernel shape is solved alone below
-  for (int i = 0; i < count; ++i)
-    if (!batchable(H[i], H[0])) return fail(SDSL_ERR_STATE, "a rebuilt request no longer fits the batch");
-  cudaStream_t bs = H[0]->st;
-  for (int i = 1; i < count; ++i) {  // the batch stream starts after every request's preparation
-    TRY_CUDA(cudaEventRecord(H[i]->ev_join, H[i]->st));
-    TRY_CUDA(cudaStreamWaitEvent(bs, H[i]->ev_join, 0));
-  }
-  cudaEvent_t e0, e1;
-  TRY_CUDA(cudaEventCreate(&e0));
-  TRY_CUDA(cudaEventCreate(&e1));
-  cudaEventRecord(e0, bs);
-  sdsl_status sb = batch_pcg(H, bs);
-  cudaEventRecord(e1, bs);
-  cudaEventSynchronize(e1);
-  float ms = 0.f;
-  cudaEventElapsedTime(&ms, e0, e1);
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  TRY(sb);
-  for (int i = 1; i < count; ++i) {
-    TRY_CUDA(cudaEventRecord(H[0]->ev_join, bs));
-    TRY_CUDA(cudaStreamWaitEvent(H[i]->st, H[0]->ev_join, 0));
-  }
-  sdsl_status first = SDSL_OK;
-  for (int i = 0; i < count; ++i) {
-    sdsl_handle h = H[i];
-    h->stats.ms_solve = ms;
-    const sdsl_status s =
-        solve_conclude(h, x[i], x0_zero, st ? &st[i] : nullptr, (sdsl_status)h->stats.status, reused[i], rebuilt[i]);
-    if (s != SDSL_OK && first == SDSL_OK) first = s;
-  }
-  return first;
+  if (first != SDSL_OK) return fail(first, "a solve of the batch did not succeed");
+  return SDSL_OK;
 }
 
 sdsl_status sdsl_get_stats(sdsl_handle h, sdsl_stats* st) {

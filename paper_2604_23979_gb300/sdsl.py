@@ -89,6 +89,12 @@ def load():
     L.sdsl_update_diag.argtypes = [H, _VP]
     L.sdsl_set_tau.argtypes = [H, C.c_double]
     L.sdsl_batch_solve.argtypes = [C.c_int, _VP, _VP, _VP, C.c_int, _VP]
+    L.sdsl_batch_create.argtypes = [C.c_int, C.POINTER(C.c_void_p)]
+    L.sdsl_batch_add.argtypes = [_VP, _VP, _VP, _VP, C.c_int]
+    L.sdsl_batch_step.argtypes = [_VP, C.c_int, _VP, _VP, C.c_int, C.POINTER(C.c_int)]
+    L.sdsl_batch_size.argtypes = [_VP]
+    L.sdsl_batch_size.restype = C.c_int
+    L.sdsl_batch_free.argtypes = [_VP]
     L.sdsl_free.argtypes = [H]
     L.sdsl_get_stats.argtypes = [H, C.POINTER(sdsl_stats)]
     L.sdsl_get_info.argtypes = [H, C.POINTER(sdsl_info)]
@@ -107,8 +113,8 @@ def load():
     L.sdsl_kernel_launches.restype = C.c_int64
     L.sdsl_last_error.argtypes = []
     L.sdsl_last_error.restype = C.c_char_p
-    for f in ("sdsl_setup", "sdsl_factor", "sdsl_solve", "sdsl_batch_solve", "sdsl_update_diag", "sdsl_set_tau",
-              "sdsl_free", "sdsl_get_stats",
+    for f in ("sdsl_setup", "sdsl_factor", "sdsl_solve", "sdsl_batch_solve", "sdsl_batch_create", "sdsl_batch_add",
+              "sdsl_batch_step", "sdsl_batch_free", "sdsl_update_diag", "sdsl_set_tau", "sdsl_free", "sdsl_get_stats",
               "sdsl_get_info", "sdsl_export_system", "sdsl_export_precond", "sdsl_export_levels",
               "sdsl_export_schur", "sdsl_export_schur_lu", "sdsl_spmv", "sdsl_precond_apply", "sdsl_normal_spmv_noalloc"):
         getattr(L, f).restype = C.c_int
@@ -199,6 +205,43 @@ def sdsl_batch_solve(hs, bs, xs, x0_zero=True, allow=(ERR_NOT_CONVERGED,)):
                                  1 if x0_zero else 0, C.cast(st, C.c_void_p))
     _check(rc, allow)
     return list(st)
+
+
+def sdsl_batch_create(graph_iters=16):
+    B = C.c_void_p()
+    _check(load().sdsl_batch_create(int(graph_iters), C.byref(B)))
+    return B
+
+
+def sdsl_batch_add(B, h, b, x, x0_zero=True):
+    """Add a request (factored handle h, right-hand side b, solution x) to the
+    batch; b and x must stay alive until the request is handed back."""
+    if (isinstance(x, np.ndarray) and not x.flags.c_contiguous) or (hasattr(x, "is_contiguous")
+                                                                     and not x.is_contiguous()):
+        raise ValueError("x must be contiguous (it receives the solution)")
+    pb, px = _ptr(b), _ptr(x)
+    if pb[2] is not b:
+        raise ValueError("b must be contiguous (it is read while the batch runs)")
+    return _check(load().sdsl_batch_add(B, h, pb[0], px[0], 1 if x0_zero else 0))
+
+
+def sdsl_batch_step(B, max_graphs=1, cap=64):
+    """Launch the batch until a request finishes (or max_graphs graph
+    launches); returns [(handle value, stats)] of the requests that left."""
+    hs = (C.c_void_p * cap)()
+    st = (sdsl_stats * cap)()
+    nd = C.c_int(0)
+    _check(load().sdsl_batch_step(B, int(max_graphs), C.cast(hs, C.c_void_p), C.cast(st, C.c_void_p), int(cap),
+                                  C.byref(nd)))
+    return [(hs[k], st[k]) for k in range(nd.value)]
+
+
+def sdsl_batch_size(B):
+    return int(load().sdsl_batch_size(B))
+
+
+def sdsl_batch_free(B):
+    return _check(load().sdsl_batch_free(B))
 
 
 def sdsl_update_diag(h, theta):

@@ -171,12 +171,15 @@ class Scheduler:
 # --------------------------------------------------------------------------- GPU executor
 
 class _Batcher:
-    """Collects ready solves from the workers and runs all those waiting at
-    once through sdsl_batch_solve (up to max_batch per call)."""
+    """Continuous batching of the workers' solves: one thread keeps a batch
+    (sdsl_batch_*) running; a solve that becomes ready joins it between graph
+    launches, and a finished solve leaves it and wakes its worker at once.  A
+    handle that does not fit the batch's kernel shape is solved alone."""
 
-    def __init__(self, sdsl, max_batch: int):
+    def __init__(self, sdsl, max_batch: int, graph_iters: int):
         self.sdsl = sdsl
         self.max_batch = max_batch
+        self.graph_iters = graph_iters
         self.q: "queue.Queue" = queue.Queue()
         self.sizes: List[int] = []
         self.thread = threading.Thread(target=self._loop, daemon=True)
@@ -194,34 +197,61 @@ class _Batcher:
         self.q.put(None)
         self.thread.join()
 
+    @staticmethod
+    def _finish(item, st=None, err=None):
+        item["st"], item["err"] = st, err
+        item["done"].set()
+
     def _loop(self):
         sdsl = self.sdsl
-        while True:
-            first = self.q.get()
-            if first is None:
-                return
-            items = [first]
-            while len(items) < self.max_batch:
+        B = sdsl.sdsl_batch_create(self.graph_iters)
+        running = {}  # handle value -> waiting item
+        closing = False
+        try:
+            while True:
+                new = []
+                if not running and not closing:
+                    new.append(self.q.get())  # idle: wait for work
+                while True:
+                    try:
+                        new.append(self.q.get_nowait())
+                    except queue.Empty:
+                        break
+                for item in new:
+                    if item is None:
+                        closing = True
+                        continue
+                    h = item["h"]
+                    hv = h.value if hasattr(h, "value") else h
+                    if len(running) >= self.max_batch:
+                        self.q.put(item)  # full: next round
+                        continue
+                    try:
+                        sdsl.sdsl_batch_add(B, h, item["b"], item["x"])
+                        running[hv] = item
+                    except sdsl.SdslError:
+                        try:  # does not fit the batch: alone
+                            st = sdsl.sdsl_solve(h, item["b"], item["x"],
+                                                 allow=(sdsl.ERR_NOT_CONVERGED, sdsl.ERR_BREAKDOWN))
+                            self._finish(item, st=st)
+                        except Exception as e:  # noqa: BLE001 -- handed to the waiting worker
+                            self._finish(item, err=e)
+                if not running:
+                    if closing:
+                        return
+                    continue
+                self.sizes.append(len(running))
                 try:
-                    nxt = self.q.get_nowait()
-                except queue.Empty:
-                    break
-                if nxt is None:
-                    self.q.put(None)
-                    break
-                items.append(nxt)
-            self.sizes.append(len(items))
-            try:
-                sts = sdsl.sdsl_batch_solve([i["h"] for i in items], [i["b"] for i in items],
-                                            [i["x"] for i in items],
-                                            allow=(sdsl.ERR_NOT_CONVERGED, sdsl.ERR_BREAKDOWN))
-                for i, st in zip(items, sts):
-                    i["st"] = st
-            except Exception as e:  # noqa: BLE001 -- handed to every waiting worker
-                for i in items:
-                    i["err"] = e
-            for i in items:
-                i["done"].set()
+                    out = sdsl.sdsl_batch_step(B, max_graphs=1, cap=len(running))
+                except Exception as e:  # noqa: BLE001 -- every member's worker gets it
+                    for item in running.values():
+                        self._finish(item, err=e)
+                    running.clear()
+                    continue
+                for hv, st in out:
+                    self._finish(running.pop(hv), st=st)
+        finally:
+            sdsl.sdsl_batch_free(B)
 
 
 class GpuServer:
@@ -229,7 +259,7 @@ class GpuServer:
 
     def __init__(self, slots: int = 8, factor_prec: int = 32, device: int = 0, reserve_frac: float = 0.1,
                  budget_bytes: Optional[int] = None, keep_x: bool = False, graph_iters: int = 16,
-                 batch: bool = True, max_batch: int = 16):
+                 batch: bool = True, max_batch: int = 16, batchers: int = 1):
         import torch
 
         from . import sdsl
@@ -250,9 +280,10 @@ class GpuServer:
         self.streams = [torch.cuda.Stream(self.dev) for _ in range(slots)]
         self.batch = batch
         self.max_batch = max_batch
-        self._batcher: Optional[_Batcher] = None
+        self.n_batchers = max(1, batchers)
+        self._batchers: List[_Batcher] = []
 
-    def _serve_one(self, req, stream, t0: float) -> List[SolveRecord]:
+    def _serve_one(self, req, stream, t0: float, slot: int = 0) -> List[SolveRecord]:
         torch, sdsl = self.torch, self.sdsl
         prob = req.problem
         A = prob.A
@@ -277,8 +308,8 @@ class GpuServer:
                         start = time.perf_counter() - t0
                         d_th.copy_(torch.from_numpy(th).pin_memory(), non_blocking=True)
                         sdsl.sdsl_update_diag(h, d_th)
-                    if self._batcher is not None:
-                        st = self._batcher.solve(h, d_b, d_x)
+                    if self._batchers:  # each slot feeds one batcher (batches overlap like streams)
+                        st = self._batchers[slot % len(self._batchers)].solve(h, d_b, d_x)
                     else:
                         st = sdsl.sdsl_solve(h, d_b, d_x, allow=(sdsl.ERR_NOT_CONVERGED, sdsl.ERR_BREAKDOWN))
                     x = d_x.cpu().numpy() if self.keep_x else None
@@ -301,24 +332,25 @@ class GpuServer:
         t0_box = {}
 
         def execute(i: int, slot: int):
-            recs[i] = self._serve_one(requests[i], self.streams[slot], t0_box["t0"])
+            recs[i] = self._serve_one(requests[i], self.streams[slot], t0_box["t0"], slot)
 
         sched = Scheduler(self.slots, self.budget)
-        self._batcher = _Batcher(self.sdsl, self.max_batch) if self.batch else None
+        self._batchers = ([_Batcher(self.sdsl, self.max_batch, self.graph_iters) for _ in range(self.n_batchers)]
+                          if self.batch else [])
         t0_box["t0"] = time.perf_counter()
         try:
             admit, done, maxc = sched.run(arrivals, costs, execute)
         finally:
             sizes = []
-            if self._batcher is not None:
-                self._batcher.close()
-                sizes = self._batcher.sizes
-                self._batcher = None
+            for b in self._batchers:
+                b.close()
+                sizes += b.sizes
+            self._batchers = []
         results = [RequestResult(i, arrivals[i], admit[i], recs[i][-1].done_s, requests[i].problem.A.nrows, recs[i])
                    for i in range(n)]
         summ = summarize(results, maxc)
-        if sizes:
-            summ["batches"] = len(sizes)
+        if sizes:  # requests running together, sampled at every graph launch
+            summ["batch_steps"] = len(sizes)
             summ["mean_batch"] = round(float(np.mean(sizes)), 2)
             summ["max_batch"] = int(max(sizes))
         return results, summ

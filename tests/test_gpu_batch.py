@@ -115,3 +115,45 @@ def test_batch_with_unbatchable_handles_solves_each():
     for i in range(2):
         assert sts[i].iters == alone[i][1]
         assert np.array_equal(xs[i], alone[i][0])
+
+
+def test_continuous_batch_join_and_leave():
+    """Requests join a running batch between graph launches and leave as soon
+    as their own solve ends; every result equals the solve alone, bit for
+    bit, and a request that finishes early is handed back before the others."""
+    ps = problems()
+    alone = solve_alone(ps, 32)
+    hs, keeps = [], []
+    B = sdsl.sdsl_batch_create(16)
+    try:
+        for p in ps:
+            h, keep = setup(p, 32, **BATCH_OPTS)
+            sdsl.sdsl_factor(h)
+            hs.append(h)
+            keeps.append(keep)
+        xs = [np.zeros(len(p.b)) for p in ps]
+        order, steps = [], 0
+        for i in range(3):  # three start together
+            sdsl.sdsl_batch_add(B, hs[i], ps[i].b, xs[i])
+        pending = list(range(3, len(ps)))
+        while sdsl.sdsl_batch_size(B) > 0 or pending:
+            if pending and steps % 2 == 1:  # the others join while the batch runs
+                i = pending.pop(0)
+                sdsl.sdsl_batch_add(B, hs[i], ps[i].b, xs[i])
+            out = sdsl.sdsl_batch_step(B, max_graphs=1, cap=8)
+            steps += 1
+            for hv, st in out:
+                i = [h.value for h in hs].index(hv)
+                order.append(i)
+                assert st.status == alone[i][2] and st.iters == alone[i][1], (i, st.iters, alone[i][1])
+            assert steps < 10000
+    finally:
+        sdsl.sdsl_batch_free(B)
+        for h in hs:
+            sdsl.sdsl_free(h)
+    assert sorted(order) == list(range(len(ps)))
+    for i in range(len(ps)):
+        assert np.array_equal(xs[i].view(np.int64), alone[i][0].view(np.int64)), f"request {i} differs"
+    # the request with the fewest iterations among the first three leaves first
+    first3 = sorted(range(3), key=lambda i: alone[i][1])
+    assert order.index(first3[0]) < order.index(first3[2])
