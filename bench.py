@@ -40,7 +40,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--prec", type=int, default=32, choices=[32, 64])
+    ap.add_argument("--prec", type=int, default=32, choices=[16, 32, 64],
+                    help="factor storage: 64 FP64, 32 FP32 (default), 16 BF16 (trial)")
     ap.add_argument("--scale", type=float, default=1.0, help="workload scale (1.0 = the benchmark size)")
     ap.add_argument("--quick", action="store_true", help="no CPU baseline, e2e, FP64 form or profile pass")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -243,7 +244,7 @@ def run_ours(args, ws, rank, local):
             o.method = method
         o.profile = 1 if profile else 0
         o.solve_kernel = args.solve_kernel
-        o.apply_prec = args.apply_prec if prec == 32 else 0
+        o.apply_prec = args.apply_prec if prec == 32 or (prec == 16 and args.apply_prec != 64) else 0
         o.sweep_warps = args.sweep_warps
         o.sweep_backoff_ns = args.backoff_ns
         o.sweep_lane_entries = args.lane_entries
@@ -315,7 +316,8 @@ def run_ours(args, ws, rank, local):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": (f"f64 loop, f32 factors ({APPLY_NAMES[args.apply_prec]} apply)" if args.prec == 32 else "f64"),
+        "dtype": (f"f64 loop, {'f32' if args.prec == 32 else 'bf16'} factors ({APPLY_NAMES[args.apply_prec]} apply)"
+                  if args.prec != 64 else "f64"),
         "data": "synthetic (seeded staircase LP matrix; the paper's datasets are not available)",
         "config": {"workload": WORKLOAD if args.scale == 1.0 else WORKLOAD + f" scaled x{args.scale}",
                    "n": A.nrows, "nnz_A": int(A.nnz), "nnz_S": int(last.nnz_system),
@@ -353,6 +355,15 @@ def run_ours(args, ws, rank, local):
                              "iters": int(st_other[-1][0].iters),
                              "solve_ms": round(st_other[-1][0].ms_solve, 3),
                              "factor_ms": round(st_other[-1][1].ms_factor, 3)}
+        if args.prec != 16:
+            # BF16 factor storage (the coarsest the error budget might allow):
+            # one untimed solve tunes the new structure key, then two timed
+            timed_steps(16, 1)
+            t_b, st_b = timed_steps(16, 2)
+            sb = st_b[-1][0]
+            out["bf16_form"] = {"factor_prec": 16, "status": int(sb.status), "iters": int(sb.iters),
+                                "time_to_1e8_ms": round(statistics.median(t_b), 3),
+                                "solve_ms": round(sb.ms_solve, 3), "factor_ms": round(st_b[-1][1].ms_factor, 3)}
         # the other Krylov method on the same preconditioner (BiCGSTAB is the
         # pairing of Sec. 4.3; a pass holds two products and two applies)
         t_k, st_k = timed_steps(args.prec, 2, method=sdsl.BJ_BICGSTAB)

@@ -73,7 +73,8 @@ typedef struct {
   double tau;                    /* filter threshold of Eq. (filter), >= 0; 1e-3 in Sec. 3.2 */
   double delta;                  /* diagonal correction of Eq. (diagcorr), >= 0; 1e-12 in Sec. 3.3 */
   double rho;                    /* regularisation: rho*I added to S (normal) or the (2,2) block (augmented) */
-  int factor_prec;               /* 64 or 32: storage/apply precision of the factors; the Krylov loop is FP64 */
+  int factor_prec;               /* storage of the factors: 64, 32 or 16 (BF16; Block Jacobi with the staged
+                                    solves only -- a trial of the coarsest storage); the Krylov loop is FP64 */
   double rtol;                   /* relative residual target ||b - A x|| / ||b|| (1e-8 in Sec. 4) */
   int64_t maxit;                 /* iteration cap (products with the system matrix) */
   int restart;                   /* GMRES restart length m */
@@ -118,16 +119,19 @@ typedef struct {
                                     that leave at most this many of its entries per lane; 0 auto, 1..64 */
   int schur_lu;                  /* BBD border Schur LU: 0 auto (blocked, trailing update on tensor cores),
                                     1 blocked on CUDA cores, 2 unblocked (one column per step) */
-  int sweep_wait;                /* readiness in those sweeps: 0 auto, 1 per value (a tile waits until every
-                                    value it reads is solved), 2 per level (a tile waits until the previous
-                                    level of its block is complete, one shared counter per level) */
+  int sweep_wait;                /* readiness in those sweeps: 0 auto (2), 1 per value (a tile waits until
+                                    every value it reads is solved), 2 per level (a tile's far entries wait, parked on an mbarrier, until the
+                                    level sweep_far_gap below is complete; its near entries per value),
+                                    3 level-synchronous (the block's warps step through its levels together,
+                                    one named barrier per level; no waits inside a level) */
   int wait_limit;                /* polls after which a wait in those sweeps gives up and the solve returns
                                     SDSL_ERR_TIMEOUT; 0 = default (2^23 polls, about a second; 1,024 under
                                     wait_test) */
   int sweep_far_gap;             /* tile shape of the staged sweeps: entries whose column lies at least this
                                     many levels below the row are summed first, behind one wait on a level
                                     count; the nearer ones are read by the row's first lane last, polling
-                                    the values; 0 = auto (3), else 2..16 */
+                                    the values; 0 = auto (3, or tuned), else 2..16; 1 (every entry far)
+                                    only with sweep_wait 1.  The level-synchronous sweep uses 1 */
   int64_t tau_switch_step;       /* two-phase filter (Sec. 4.3): from this IPM step on (counted in
                                     sdsl_update_diag calls) builds filter with tau_after; 0 = off */
   double tau_after;              /* the second phase's threshold (1e-2 in Sec. 4.3) */

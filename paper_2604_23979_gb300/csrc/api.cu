@@ -456,9 +456,10 @@ void choose_spmv_plan(sdsl_handle h) {
 struct TuneKey {
   int dev, method, fprec, aprec;
   int64_t N, a_nnz, s_nnz, nb;
+  int64_t fixed;  // the options that narrow the candidates (packed): a choice is reused only under the same ones
   bool operator<(const TuneKey& o) const {
-    return std::tie(dev, method, fprec, aprec, N, a_nnz, s_nnz, nb) <
-           std::tie(o.dev, o.method, o.fprec, o.aprec, o.N, o.a_nnz, o.s_nnz, o.nb);
+    return std::tie(dev, method, fprec, aprec, N, a_nnz, s_nnz, nb, fixed) <
+           std::tie(o.dev, o.method, o.fprec, o.aprec, o.N, o.a_nnz, o.s_nnz, o.nb, o.fixed);
   }
 };
 struct TuneChoice {
@@ -473,7 +474,10 @@ std::map<TuneKey, TuneChoice>& tune_cache() {
   return m;
 }
 TuneKey tune_key(sdsl_handle h, int apply) {
-  return TuneKey{h->dev, h->method, h->opt.factor_prec, apply, h->N, h->a_nnz, h->s_nnz, h->nblocks};
+  const sdsl_options& o = h->opt;
+  const int64_t fixed = (int64_t)o.sweep_lane_entries | (int64_t)o.sweep_far_gap << 8 | (int64_t)o.sweep_wait << 16 |
+                        (int64_t)o.wait_test << 20 | (int64_t)o.spmv_form << 24 | (int64_t)o.sweep_slots << 28;
+  return TuneKey{h->dev, h->method, h->opt.factor_prec, apply, h->N, h->a_nnz, h->s_nnz, h->nblocks, fixed};
 }
 
 // Mean device time of one call of `launch` (after one untimed call).
@@ -1077,7 +1081,8 @@ sdsl_status build_vtiles(sdsl_handle h, bool f32, int apply, int E, int gap, Are
   TriSolve& M = h->M;
   const int64_t nb = h->nblocks;
   const int64_t nrows = h->h_bp[nb];
-  const int tsz = f32 ? 4 : 8;
+  const int tprec = h->opt.factor_prec == 16 ? 16 : f32 ? 32 : 64;  // stored value size: 2, 4 or 8 bytes
+  const int tsz = tprec / 8;
   const int tc = apply == 32 ? 4 : 8;
   M.far_gap = gap;
   const int kWarps = 16;
@@ -1212,10 +1217,12 @@ sdsl_status build_vtiles(sdsl_handle h, bool f32, int apply, int E, int gap, Are
   M.max_tiles = mt;
   M.kreg = E <= 8 ? 8 : 16;
   M.max_levels = (int)maxlev;
-  M.level_wait = h->opt.sweep_wait == 1 ? 0 : 1;  // auto: per-level barriers
+  // per-value readiness where asked for; otherwise gap 1 (every entry far)
+  // is the level-synchronous sweep and a larger gap the per-level barriers
+  M.level_wait = h->opt.sweep_wait == 1 ? 0 : gap == 1 ? 2 : 1;
   // tiles of every level, in the order of the level offsets (block, level)
   for (int dir = 0; dir < 2; ++dir) {
-    std::vector<int32_t> lt;
+    std::vector<int32_t> lt, le;
     const Plan& P = plan[dir];
     const std::vector<int32_t>& nl = dir == 0 ? h->h_nlev_lo : h->h_nlev_up;
     int64_t t = 0;
@@ -1224,12 +1231,15 @@ sdsl_status build_vtiles(sdsl_handle h, bool f32, int apply, int E, int gap, Are
         int32_t c = 0;
         while (t < P.tile_ptr[k + 1] && P.meta[3 * t] == l) { ++c; ++t; }
         lt.push_back(std::max<int32_t>(c, 1));
+        le.push_back((int32_t)(t - P.tile_ptr[k]));
       }
     }
-    int32_t* d_lt;
+    int32_t *d_lt, *d_le;
     TRY(out.get(&d_lt, lt.size()));
+    TRY(out.get(&d_le, le.size()));
     TRY(to_dev(h, d_lt, lt.data(), lt.size()));
-    if (dir == 0) M.fwd_ltiles = d_lt; else M.bwd_ltiles = d_lt;
+    TRY(to_dev(h, d_le, le.data(), le.size()));
+    if (dir == 0) { M.fwd_ltiles = d_lt; M.fwd_lend = d_le; } else { M.bwd_ltiles = d_lt; M.bwd_lend = d_le; }
   }
   for (int dir = 0; dir < 2; ++dir) {
     Plan& P = plan[dir];
@@ -1253,7 +1263,7 @@ sdsl_status build_vtiles(sdsl_handle h, bool f32, int apply, int E, int gap, Are
     TRY(to_dev(h, d_tile, P.tile_ptr.data(), nb + 1));
     TRY(to_dev(h, d_meta, P.meta.data(), P.meta.size()));
     TRY_CUDA(vt_fill(dir, ntiles, d_trp, d_rows, d_logv, h->row_block, h->d_bp, h->p_rp, h->p_ci, h->p_diag, h->F,
-                     h->dinv, dir == 0 ? h->row_lev_lo : h->row_lev_up, f32 ? 32 : 64, d_toff, d_meta, stream,
+                     h->dinv, dir == 0 ? h->row_lev_lo : h->row_lev_up, tprec, d_toff, d_meta, stream,
                      d_bad, gap, h->st));
     if (dir == 0) { M.fwd_stream = stream; M.fwd_toff = d_toff; M.fwd_tile = d_tile; }
     else { M.bwd_stream = stream; M.bwd_toff = d_toff; M.bwd_tile = d_tile; }
@@ -1269,14 +1279,26 @@ sdsl_status build_vtiles(sdsl_handle h, bool f32, int apply, int E, int gap, Are
 // Tile shape of the staged sweeps: build each candidate's tile streams in a
 // scratch arena and time the preconditioner apply (3 calls each).
 sdsl_status tune_sweep(sdsl_handle h, bool f32, int apply, int* E_out, int* gap_out) {
-  const int E0 = h->opt.sweep_lane_entries, G0 = h->opt.sweep_far_gap;
+  // Candidates (E, gap): gap >= 2 runs the per-level barrier protocol with
+  // that far/near split, gap 1 the level-synchronous sweep (every entry far),
+  // which is timed only when asked for (sweep_wait 3): on the staircase
+  // workloads it loses to the barrier protocol at every shape.
+  const int E0 = h->opt.sweep_lane_entries, G0 = h->opt.sweep_far_gap, W0 = h->opt.sweep_wait;
   std::vector<std::pair<int, int>> cand;
-  const int Es[] = {16, 12, 24, 32};
-  const int Gs[] = {3, 2, 4};
-  for (int e : Es)
-    for (int g : Gs)
-      if ((E0 == 0 || e == E0) && (G0 == 0 || g == G0)) cand.emplace_back(e, g);
-  if (cand.empty()) cand.emplace_back(E0 > 0 ? E0 : 16, G0 > 0 ? G0 : 3);
+  if (W0 != 3) {
+    const int Es[] = {16, 12, 24, 32};
+    const int Gs[] = {3, 2, 4};
+    for (int e : Es)
+      for (int g : Gs)
+        if ((E0 == 0 || e == E0) && (G0 == 0 || g == G0)) cand.emplace_back(e, g);
+    if (cand.empty()) cand.emplace_back(E0 > 0 ? E0 : 16, G0 > 0 ? G0 : 3);
+  }
+  if (W0 == 3) {
+    const int Es[] = {8, 4, 16, 2};
+    for (int e : Es)
+      if (E0 == 0 || e == E0) cand.emplace_back(e, 1);
+    if (E0 != 0 && cand.empty()) cand.emplace_back(E0, 1);
+  }
   TRY_CUDA(cudaMemsetAsync(h->r, 0, sizeof(double) * (size_t)h->N, h->st));
   float best = 1e30f, def = 1e30f;
   int bE = cand[0].first, bG = cand[0].second;
@@ -1427,7 +1449,8 @@ sdsl_status factor_impl(sdsl_handle h) {
     h->h_alpha[k] = kShifts[tries[k]];
     shifted += tries[k] > 0;
   }
-  const bool f32 = h->opt.factor_prec == 32;
+  const bool b16 = h->opt.factor_prec == 16;  // BF16 storage (staged solves): FP32 arrays hold the rounded values
+  const bool f32 = h->opt.factor_prec == 32 || b16;
   if (f32) {
     TRY(h->pc.get(&h->Ff, h->p_nnz));
     TRY(h->pc.get(&h->dinvf, N));
@@ -1442,6 +1465,10 @@ sdsl_status factor_impl(sdsl_handle h) {
     }
   } else {
     TRY_CUDA(ic0_finish(N, h->p_nnz, h->p_rp, h->p_diag, h->mir, h->F, h->dinv, h->Ff, h->dinvf, h->st));
+    if (b16) {
+      TRY_CUDA(round_bf16(h->p_nnz, h->Ff, h->st));
+      TRY_CUDA(round_bf16(N, h->dinvf, h->st));
+    }
   }
   if (h->method == SDSL_BBD_GMRES) {
     TRY(build_bbd(h));
@@ -1472,7 +1499,7 @@ sdsl_status factor_impl(sdsl_handle h) {
   M.lev_ptr_up = h->lev_ptr_up;
   M.lev_rows_up = h->lev_rows_up;
   M.unit_lower = h->method == SDSL_BBD_GMRES ? 1 : 0;
-  M.prec = f32 ? 32 : 64;
+  M.prec = b16 ? 16 : f32 ? 32 : 64;
   const double avg_half = N > 0 ? (double)(h->p_nnz - N) / (2.0 * (double)N) : 1.0;
   M.lanes = pow2_lanes(avg_half, 2.0);
   M.max_block = maxb;
@@ -1517,7 +1544,7 @@ sdsl_status factor_impl(sdsl_handle h) {
   if (M.staged) {
     bool ok = false;
     int E = h->opt.sweep_lane_entries > 0 ? h->opt.sweep_lane_entries : 16;
-    int gap = h->opt.sweep_far_gap > 0 ? h->opt.sweep_far_gap : 3;
+    int gap = h->opt.sweep_wait == 3 ? 1 : h->opt.sweep_far_gap > 0 ? h->opt.sweep_far_gap : 3;
     if (h->opt.tune) {
       const TuneKey key = tune_key(h, apply);
       TuneChoice ch{};
@@ -1548,6 +1575,9 @@ sdsl_status factor_impl(sdsl_handle h) {
       M.staged = 0;
     }
   }
+  if (b16 && !M.staged)
+    return fail(SDSL_ERR_ARG, "BF16 factors (factor_prec 16) need the staged solves (blocks of at most 65,535 rows "
+                              "that fit in shared memory)");
   // float-float arithmetic exists in the staged sweeps only
   if (M.apply_prec == 48 && !M.staged) {
     if (h->opt.apply_prec == 48)
@@ -1639,7 +1669,7 @@ sdsl_status factor_impl(sdsl_handle h) {
   //           values + columns; inverse diagonal; row pointers and diagonal
   //           positions (read by both solves); level row lists (both solves).
   //  direct.: read z, p; write p.
-  const double sf = f32 ? 4.0 : 8.0;
+  const double sf = b16 ? 2.0 : f32 ? 4.0 : 8.0;
   const double Nd = (double)N;
   const double offd = (double)(h->p_nnz - N);
   h->stats.kernel_bytes[0] = 12.0 * (double)h->s_nnz + 8.0 * (Nd + 1.0) + 16.0 * Nd;
@@ -2143,7 +2173,12 @@ sdsl_status sdsl_setup(const sdsl_options* opt, int64_t m, int64_t n, const int6
   if (opt->form < SDSL_FORM_CSR || opt->form > SDSL_FORM_AUGMENTED) return fail(SDSL_ERR_ARG, "unknown form");
   if (opt->method != SDSL_BJ_PCG && opt->method != SDSL_BBD_GMRES && opt->method != SDSL_BJ_BICGSTAB)
     return fail(SDSL_ERR_ARG, "unknown method");
-  if (opt->factor_prec != 64 && opt->factor_prec != 32) return fail(SDSL_ERR_ARG, "factor_prec must be 64 or 32");
+  if (opt->factor_prec != 64 && opt->factor_prec != 32 && opt->factor_prec != 16)
+    return fail(SDSL_ERR_ARG, "factor_prec must be 64, 32 or 16");
+  if (opt->factor_prec == 16 && opt->method == SDSL_BBD_GMRES)
+    return fail(SDSL_ERR_ARG, "BF16 factors are for the Block-Jacobi methods");
+  if (opt->factor_prec == 16 && opt->apply_prec == 64)
+    return fail(SDSL_ERR_ARG, "BF16 factors are applied in float-float (48) or FP32 (32) arithmetic");
   if (opt->solve_kernel < 0 || opt->solve_kernel > 3) return fail(SDSL_ERR_ARG, "solve_kernel must be 0..3");
   if (opt->spmv_form < 0 || opt->spmv_form > 3) return fail(SDSL_ERR_ARG, "spmv_form must be in 0..3");
   if (opt->orthog < 0 || opt->orthog > 1) return fail(SDSL_ERR_ARG, "orthog must be 0 or 1");
@@ -2152,7 +2187,9 @@ sdsl_status sdsl_setup(const sdsl_options* opt, int64_t m, int64_t n, const int6
     return fail(SDSL_ERR_ARG, "sweep_backoff_ns must be in -1..1000");
   if (opt->sweep_lane_entries < 0 || opt->sweep_lane_entries > 64)
     return fail(SDSL_ERR_ARG, "sweep_lane_entries must be in 0..64");
-  if (opt->sweep_wait < 0 || opt->sweep_wait > 2) return fail(SDSL_ERR_ARG, "sweep_wait must be in 0..2");
+  if (opt->sweep_wait < 0 || opt->sweep_wait > 3) return fail(SDSL_ERR_ARG, "sweep_wait must be in 0..3");
+  if (opt->sweep_wait == 3 && opt->wait_test)
+    return fail(SDSL_ERR_ARG, "wait_test exercises the barrier waits, which the level-synchronous sweep has none of");
   if (opt->schur_lu < 0 || opt->schur_lu > 2) return fail(SDSL_ERR_ARG, "schur_lu must be in 0..2");
   if (opt->wait_limit < 0) return fail(SDSL_ERR_ARG, "wait_limit must be >= 0");
   if (opt->tau_switch_step < 0 || !(opt->tau_after >= 0.0) || !(opt->tau_relax >= 0.0) || opt->tau_relax >= 1.0)
@@ -2160,8 +2197,8 @@ sdsl_status sdsl_setup(const sdsl_options* opt, int64_t m, int64_t n, const int6
   if (opt->wait_test < 0 || opt->wait_test > 1) return fail(SDSL_ERR_ARG, "wait_test must be 0 or 1");
   if (opt->sweep_slots != 0 && (opt->sweep_slots < 2 || opt->sweep_slots > 4))
     return fail(SDSL_ERR_ARG, "sweep_slots must be 0 (auto) or in 2..4");
-  if (opt->sweep_far_gap < 0 || opt->sweep_far_gap == 1 || opt->sweep_far_gap > 16)
-    return fail(SDSL_ERR_ARG, "sweep_far_gap must be 0 (auto) or in 2..16");
+  if (opt->sweep_far_gap < 0 || opt->sweep_far_gap > 16 || (opt->sweep_far_gap == 1 && opt->sweep_wait != 1))
+    return fail(SDSL_ERR_ARG, "sweep_far_gap must be 0 (auto) or in 2..16 (1 with per-value readiness)");
   if (opt->apply_prec != 0 && opt->apply_prec != 64 && opt->apply_prec != 48 && opt->apply_prec != 32)
     return fail(SDSL_ERR_ARG, "apply_prec must be 0, 32, 48 or 64");
   if (opt->factor_prec == 64 && (opt->apply_prec == 32 || opt->apply_prec == 48))

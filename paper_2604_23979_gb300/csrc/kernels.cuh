@@ -73,6 +73,7 @@ cudaError_t ilu0_factor(int64_t nblocks, const int64_t* bp, const int64_t* prp, 
 cudaError_t ic0_finish(int64_t n, int64_t nnz, const int64_t* prp, const int64_t* pdiag, const int64_t* mir,
                        double* F, const double* dinv, float* Ff, float* dinvf, cudaStream_t st);
 cudaError_t to_float(int64_t n, const double* a, float* b, cudaStream_t st);
+cudaError_t round_bf16(int64_t n, float* a, cudaStream_t st);
 // Variable-width tiles (see precond.cu): fill the stream from a host-built plan.
 // lev: level of every row within its block for this direction (far entries
 // of a row at level L have column level <= L - gap, near ones above that).
@@ -138,7 +139,7 @@ struct TriSolve {  // block triangular factors on the layout of P
   const int32_t* lev_ptr_up;
   const int32_t* lev_rows_up;
   int unit_lower;       // 1 for ILU(0) (L has a unit diagonal)
-  int prec;             // 64 or 32
+  int prec;             // storage of the factor values: 64, 32 or 16 (BF16, staged solves only)
   int lanes;            // lanes per row in the solves (2..32)
   int64_t max_block;    // largest block (rows) -> shared-memory staging if it fits
   float* yscratch;      // global staging when the block does not fit in shared memory
@@ -171,7 +172,8 @@ struct TriSolve {  // block triangular factors on the layout of P
   int staged;           // 1: staged level tiles (cp.async copies into a per-warp shared-memory ring)
   int slot_bytes;       // ring slot size; larger tiles are read from global memory directly
   int kreg;             // entries per lane and gather round of the staged solves (8 or 16)
-  int level_wait;       // staged solves: 1 = per-level completion counters, 0 = per-value readiness
+  int level_wait;       // staged solves: 0 = per-value readiness, 1 = per-level mbarriers (far part) and
+                        // per-value readiness (near part), 2 = level-synchronous (one named barrier per level)
   int max_levels;       // largest level count of a block (either direction): counters in shared memory
   int64_t max_tiles;    // max over blocks of (forward tiles + backward tiles): staged tile offsets
   int slots;            // ring slots per warp
@@ -186,6 +188,8 @@ struct TriSolve {  // block triangular factors on the layout of P
   int far_gap;          // staged tiles: entries at least this many levels below the row are "far"
   const int32_t* fwd_ltiles;  // staged tiles per level (forward), indexed like lev_off_lo: block b, level l
   const int32_t* bwd_ltiles;  // at lev_off_[lo|up][b] + l (backward)
+  const int32_t* fwd_lend;    // tiles of block b through level l (cumulative), same indexing
+  const int32_t* bwd_lend;
 };
 
 // Packed level-ordered triangle of one direction (dir 0 = strict lower in

@@ -10,6 +10,8 @@
 //               one launch).
 //   IC(0)/ILU(0) per-block zero-fill factors (Sec. 2.3 third step; Sec. 3.1),
 //               level-scheduled, one CTA per block, one warp per row.
+#include <cuda_bf16.h>
+
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -514,6 +516,15 @@ __device__ __forceinline__ int strict_count(int dir, int64_t i, int64_t s, int64
 // A lane reads its whole role with one 8-byte load.  The plan (rows of every
 // tile in packing order and their V) is built on the host; one tile per
 // thread.  *bad is set if a row has more than 255 near entries.
+// Stored factor value from the FP64 factor: FP64, FP32, or BF16 through FP32
+// (so the BF16 values equal those of the rounded FP32 copy).
+template <typename TS>
+__device__ __forceinline__ TS to_stored(double v) { return (TS)v; }
+template <>
+__device__ __forceinline__ __nv_bfloat16 to_stored<__nv_bfloat16>(double v) {
+  return __float2bfloat16_rn((float)v);
+}
+
 template <typename TS>
 __global__ void k_vt_fill(int dir, int64_t ntiles, const int32_t* __restrict__ tile_rows_ptr,
                           const int32_t* __restrict__ plan_rows, const int8_t* __restrict__ plan_logv,
@@ -551,7 +562,7 @@ __global__ void k_vt_fill(int dir, int64_t ntiles, const int32_t* __restrict__ t
       }
       const int nnear = len - nfar;
       if (nnear > 255) *bad = 1;
-      dv[r] = (TS)dinv[i];
+      dv[r] = to_stored<TS>(dinv[i]);
       for (int k = 0; k < V; ++k) {
         const int cfar = k < nfar ? (nfar - k + V - 1) / V : 0;
         rec[4 * (lane + k) + 0] = (uint16_t)(i - s);
@@ -581,7 +592,7 @@ __global__ void k_vt_fill(int dir, int64_t ntiles, const int32_t* __restrict__ t
           if (j < s || j >= e) continue;
           if ((lev[j] <= lev[i] - gap) != (pass == 1)) continue;
           col[at] = (uint16_t)(j - s);
-          val[at] = (TS)F[q];
+          val[at] = to_stored<TS>(F[q]);
           ++at;
         }
       }
@@ -593,6 +604,13 @@ __global__ void k_ic0_finish(int64_t n, const int64_t* __restrict__ prp, const i
                              const int64_t* __restrict__ mir, double* __restrict__ F) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     for (int64_t t = pdiag[i] + 1; t < prp[i + 1]; ++t) F[t] = F[mir[t]];
+}
+
+// FP32 values rounded to BF16 precision in place (the stored BF16 factor,
+// widened, for exports and checks).
+__global__ void k_round_bf16(int64_t n, float* __restrict__ a) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    a[i] = __bfloat162float(__float2bfloat16_rn(a[i]));
 }
 
 __global__ void k_to_float(int64_t n, const double* __restrict__ a, float* __restrict__ b) {
@@ -721,7 +739,12 @@ cudaError_t vt_fill(int dir, int64_t ntiles, const int32_t* tile_rows_ptr, const
                     const int32_t* pci, const int64_t* pdiag, const double* F, const double* dinv, const int32_t* lev,
                     int prec, const int64_t* toff, const int32_t* tile_meta, unsigned char* stream, int* bad,
                     int gap, cudaStream_t st) {
-  if (prec == 32) {
+  if (prec == 16) {
+    k_vt_fill<__nv_bfloat16><<<grid_for(ntiles, 128), 128, 0, st>>>(dir, ntiles, tile_rows_ptr, plan_rows,
+                                                                    plan_logv, row_block, bp, prp, pci, pdiag, F,
+                                                                    dinv, lev, toff, tile_meta, stream, bad, gap);
+    count_launch();
+  } else if (prec == 32) {
     k_vt_fill<float><<<grid_for(ntiles, 128), 128, 0, st>>>(dir, ntiles, tile_rows_ptr, plan_rows, plan_logv,
                                                             row_block, bp, prp, pci, pdiag, F, dinv, lev, toff,
                                                             tile_meta, stream, bad, gap); count_launch();
@@ -730,6 +753,11 @@ cudaError_t vt_fill(int dir, int64_t ntiles, const int32_t* tile_rows_ptr, const
                                                              row_block, bp, prp, pci, pdiag, F, dinv, lev, toff,
                                                              tile_meta, stream, bad, gap); count_launch();
   }
+  return cudaGetLastError();
+}
+
+cudaError_t round_bf16(int64_t n, float* a, cudaStream_t st) {
+  k_round_bf16<<<grid_for(n, 256), 256, 0, st>>>(n, a); count_launch();
   return cudaGetLastError();
 }
 

@@ -18,6 +18,8 @@
 // shared memory, initialised to a signalling-NaN sentinel; a tile polls
 // (warp-uniformly, bounded) until every value it reads is no longer the
 // sentinel, so no barrier separates the levels.
+#include <cuda_bf16.h>
+
 #include <type_traits>
 
 #include "pcg_common.cuh"
@@ -113,6 +115,7 @@ __device__ __forceinline__ double ff_to_double(unsigned long long v) { return (d
 // row waits for its near entries, which the leader then adds one by one.
 template <typename TS, typename TC, bool FF>
 struct SweepArith {  // plain: TC = float or double
+  using TSt = TS;
   using X = TC;
   using VV = TC;
   using D = TC;
@@ -121,7 +124,10 @@ struct SweepArith {  // plain: TC = float or double
   };
   static __device__ __forceinline__ X sent() { return sentinel(TC(0)); }
   static __device__ __forceinline__ bool is_sent(X x) { return is_sentinel(x); }
-  static __device__ __forceinline__ VV val(TS v) { return (TC)v; }
+  static __device__ __forceinline__ VV val(TS v) {
+    if constexpr (std::is_same<TS, __nv_bfloat16>::value) return (TC)__bfloat162float(v);
+    else return (TC)v;
+  }
   static __device__ __forceinline__ void init(Acc& a, X minus_in_of) { a.a0 = -minus_in_of; a.a1 = TC(0); }
   static __device__ __forceinline__ void add(Acc& a, int k, VV v, X x) {  // k: unrolled slot
     if (k & 1) a.a1 = fma(v, x, a.a1);
@@ -137,7 +143,8 @@ struct SweepArith {  // plain: TC = float or double
 };
 
 template <typename TS, typename TC>
-struct SweepArith<TS, TC, true> {  // float-float (TS = float)
+struct SweepArith<TS, TC, true> {  // float-float (TS = float or BF16)
+  using TSt = TS;
   using X = unsigned long long;
   using VV = float;
   using D = float;
@@ -146,7 +153,10 @@ struct SweepArith<TS, TC, true> {  // float-float (TS = float)
   };
   static __device__ __forceinline__ X sent() { return kFFSentinel; }
   static __device__ __forceinline__ bool is_sent(X x) { return x == kFFSentinel; }
-  static __device__ __forceinline__ VV val(float v) { return v; }
+  static __device__ __forceinline__ VV val(TS v) {
+    if constexpr (std::is_same<TS, __nv_bfloat16>::value) return __bfloat162float(v);
+    else return (float)v;
+  }
   static __device__ __forceinline__ void init(Acc& a, X in) {
     a.s0 = -ff_hi(in);
     a.c0 = -ff_lo(in);
@@ -262,6 +272,84 @@ __device__ __forceinline__ void load_ready(const int (&jj)[KR], typename AR::X (
   }
 }
 
+// One tile of a sweep: the rows of one level in one warp.  The lanes' far
+// entries are summed (after wait_far, which may park the warp until the far
+// levels are complete), added into each row's leader, then the leader adds
+// its near entries, polling their values until final (after wait_near), and
+// stores the row's value.  Returns the tile's level.
+template <typename AR, int KREG, int KNEAR, typename WaitFar, typename WaitNear>
+__device__ __forceinline__ int solve_tile(const unsigned char* base, int lane, volatile typename AR::X* in,
+                                          volatile typename AR::X* out, bool unit, unsigned backoff, int limit,
+                                          int* timeout, WaitFar wait_far, WaitNear wait_near) {
+  using X = typename AR::X;
+  using VV = typename AR::VV;
+  using D = typename AR::D;
+  using TS = typename AR::TSt;
+  const int nr = reinterpret_cast<const int32_t*>(base)[0];
+  const int ne = reinterpret_cast<const int32_t*>(base)[1];
+  const int level = reinterpret_cast<const int32_t*>(base)[2];
+  const uint2 rec = reinterpret_cast<const uint2*>(base + 16)[lane];  // this lane's role, one load
+  const int row = (int)(rec.x & 0xFFFFu);
+  const int first = (int)(rec.x >> 16);
+  const int nfar = (int)(rec.y & 0xFFu);
+  const int V = 1 << ((rec.y >> 8) & 0xFFu);
+  const int r = (int)((rec.y >> 16) & 0x7Fu);
+  const bool leader = ((rec.y >> 23) & 1u) != 0;
+  const int nnear = (int)(rec.y >> 24);
+  const int Vmax = (int)__reduce_max_sync(0xffffffffu, (unsigned)V);
+  const TS* dv = reinterpret_cast<const TS*>(base + 16 + 256);
+  const uint16_t* cols = reinterpret_cast<const uint16_t*>(base + 16 + 256 + ((nr * (int)sizeof(TS) + 15) & ~15));
+  const TS* vals = reinterpret_cast<const TS*>(reinterpret_cast<const unsigned char*>(cols) + ((2 * ne + 15) & ~15));
+  // The right-hand side and the inverse diagonal are final before the
+  // sweep starts: read them first, off the critical path.
+  const X inr = leader ? in[row] : X(0);
+  const D dvr = leader && !unit ? (D)AR::val(dv[r]) : D(1);
+  typename AR::Acc acc;
+  AR::init(acc, inr);
+  // far entries of the lane, KREG per warp-uniform round
+  const int rfar = __reduce_max_sync(0xffffffffu, (unsigned)((nfar + KREG - 1) / KREG));
+  if (rfar > 0) wait_far(level);
+  for (int c = 0; c < rfar; ++c) {
+    int jj[KREG];
+    VV vv[KREG];
+    X xv[KREG];
+#pragma unroll
+    for (int k2 = 0; k2 < KREG; ++k2) {
+      const int idx = c * KREG + k2;
+      const bool ok = idx < nfar;
+      const int e = first + idx * V;
+      jj[k2] = ok ? (int)cols[e] : -1;
+      vv[k2] = ok ? AR::val(vals[e]) : VV(0);
+    }
+    load_ready<AR, KREG>(jj, xv, out, backoff, limit, timeout);
+#pragma unroll
+    for (int k2 = 0; k2 < KREG; ++k2) AR::add(acc, k2, vv[k2], xv[k2]);
+  }
+  AR::gather(acc, V, Vmax);
+  wait_near(level);
+  // near entries (leader lanes), KNEAR per round
+  const int near0 = first - nnear;
+  const int rnear = __reduce_max_sync(0xffffffffu, (unsigned)((nnear + KNEAR - 1) / KNEAR));
+  for (int c = 0; c < rnear; ++c) {
+    int jj[KNEAR];
+    VV vv[KNEAR];
+    X xv[KNEAR];
+#pragma unroll
+    for (int k2 = 0; k2 < KNEAR; ++k2) {
+      const int idx = c * KNEAR + k2;
+      const bool ok = idx < nnear;
+      jj[k2] = ok ? (int)cols[near0 + idx] : -1;
+      vv[k2] = ok ? AR::val(vals[near0 + idx]) : VV(0);
+    }
+    load_ready<AR, KNEAR>(jj, xv, out, backoff, limit, timeout);
+#pragma unroll
+    for (int k2 = 0; k2 < KNEAR; ++k2)
+      if (jj[k2] >= 0) AR::add_near(acc, vv[k2], xv[k2]);
+  }
+  if (leader) out[row] = AR::finish(acc, dvr);
+  return level;
+}
+
 // One sweep of a block.  `in` holds the right-hand side, `out` the solution
 // (sentinel until solved; an aligned store publishes value and readiness at
 // once).  Only warps w < W take tiles.  A tile's rows are at one level L.
@@ -284,9 +372,6 @@ __device__ __forceinline__ void sweep_staged(const unsigned char* __restrict__ s
                                              int* timeout, int W, unsigned backoff, uint64_t* done, int limit,
                                              int pad, int gap) {
   using AR = SweepArith<TS, TC, FF>;
-  using X = typename AR::X;
-  using VV = typename AR::VV;
-  using D = typename AR::D;
   const int lane = lane_id(), w = threadIdx.x >> 5;
   if (w >= W) return;
   const int nk = ntile > w ? (ntile - w + W - 1) / W : 0;  // tiles of this warp
@@ -311,6 +396,15 @@ __device__ __forceinline__ void sweep_staged(const unsigned char* __restrict__ s
   };
 #pragma unroll
   for (int d = 0; d < SLOTS - 1; ++d) issue(d);
+  // far part: park until level L - gap is complete; near part: under the
+  // timeout-path test the tile first waits for level L - 1, whose barrier
+  // then expects one arrival more than it gets
+  auto wait_far = [&](int level) {
+    if (done && level >= gap) wait_level(done, level - gap, limit, timeout);
+  };
+  auto wait_near = [&](int level) {
+    if (pad && done && level >= 1) wait_level(done, level - 1, limit, timeout);
+  };
   for (int k = 0; k < nk; ++k) {
     const int t = w + k * W;
     const int64_t a = toff_s[t];
@@ -319,72 +413,8 @@ __device__ __forceinline__ void sweep_staged(const unsigned char* __restrict__ s
     __syncwarp();
     // A tile larger than a slot (one very long row) is read in place.
     const unsigned char* base = bytes <= slot_bytes ? ring + (k % SLOTS) * slot_bytes : stream + a;
-    const int nr = reinterpret_cast<const int32_t*>(base)[0];
-    const int ne = reinterpret_cast<const int32_t*>(base)[1];
-    const int level = reinterpret_cast<const int32_t*>(base)[2];
-    const unsigned needs = reinterpret_cast<const uint32_t*>(base)[3];
-    (void)needs;  // tiles of levels L - 1 and L - gap: the barriers carry these counts
-    const uint2 rec = reinterpret_cast<const uint2*>(base + 16)[lane];  // this lane's role, one load
-    const int row = (int)(rec.x & 0xFFFFu);
-    const int first = (int)(rec.x >> 16);
-    const int nfar = (int)(rec.y & 0xFFu);
-    const int V = 1 << ((rec.y >> 8) & 0xFFu);
-    const int r = (int)((rec.y >> 16) & 0x7Fu);
-    const bool leader = ((rec.y >> 23) & 1u) != 0;
-    const int nnear = (int)(rec.y >> 24);
-    const int Vmax = (int)__reduce_max_sync(0xffffffffu, (unsigned)V);
-    const TS* dv = reinterpret_cast<const TS*>(base + 16 + 256);
-    const uint16_t* cols = reinterpret_cast<const uint16_t*>(base + 16 + 256 + ((nr * (int)sizeof(TS) + 15) & ~15));
-    const TS* vals = reinterpret_cast<const TS*>(reinterpret_cast<const unsigned char*>(cols) + ((2 * ne + 15) & ~15));
-    // The right-hand side and the inverse diagonal are final before the
-    // sweep starts: read them first, off the critical path.
-    const X inr = leader ? in[row] : X(0);
-    const D dvr = leader && !unit ? (D)dv[r] : D(1);
-    typename AR::Acc acc;
-    AR::init(acc, inr);
-    // far entries of the lane, KREG per warp-uniform round
-    const int rfar = __reduce_max_sync(0xffffffffu, (unsigned)((nfar + KREG - 1) / KREG));
-    if (done && level >= gap && rfar > 0) wait_level(done, level - gap, limit, timeout);
-    for (int c = 0; c < rfar; ++c) {
-      int jj[KREG];
-      VV vv[KREG];
-      X xv[KREG];
-#pragma unroll
-      for (int k2 = 0; k2 < KREG; ++k2) {
-        const int idx = c * KREG + k2;
-        const bool ok = idx < nfar;
-        const int e = first + idx * V;
-        jj[k2] = ok ? (int)cols[e] : -1;
-        vv[k2] = ok ? AR::val(vals[e]) : VV(0);
-      }
-      load_ready<AR, KREG>(jj, xv, out, backoff, limit, timeout);
-#pragma unroll
-      for (int k2 = 0; k2 < KREG; ++k2) AR::add(acc, k2, vv[k2], xv[k2]);
-    }
-    AR::gather(acc, V, Vmax);
-    // near entries (leader lanes), KNEAR per round; under the timeout-path
-    // test the tile first waits for level L - 1, whose barrier then expects
-    // one arrival more than it gets
-    if (pad && done && level >= 1) wait_level(done, level - 1, limit, timeout);
-    const int near0 = first - nnear;
-    const int rnear = __reduce_max_sync(0xffffffffu, (unsigned)((nnear + KNEAR - 1) / KNEAR));
-    for (int c = 0; c < rnear; ++c) {
-      int jj[KNEAR];
-      VV vv[KNEAR];
-      X xv[KNEAR];
-#pragma unroll
-      for (int k2 = 0; k2 < KNEAR; ++k2) {
-        const int idx = c * KNEAR + k2;
-        const bool ok = idx < nnear;
-        jj[k2] = ok ? (int)cols[near0 + idx] : -1;
-        vv[k2] = ok ? AR::val(vals[near0 + idx]) : VV(0);
-      }
-      load_ready<AR, KNEAR>(jj, xv, out, backoff, limit, timeout);
-#pragma unroll
-      for (int k2 = 0; k2 < KNEAR; ++k2)
-        if (jj[k2] >= 0) AR::add_near(acc, vv[k2], xv[k2]);
-    }
-    if (leader) out[row] = AR::finish(acc, dvr);
+    const int level =
+        solve_tile<AR, KREG, KNEAR>(base, lane, in, out, unit, backoff, limit, timeout, wait_far, wait_near);
     __syncwarp();  // the slot of tile k-1 is free: refill it with tile k+SLOTS-1
     if (done) {
       // The tile arrives on level L's barrier once its values are stored and
@@ -395,6 +425,61 @@ __device__ __forceinline__ void sweep_staged(const unsigned char* __restrict__ s
       if (lane == 0) mbar_arrive(done + level);
     }
     issue(k + SLOTS - 1);
+  }
+  cp_async_wait<0>();
+}
+
+// Level-synchronous sweep of a block: the W sweeping warps step through the
+// block's nlev levels together, one named barrier (bar.sync 1, W warps) per
+// level, which also makes the level's stored values visible to all of them.
+// Every entry of a level-L tile lies at a level below L and is final when
+// the tile starts, so no wait sits inside a level and nothing spins: a level
+// costs its slowest tile plus one barrier.  Tiles are staged as in
+// sweep_staged; lend[l] (shared memory) ends level l's tiles, so a warp
+// knows which of its tiles belong to a level without waiting for their
+// bytes.  Each warp passes exactly nlev barriers.
+template <typename TS, typename TC, bool FF, int SLOTS, int KREG, int KNEAR>
+__device__ __forceinline__ void sweep_levels(const unsigned char* __restrict__ stream, const int64_t* toff_s,
+                                             int ntile, const int32_t* lend, int nlev, unsigned char* ring,
+                                             int slot_bytes,
+                                             volatile typename SweepArith<TS, TC, FF>::X* in,
+                                             volatile typename SweepArith<TS, TC, FF>::X* out, bool unit,
+                                             int* timeout, int W, int limit) {
+  using AR = SweepArith<TS, TC, FF>;
+  const int lane = lane_id(), w = threadIdx.x >> 5;
+  if (w >= W) return;
+  const int nk = ntile > w ? (ntile - w + W - 1) / W : 0;  // tiles of this warp
+  auto issue = [&](int k) {
+    if (k < nk) {
+      const int t = w + k * W;
+      const int64_t a = toff_s[t];
+      const int n16 = (int)((toff_s[t + 1] - a) >> 4);
+      if (n16 * 16 <= slot_bytes) {
+        unsigned char* dst = ring + (k % SLOTS) * slot_bytes;
+        const unsigned char* src = stream + a;
+        for (int c = lane; c < n16; c += 32) cp_async16(dst + 16 * c, src + 16 * c);
+      }
+    }
+    cp_async_commit();
+  };
+#pragma unroll
+  for (int d = 0; d < SLOTS - 1; ++d) issue(d);
+  auto none = [](int) {};
+  int k = 0;
+  for (int level = 0; level < nlev; ++level) {
+    const int tend = lend[level];
+    for (; k < nk && w + k * W < tend; ++k) {
+      const int t = w + k * W;
+      const int64_t a = toff_s[t];
+      const int bytes = (int)(toff_s[t + 1] - a);
+      cp_async_wait<SLOTS - 2>();
+      __syncwarp();
+      const unsigned char* base = bytes <= slot_bytes ? ring + (k % SLOTS) * slot_bytes : stream + a;
+      solve_tile<AR, KREG, KNEAR>(base, lane, in, out, unit, 0u, limit, timeout, none, none);
+      __syncwarp();
+      issue(k + SLOTS - 1);
+    }
+    asm volatile("bar.sync 1, %0;" ::"r"(W * 32) : "memory");
   }
   cp_async_wait<0>();
 }
@@ -434,7 +519,9 @@ __device__ __forceinline__ void update_staged_body(const TriSolve& M, const doub
   const int64_t tb0 = M.bwd_tile[b];
   const int ntb = (int)(M.bwd_tile[b + 1] - tb0);
   int64_t* toff_b = toff_f + ntf + 1;
-  uint64_t* done = M.level_wait ? reinterpret_cast<uint64_t*>(toff_f + M.max_tiles + 2) : nullptr;
+  uint64_t* done = M.level_wait == 1 ? reinterpret_cast<uint64_t*>(toff_f + M.max_tiles + 2) : nullptr;
+  const bool lsync = M.level_wait == 2;
+  int32_t* lend = reinterpret_cast<int32_t*>(toff_f + M.max_tiles + 2);  // level-synchronous: tile ends per level
   const int lf0 = M.lev_off_lo[b], nlf = M.lev_off_lo[b + 1] - lf0;  // levels of this block, forward
   const int lb0 = M.lev_off_up[b], nlb = M.lev_off_up[b + 1] - lb0;  // and backward
   for (int t = threadIdx.x; t <= ntf; t += blockDim.x) toff_f[t] = M.fwd_toff[tf0 + t];
@@ -442,6 +529,8 @@ __device__ __forceinline__ void update_staged_body(const TriSolve& M, const doub
   if (done)
     for (int t = threadIdx.x; t < nlf; t += blockDim.x)
       mbar_init(done + t, (unsigned)(M.fwd_ltiles[lf0 + t] + M.wait_pad));
+  if (lsync)
+    for (int t = threadIdx.x; t < nlf; t += blockDim.x) lend[t] = M.fwd_lend[lf0 + t];
   if (threadIdx.x == 0) timeout = 0;
   double rr = 0.0;
   if (mode == 0) {
@@ -466,9 +555,13 @@ __device__ __forceinline__ void update_staged_body(const TriSolve& M, const doub
   }
   const double rrb = block_sum(rr, sh);
   __syncthreads();
-  sweep_staged<TS, TC, FF, SLOTS, KREG, kNear>(M.fwd_stream, toff_f, ntf, ring, M.slot_bytes, yb, yf,
-                                               M.unit_lower != 0, &timeout, M.sweep_warps, (unsigned)M.backoff_ns,
-                                               done, M.wait_limit, M.wait_pad, M.far_gap);
+  if (lsync)
+    sweep_levels<TS, TC, FF, SLOTS, KREG, kNear>(M.fwd_stream, toff_f, ntf, lend, nlf, ring, M.slot_bytes, yb, yf,
+                                                 M.unit_lower != 0, &timeout, M.sweep_warps, M.wait_limit);
+  else
+    sweep_staged<TS, TC, FF, SLOTS, KREG, kNear>(M.fwd_stream, toff_f, ntf, ring, M.slot_bytes, yb, yf,
+                                                 M.unit_lower != 0, &timeout, M.sweep_warps, (unsigned)M.backoff_ns,
+                                                 done, M.wait_limit, M.wait_pad, M.far_gap);
   __syncthreads();
   for (int64_t i = threadIdx.x; i < e0 - s0; i += blockDim.x) yb[i] = S;
   if (done) {
@@ -477,10 +570,16 @@ __device__ __forceinline__ void update_staged_body(const TriSolve& M, const doub
     for (int t = threadIdx.x; t < nlb; t += blockDim.x)
       mbar_init(done + t, (unsigned)(M.bwd_ltiles[lb0 + t] + M.wait_pad));
   }
+  if (lsync)
+    for (int t = threadIdx.x; t < nlb; t += blockDim.x) lend[t] = M.bwd_lend[lb0 + t];
   __syncthreads();
-  sweep_staged<TS, TC, FF, SLOTS, KREG, kNear>(M.bwd_stream, toff_b, ntb, ring, M.slot_bytes, yf, yb, false,
-                                               &timeout, M.sweep_warps, (unsigned)M.backoff_ns, done, M.wait_limit,
-                                               M.wait_pad, M.far_gap);
+  if (lsync)
+    sweep_levels<TS, TC, FF, SLOTS, KREG, kNear>(M.bwd_stream, toff_b, ntb, lend, nlb, ring, M.slot_bytes, yf, yb,
+                                                 false, &timeout, M.sweep_warps, M.wait_limit);
+  else
+    sweep_staged<TS, TC, FF, SLOTS, KREG, kNear>(M.bwd_stream, toff_b, ntb, ring, M.slot_bytes, yf, yb, false,
+                                                 &timeout, M.sweep_warps, (unsigned)M.backoff_ns, done, M.wait_limit,
+                                                 M.wait_pad, M.far_gap);
   __syncthreads();
   double rz = 0.0, zq = 0.0;
   for (int64_t i = s0 + threadIdx.x; i < e0; i += blockDim.x) {
@@ -538,7 +637,7 @@ cudaError_t launch_staged(const TriSolve& M, const double* p, const double* q, d
                           double* pp, double* part, PcgState* s, int mode, cudaStream_t st) {
   constexpr size_t kTY = std::is_same<TC, ff_tag>::value ? 8 : sizeof(TC);
   const size_t need = staged_smem_bytes(M.max_block, kTY, kSweepWarps, M.slot_bytes, M.slots, M.max_tiles,
-                                        M.level_wait ? M.max_levels : 0);
+                                        M.level_wait != 0 ? M.max_levels : 0);
   auto kern = k_pcg_update_staged<TS, TC, SLOTS, KREG>;
   SDSL_CUDA_TRY((allow_max_dynamic_smem<k_pcg_update_staged<TS, TC, SLOTS, KREG>>()));
   kern<<<(unsigned)M.nblocks, kSweepWarps * 32, need, st>>>(M, p, q, x, r, z, pp, part, s, mode); count_launch();
@@ -593,6 +692,10 @@ cudaError_t batch_shape(const TriSolve& M, const BatchReq* reqs, const BatchItem
 cudaError_t batch_update(const TriSolve& M0, const BatchReq* reqs, const BatchItem* items, int nitems, int grid,
                          size_t smem, cudaStream_t st) {
   if (nitems <= 0) return cudaSuccess;
+  if (M0.prec == 16) {
+    if (M0.apply_prec == 32) return batch_shape<__nv_bfloat16, float>(M0, reqs, items, nitems, grid, smem, st);
+    return batch_shape<__nv_bfloat16, ff_tag>(M0, reqs, items, nitems, grid, smem, st);
+  }
   if (M0.prec == 64) return batch_shape<double, double>(M0, reqs, items, nitems, grid, smem, st);
   if (M0.apply_prec == 64) return batch_shape<float, double>(M0, reqs, items, nitems, grid, smem, st);
   if (M0.apply_prec == 48) return batch_shape<float, ff_tag>(M0, reqs, items, nitems, grid, smem, st);
@@ -602,7 +705,7 @@ cudaError_t batch_update(const TriSolve& M0, const BatchReq* reqs, const BatchIt
 size_t staged_smem_bytes_of(const TriSolve& M) {
   const size_t tc = M.apply_prec == 32 ? 4 : 8;
   return staged_smem_bytes(M.max_block, tc, kSweepWarps, M.slot_bytes, M.slots, M.max_tiles,
-                           M.level_wait ? M.max_levels : 0);
+                           M.level_wait != 0 ? M.max_levels : 0);
 }
 
 size_t staged_smem_bytes(int64_t max_block, size_t tc_size, int warps, int slot_bytes, int slots, int64_t max_tiles,
@@ -613,6 +716,10 @@ size_t staged_smem_bytes(int64_t max_block, size_t tc_size, int warps, int slot_
 
 cudaError_t update_staged(const TriSolve& M, const double* p, const double* q, double* x, double* r, double* z,
                           double* pp, double* part, PcgState* s, int mode, cudaStream_t st) {
+  if (M.prec == 16) {
+    if (M.apply_prec == 32) return launch_shape<__nv_bfloat16, float>(M, p, q, x, r, z, pp, part, s, mode, st);
+    return launch_shape<__nv_bfloat16, ff_tag>(M, p, q, x, r, z, pp, part, s, mode, st);
+  }
   if (M.prec == 64) return launch_shape<double, double>(M, p, q, x, r, z, pp, part, s, mode, st);
   if (M.apply_prec == 64) return launch_shape<float, double>(M, p, q, x, r, z, pp, part, s, mode, st);
   if (M.apply_prec == 48) return launch_shape<float, ff_tag>(M, p, q, x, r, z, pp, part, s, mode, st);

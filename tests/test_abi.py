@@ -50,7 +50,7 @@ def test_host_only_entry_points(lib):
     assert lib.sdsl_setup(None, 1, 1, None, None, None, None, ctypes.byref(h)) == sdsl.ERR_ARG
     assert h.value is None
     # option validation happens before any device work
-    o.factor_prec = 16
+    o.factor_prec = 8
     assert lib.sdsl_setup(ctypes.byref(o), 1, 1, None, None, None, None, ctypes.byref(h)) == sdsl.ERR_ARG
     assert b"factor_prec" in lib.sdsl_last_error()
 

@@ -116,15 +116,46 @@ def test_block_beyond_staged_limit():
 def test_staged_readiness_modes_agree(prec):
     """The staged sweeps with per-value readiness and with per-level counters
     compute every row in the same order: bit-identical solutions and counts,
-    and the FP64 form meets the oracle's bars."""
+    and the FP64 form meets the oracle's bars (the autotuner is off: it would
+    time each option set on its own and may pick another product form)."""
     prob = CASES["c2-5pct"]()
-    g1 = run_bj(prob, prec, solve_kernel=3, sweep_wait=1)
-    g2 = run_bj(prob, prec, solve_kernel=3, sweep_wait=2)
+    shape = dict(solve_kernel=3, sweep_lane_entries=16, sweep_far_gap=3, tune=0)
+    g1 = run_bj(prob, prec, sweep_wait=1, **shape)
+    g2 = run_bj(prob, prec, sweep_wait=2, **shape)
     assert g1["stats"]["iters"] == g2["stats"]["iters"]
     assert np.array_equal(g1["x"], g2["x"])
     if prec == 64:
         ref_state, ref = oracle.bj_solve(prob)
         check_solution(prob, ref_state, ref, g2)
+
+
+@pytest.mark.parametrize("prec,E", [(64, 8), (32, 4), (32, 16)])
+def test_level_synchronous_sweep_agrees(prec, E):
+    """The level-synchronous sweep (one named barrier per level, every entry
+    of a tile summed as far) computes each row in the order of the per-value
+    protocol on the same tiles (far gap 1): bit-identical solutions and
+    counts; the solve meets the oracle's bars (FP64 factors, and FP32
+    factors under the float-float apply)."""
+    prob = CASES["c2-5pct"]()
+    g1 = run_bj(prob, prec, solve_kernel=3, sweep_wait=1, sweep_far_gap=1, sweep_lane_entries=E, tune=0)
+    g3 = run_bj(prob, prec, solve_kernel=3, sweep_wait=3, sweep_lane_entries=E, tune=0)
+    assert g3["stats"]["sweep_shape"] == [E, 1]
+    assert g1["stats"]["iters"] == g3["stats"]["iters"]
+    assert np.array_equal(g1["x"], g3["x"])
+    ref_state, ref = oracle.bj_solve(prob)
+    check_solution(prob, ref_state, ref, g3)
+
+
+def test_level_synchronous_sweep_edge_blocks():
+    """Level-synchronous sweeps on single-row, empty-level-free ragged blocks
+    and one block holding every row: same solution as the per-value protocol."""
+    for bp in ([0, 1, 2, 50, 51, 300], [0, 300]):
+        prob = W.config1(m=300, n=750)
+        prob.block_ptr = np.asarray(bp, dtype=np.int64)
+        g1 = run_bj(prob, 64, solve_kernel=3, sweep_wait=1, sweep_far_gap=1, sweep_lane_entries=2, tune=0)
+        g3 = run_bj(prob, 64, solve_kernel=3, sweep_wait=3, sweep_lane_entries=2, tune=0)
+        assert g1["stats"]["status"] == 0 and g3["stats"]["status"] == 0
+        assert np.array_equal(g1["x"], g3["x"])
 
 
 @pytest.mark.parametrize("form", [1, 2, 3])
