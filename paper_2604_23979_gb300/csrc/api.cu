@@ -649,17 +649,25 @@ cudaError_t product(sdsl_handle h, const double* y, double* out) {
   return spmv(h->A, y, out, h->st);
 }
 
+// The product of a BiCGSTAB pass: the factored form returns at once when the
+// solve has stopped (the explicit form always runs).
+cudaError_t pass_product(sdsl_handle h, const double* y, double* out) {
+  if (h->A.factored) return factored_product(h->A, y, out, nullptr, h->state, 2, h->st);
+  return spmv(h->A, y, out, h->st);
+}
+
 // One BiCGSTAB pass (bicgstab.cu).  The mode-0 PCG update computes
 // x += alpha ph, s = r - alpha v (in r), sh = M^{-1} s (in z) and ||s||^2
-// with its convergence test; v is kept in q.
+// with its convergence test; v is kept in q.  Every kernel of a pass returns
+// at once after the solve has stopped, so graphs of many passes waste little.
 sdsl_status enqueue_bicg_iteration(sdsl_handle h) {
   const int64_t N = h->N;
   TRY_CUDA(bicg_direction(N, h->r, h->q, h->p, h->state, h->bicg, h->st));
-  TRY_CUDA(precond_apply(h->M, h->p, h->ph, nullptr, h->part_blk, h->state, 2, h->st));
-  TRY_CUDA(product(h, h->ph, h->q));
+  TRY_CUDA(precond_apply(h->M, h->p, h->ph, nullptr, h->part_blk, h->state, 3, h->st));
+  TRY_CUDA(pass_product(h, h->ph, h->q));
   TRY_CUDA(bicg_alpha(N, h->rt, h->q, h->state, h->bicg, h->st));
   TRY_CUDA(pcg_update_precond(h->M, h->ph, h->q, h->x, h->r, h->z, h->part_blk, h->state, h->st));
-  TRY_CUDA(product(h, h->z, h->tv));
+  TRY_CUDA(pass_product(h, h->z, h->tv));
   TRY_CUDA(bicg_omega(N, h->tv, h->r, h->state, h->bicg, h->st));
   TRY_CUDA(bicg_finish(N, h->z, h->tv, h->rt, h->x, h->r, h->state, h->bicg, h->st));
   return SDSL_OK;
@@ -770,10 +778,7 @@ sdsl_status plan_sell(sdsl_handle h) {
 
 sdsl_status build_graph(sdsl_handle h) {
   destroy_graph(h);
-  // BiCGSTAB: the apply and the products of the passes captured after the
-  // converged one still run (only the scalar steps return early), so its
-  // graphs are kept short.
-  const int G = h->method == SDSL_BJ_BICGSTAB ? std::min(h->opt.graph_iters, 4) : h->opt.graph_iters;
+  const int G = h->opt.graph_iters;
   if (G <= 0) return SDSL_OK;
   cudaGraph_t g = nullptr;
   const long long before = launches_so_far();

@@ -264,7 +264,8 @@ cudaError_t spmv(const SpmvPlan& A, const double* x, double* y, cudaStream_t st)
 cudaError_t time_spmv(const SpmvPlan& A, const double* x, double* y, int reps, float* ms, cudaStream_t st);
 // q = A p, partial p^T q; last CTA: alpha = rho/pq, iters++.
 // q = A (theta o (A^T p)) + rho p through the scratch A.u (n entries); with
-// pcg = 1 also the partial p^T q and, in the last CTA, alpha = rho/pq, iters++.
+// pcg = 1 also the partial p^T q and, in the last CTA, alpha = rho/pq, iters++;
+// with pcg = 2 the product alone, skipped once s->done is set.
 cudaError_t factored_product(const SpmvPlan& A, const double* p, double* q, double* part, PcgState* s, int pcg,
                              cudaStream_t st);
 int product_occupancy(int kind, int lanes);
@@ -283,7 +284,7 @@ size_t sf_smem_bytes(int64_t max_block, size_t tc_size);
 // p = z + beta p
 cudaError_t pcg_direction(int64_t n, const double* z, double* p, PcgState* s, cudaStream_t st);
 // z = M^{-1} r (no update).  mode 1: also p_out = z, s->rho = r^T z, s->rr =
-// ||r||^2 (PCG start / restart); mode 2: z only.
+// ||r||^2 (PCG start / restart); mode 2: z only; mode 3: z only, skipped once s->done is set.
 cudaError_t precond_apply(const TriSolve& M, const double* r, double* z, double* p_out, double* part, PcgState* s,
                           int mode, cudaStream_t st);
 // t = b - A x, ||t||^2 -> s->tr; if write_r, r = t.

@@ -217,7 +217,7 @@ __global__ void __launch_bounds__(kThreads) k_a_u_dot(int64_t m, const int64_t* 
       loc = __fma_rn(p[i], qi, loc);
     }
   }
-  if (!pcg) return;
+  if (pcg != 1) return;
   const double tot = block_sum(loc, sh);
   if (threadIdx.x == 0) part[blockIdx.x] = tot;
   if (last_block(&s->ticket[0])) {
@@ -344,7 +344,7 @@ __global__ void __launch_bounds__(kThreads) k_pcg_update(TriSolve M, const doubl
                                                          double* __restrict__ r, double* __restrict__ z,
                                                          double* __restrict__ pp, double* __restrict__ part,
                                                          PcgState* __restrict__ s, int mode) {
-  if (mode == 0 && s->done) return;
+  if ((mode == 0 || mode == 3) && s->done) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double sh[kThreads / 32];
   const int b = blockIdx.x;
@@ -535,7 +535,7 @@ __global__ void __launch_bounds__(1024) k_pcg_update_sf(TriSolve M, const double
                                                         double* __restrict__ r, double* __restrict__ z,
                                                         double* __restrict__ pp, double* __restrict__ part,
                                                         PcgState* __restrict__ s, int mode) {
-  if (mode == 0 && s->done) return;
+  if ((mode == 0 || mode == 3) && s->done) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double sh[32];
   __shared__ int timeout;

@@ -45,7 +45,7 @@ __device__ __forceinline__ void update_epilogue(const TriSolve& M, double rrb, d
     part[2 * nb + b] = zqb;
     if (timed_out) s->err = 1;
   }
-  if (mode == 2) return;
+  if (mode >= 2) return;
   if (last_block(&s->ticket[2], (unsigned)nb)) {
     if (threadIdx.x < 32) {
       const double rrt = warp_fixed_sum(part, nb);

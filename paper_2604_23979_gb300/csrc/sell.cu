@@ -132,8 +132,9 @@ __global__ void __launch_bounds__(kSellThreads) k_sell_at_theta(SellMat S, const
   sell_at_theta_body(S, theta, p, u, (int)blockIdx.x, (int)gridDim.x);
 }
 
-// q = A u + rho p on the SELL copy of A; with pcg: partial p^T q per CTA, the
-// last CTA of the grid sums the partials in CTA order and sets alpha, iters.
+// q = A u + rho p on the SELL copy of A; with pcg 1: partial p^T q per CTA, the
+// last CTA of the grid sums the partials in CTA order and sets alpha, iters;
+// pcg 2: the product alone, skipped once the solve has stopped.
 __device__ __forceinline__ void sell_a_u_dot_body(const SellMat& S, const double* __restrict__ u, double rho,
                                                   const double* __restrict__ p, double* __restrict__ q,
                                                   double* __restrict__ part, PcgState* __restrict__ s, int pcg,
@@ -153,7 +154,7 @@ __device__ __forceinline__ void sell_a_u_dot_body(const SellMat& S, const double
       loc = __fma_rn(p[i], qi, loc);
     }
   }
-  if (!pcg) return;
+  if (pcg != 1) return;
   const double tot = block_sum(loc, sh);
   if (threadIdx.x == 0) part[vb] = tot;
   if (last_block(&s->ticket[0], (unsigned)vg)) {

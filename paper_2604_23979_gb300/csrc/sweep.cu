@@ -486,7 +486,7 @@ __device__ __forceinline__ void sweep_levels(const unsigned char* __restrict__ s
 
 // mode 0: x += alpha p, r -= alpha q, ||r||^2, z = M^{-1} r, r^T z, z^T q;
 // mode 1: z = M^{-1} r only, then rho = r^T z and p = z (start or restart);
-// mode 2: z = M^{-1} r only.
+// mode 2: z = M^{-1} r only; mode 3: mode 2, skipped once the solve has stopped.
 // Block b of one request (the whole CTA): the body of the single-request
 // kernel below and of the batched one (batch.cu's persistent launches walk a
 // table of (request, block) items through the same code).
@@ -608,7 +608,7 @@ __global__ void __launch_bounds__(kSweepWarps * 32) k_pcg_update_staged(TriSolve
                                                                         double* __restrict__ z, double* __restrict__ pp,
                                                                         double* __restrict__ part,
                                                                         PcgState* __restrict__ s, int mode) {
-  if (mode == 0 && s->done) return;
+  if ((mode == 0 || mode == 3) && s->done) return;
   update_staged_body<TS, TC, SLOTS, KREG>(M, p, q, x, r, z, pp, part, s, mode, (int)blockIdx.x);
 }
 
