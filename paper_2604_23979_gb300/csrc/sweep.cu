@@ -411,10 +411,14 @@ __device__ __forceinline__ void sweep_staged(const unsigned char* __restrict__ s
     const int bytes = (int)(toff_s[t + 1] - a);
     cp_async_wait<SLOTS - 2>();
     __syncwarp();
-    // A tile larger than a slot (one very long row) is read in place.
-    const unsigned char* base = bytes <= slot_bytes ? ring + (k % SLOTS) * slot_bytes : stream + a;
+    // A tile larger than a slot (one very long row) is read in place.  The
+    // two calls keep the usual path's pointers in the shared window.
     const int level =
-        solve_tile<AR, KREG, KNEAR>(base, lane, in, out, unit, backoff, limit, timeout, wait_far, wait_near);
+        bytes <= slot_bytes
+            ? solve_tile<AR, KREG, KNEAR>(ring + (k % SLOTS) * slot_bytes, lane, in, out, unit, backoff, limit,
+                                          timeout, wait_far, wait_near)
+            : solve_tile<AR, KREG, KNEAR>(stream + a, lane, in, out, unit, backoff, limit, timeout, wait_far,
+                                          wait_near);
     __syncwarp();  // the slot of tile k-1 is free: refill it with tile k+SLOTS-1
     if (done) {
       // The tile arrives on level L's barrier once its values are stored and
@@ -474,8 +478,11 @@ __device__ __forceinline__ void sweep_levels(const unsigned char* __restrict__ s
       const int bytes = (int)(toff_s[t + 1] - a);
       cp_async_wait<SLOTS - 2>();
       __syncwarp();
-      const unsigned char* base = bytes <= slot_bytes ? ring + (k % SLOTS) * slot_bytes : stream + a;
-      solve_tile<AR, KREG, KNEAR>(base, lane, in, out, unit, 0u, limit, timeout, none, none);
+      if (bytes <= slot_bytes)
+        solve_tile<AR, KREG, KNEAR>(ring + (k % SLOTS) * slot_bytes, lane, in, out, unit, 0u, limit, timeout, none,
+                                    none);
+      else
+        solve_tile<AR, KREG, KNEAR>(stream + a, lane, in, out, unit, 0u, limit, timeout, none, none);
       __syncwarp();
       issue(k + SLOTS - 1);
     }

@@ -46,7 +46,7 @@ def solve_alone(ps, prec):
     return out
 
 
-@pytest.mark.parametrize("prec", [32, 64])
+@pytest.mark.parametrize("prec", [32, 64, 16])
 def test_batch_equals_alone_bit_for_bit(prec):
     ps = problems()
     alone = solve_alone(ps, prec)
