@@ -59,12 +59,21 @@ enum { SDSL_FORM_CSR = 0, SDSL_FORM_NORMAL = 1, SDSL_FORM_AUGMENTED = 2 };
  * (two products and two preconditioner applies each); a pass whose first
  * half meets the tolerance ends there.  Breakdown (a zero or non-finite
  * rt.v, t.t, omega or rho) returns SDSL_ERR_BREAKDOWN. */
-enum { SDSL_BJ_PCG = 0, SDSL_BBD_GMRES = 1, SDSL_BJ_BICGSTAB = 2 };
+/* SDSL_BBD_GCR: restarted right-preconditioned GCR(m) (the paper's IGCR(m)
+ * paired with BBD in Sec. 4.2-4.3, read as the GCR of Eisenstat, Elman and
+ * Schultz 1983) with the BBD preconditioner of SDSL_BBD_GMRES, on the
+ * augmented form; m = restart.  Each step: p = M^{-1} r, q = K p, q and p
+ * orthogonalised against the step's earlier q (modified Gram-Schmidt, the
+ * same coefficients applied to p), normalised by ||q||; x += (q^T r) p,
+ * r -= (q^T r) q.  A cycle starts from the true residual.  stats.iters
+ * counts products; a zero or non-finite ||q|| returns SDSL_ERR_BREAKDOWN. */
+enum { SDSL_BJ_PCG = 0, SDSL_BBD_GMRES = 1, SDSL_BJ_BICGSTAB = 2, SDSL_BBD_GCR = 3 };
 enum { SDSL_MEM_HOST = 0, SDSL_MEM_DEVICE = 1 };
 
 typedef struct {
   int form;                      /* SDSL_FORM_*: what sdsl_setup receives */
-  int method;                    /* SDSL_BJ_PCG, SDSL_BJ_BICGSTAB (Sec. 2.3) or SDSL_BBD_GMRES (Sec. 2.4) */
+  int method;                    /* SDSL_BJ_PCG, SDSL_BJ_BICGSTAB (Sec. 2.3), SDSL_BBD_GMRES or
+                                    SDSL_BBD_GCR (Sec. 2.4) */
   int64_t nblocks;               /* number of diagonal blocks (Sec. 2.3 "partition") */
   const int64_t* block_ptr;      /* host, nblocks+1 row offsets of the blocks; NULL = equal split.
                                     Augmented form: row blocks of A (last entry = m - border) */

@@ -195,6 +195,7 @@ namespace {
 // Block Jacobi (Sec. 2.3) under either Krylov method: the same IC(0)
 // preconditioner, staged sweeps and product plans.
 inline bool bj_method(const sdsl_handle h) { return h->method == SDSL_BJ_PCG || h->method == SDSL_BJ_BICGSTAB; }
+inline bool bbd_method(int method) { return method == SDSL_BBD_GMRES || method == SDSL_BBD_GCR; }
 
 struct Scope {  // join the caller's stream on entry and exit
   sdsl_handle h;
@@ -1073,6 +1074,104 @@ sdsl_status gmres_solve(sdsl_handle h) {
   return fail(result, "GMRES reached maxit before the tolerance");
 }
 
+// Restarted right-preconditioned GCR(m) with the BBD preconditioner (the
+// paper's IGCR(m), Sec. 4.2-4.3).  A cycle starts from the true residual;
+// step j: p_j = M^{-1} r, q_j = K p_j; q_j is orthogonalised against the
+// cycle's q_0 .. q_{j-1} by modified Gram-Schmidt (a chain of mgs_step, each
+// coefficient taken after the previous subtraction), the same coefficients
+// are subtracted from p_j, and both are divided by ||q_j||; then
+// x += (q_j^T r) p_j, r -= (q_j^T r) q_j.  q_j lives in V, p_j in Z.
+sdsl_status gcr_solve(sdsl_handle h) {
+  const int64_t N = h->N;
+  const int m = std::max(1, h->opt.restart);
+  sdsl_stats& S = h->stats;
+  S.iters = 0;
+  S.restarts = 0;
+  unsigned int* ticket = reinterpret_cast<unsigned int*>(h->part + 152 * 32);
+  double* bn2 = h->scalars;
+  TRY_CUDA(norm2_sq(N, h->b, h->part, bn2, ticket, h->st));
+  double bnorm2 = 0.0;
+  TRY(to_host(h, &bnorm2, bn2, 1));
+  TRY(sync(h, "gcr init"));
+  if (bnorm2 == 0.0) {
+    TRY_CUDA(cudaMemsetAsync(h->x, 0, sizeof(double) * (size_t)N, h->st));
+    S.rel_res_true = S.rel_res_rec = 0.0;
+    S.status = SDSL_OK;
+    return SDSL_OK;
+  }
+  const double bnorm = std::sqrt(bnorm2), tol = h->opt.rtol * bnorm;
+  SpmvPlan A = h->A;
+  A.factored = 0;
+  double* c = h->gh;              // the step's Gram-Schmidt coefficients c_0 .. c_{j-1}
+  double* d2 = h->gh + m;         // ||q_j||^2
+  double* al = h->gh + m + 1;     // q_j^T r
+  double* rn2 = h->gh + m + 2;    // ||r||^2
+  double* dn = h->scalars + 1;    // ||q_j||, the divisor
+  int64_t it = 0;
+  double rnorm = 0.0, tnorm = 0.0;
+  bool fresh = false;  // tnorm belongs to the current x
+  sdsl_status result = SDSL_ERR_NOT_CONVERGED;
+  for (;;) {
+    TRY_CUDA(pcg_init_state(h->state, 0.0, 0, h->st));
+    TRY_CUDA(true_residual(A, h->b, h->x, h->r, h->part, h->state, 1, h->st));
+    TRY(to_host(h, h->h_state, h->state, 1));
+    TRY(sync(h, "gcr residual"));
+    tnorm = rnorm = std::sqrt(h->h_state->tr);
+    fresh = true;
+    if (tnorm <= tol) { result = SDSL_OK; break; }
+    if (it >= h->opt.maxit) break;
+    S.restarts += 1;
+    bool breakdown = false;
+    for (int j = 0; j < m && it < h->opt.maxit; ++j) {
+      double* pj = h->Z + (int64_t)j * N;
+      double* qj = h->V + (int64_t)j * N;
+      TRY(bbd_apply(h, h->r, pj));
+      TRY_CUDA(spmv(A, pj, qj, h->st));
+      ++it;
+      fresh = false;
+      for (int i = 0; i < j; ++i)
+        TRY_CUDA(mgs_step(N, qj, i ? h->V + (int64_t)(i - 1) * N : nullptr, i ? c + i - 1 : nullptr,
+                          h->V + (int64_t)i * N, h->gpart, c + i, h->st));
+      TRY_CUDA(mgs_step(N, qj, j ? h->V + (int64_t)(j - 1) * N : nullptr, j ? c + j - 1 : nullptr, nullptr,
+                        h->gpart, d2, h->st));
+      if (j > 0) TRY_CUDA(sub_multi(N, j, h->Z, N, c, pj, h->st));
+      double dd = 0.0;
+      TRY(to_host(h, &dd, d2, 1));
+      TRY(sync(h, "gcr norm"));
+      const double d = std::sqrt(dd);
+      if (!(d > 0.0) || !std::isfinite(d)) { breakdown = true; break; }
+      TRY(to_dev(h, dn, &d, 1));
+      TRY_CUDA(scale_to(N, dn, 1, qj, qj, h->st));
+      TRY_CUDA(scale_to(N, dn, 1, pj, pj, h->st));
+      TRY_CUDA(multidot(N, 1, qj, N, h->r, h->gpart, al, h->st));
+      TRY_CUDA(add_multi(N, 1, h->Z + (int64_t)j * N, N, al, h->x, h->st));
+      TRY_CUDA(sub_multi(N, 1, qj, N, al, h->r, h->st));
+      TRY_CUDA(norm2_sq(N, h->r, h->part, rn2, ticket, h->st));
+      double r2 = 0.0;
+      TRY(to_host(h, &r2, rn2, 1));
+      TRY(sync(h, "gcr step"));
+      rnorm = std::sqrt(r2);
+      if (rnorm <= tol) break;
+    }
+    if (breakdown) { result = SDSL_ERR_BREAKDOWN; break; }
+  }
+  if (!fresh) {  // the true residual of the final iterate
+    TRY_CUDA(pcg_init_state(h->state, 0.0, 0, h->st));
+    TRY_CUDA(true_residual(A, h->b, h->x, h->r, h->part, h->state, 0, h->st));
+    TRY(to_host(h, h->h_state, h->state, 1));
+    TRY(sync(h, "gcr final residual"));
+    tnorm = std::sqrt(h->h_state->tr);
+  }
+  S.iters = it;
+  S.restarts = std::max<int64_t>(0, S.restarts - 1);
+  S.rel_res_true = tnorm / bnorm;
+  S.rel_res_rec = rnorm / bnorm;
+  S.status = result;
+  if (result == SDSL_OK) return SDSL_OK;
+  if (result == SDSL_ERR_BREAKDOWN) return fail(result, "GCR breakdown: a direction with zero or non-finite norm");
+  return fail(result, "GCR reached maxit before the tolerance");
+}
+
 // Variable-width tile streams of the staged sweeps (both directions).
 // Rows of one level are packed into 32-lane tiles, each row with V lanes
 // (the smallest power of two with E*V >= its entry count, at most 32, E the
@@ -1335,7 +1434,7 @@ sdsl_status factor_impl(sdsl_handle h) {
   destroy_graph(h);
   h->factored = false;
   const int64_t N = h->N, nb = h->nblocks;
-  const int whole = h->method == SDSL_BBD_GMRES ? 1 : 0;
+  const int whole = bbd_method(h->method) ? 1 : 0;
   // Eq. (filter) + Eq. (diagcorr)
   TRY_CUDA(diag_values(N, h->s_rp, h->s_ci, h->s_v, h->dvals, h->st));
   TRY(h->pc.get(&h->p_rp, N + 1));
@@ -1463,7 +1562,7 @@ sdsl_status factor_impl(sdsl_handle h) {
     h->Ff = nullptr;
     h->dinvf = nullptr;
   }
-  if (h->method == SDSL_BBD_GMRES) {
+  if (bbd_method(h->method)) {
     if (f32) {
       TRY_CUDA(to_float(h->p_nnz, h->F, h->Ff, h->st));
       TRY_CUDA(to_float(N, h->dinv, h->dinvf, h->st));
@@ -1475,7 +1574,7 @@ sdsl_status factor_impl(sdsl_handle h) {
       TRY_CUDA(round_bf16(N, h->dinvf, h->st));
     }
   }
-  if (h->method == SDSL_BBD_GMRES) {
+  if (bbd_method(h->method)) {
     TRY(build_bbd(h));
     const int mres = std::max(1, h->opt.restart);
     TRY(h->pc.get(&h->V, (size_t)(mres + 1) * N));
@@ -1503,7 +1602,7 @@ sdsl_status factor_impl(sdsl_handle h) {
   M.lev_off_up = h->lev_off_up;
   M.lev_ptr_up = h->lev_ptr_up;
   M.lev_rows_up = h->lev_rows_up;
-  M.unit_lower = h->method == SDSL_BBD_GMRES ? 1 : 0;
+  M.unit_lower = bbd_method(h->method) ? 1 : 0;
   M.prec = b16 ? 16 : f32 ? 32 : 64;
   const double avg_half = N > 0 ? (double)(h->p_nnz - N) / (2.0 * (double)N) : 1.0;
   M.lanes = pow2_lanes(avg_half, 2.0);
@@ -1655,7 +1754,7 @@ sdsl_status factor_impl(sdsl_handle h) {
   h->stats.tau_used = tau;
   h->stats.ms_factor = elapsed(h);
   h->stats.nnz_precond = h->p_nnz;
-  h->stats.nnz_factor = h->method == SDSL_BBD_GMRES ? h->p_nnz : (h->p_nnz + N) / 2;
+  h->stats.nnz_factor = bbd_method(h->method) ? h->p_nnz : (h->p_nnz + N) / 2;
   h->stats.spmv_lanes = h->A.lanes;
   h->stats.product_lanes[0] = h->A.factored ? (h->A.sell ? -1 : h->A.at_lanes) : 0;
   h->stats.product_lanes[1] = h->A.factored ? (h->A.sell ? -1 : h->A.a_lanes) : 0;
@@ -2035,6 +2134,7 @@ sdsl_status solve_attempt(sdsl_handle h, int x0_zero, sdsl_stats* st) {
   if (x0_zero) TRY_CUDA(cudaMemsetAsync(h->x, 0, sizeof(double) * (size_t)h->N, h->st));
   else TRY_CUDA(cudaMemcpyAsync(h->x, h->x0, sizeof(double) * (size_t)h->N, cudaMemcpyDeviceToDevice, h->st));
   sdsl_status s = h->method == SDSL_BBD_GMRES      ? gmres_solve(h)
+                  : h->method == SDSL_BBD_GCR     ? gcr_solve(h)
                   : h->method == SDSL_BJ_BICGSTAB ? bicg_solve(h)
                                                   : pcg_solve(h, st);
   cudaEventRecord(h->ev_b, h->st);
@@ -2176,11 +2276,11 @@ sdsl_status sdsl_setup(const sdsl_options* opt, int64_t m, int64_t n, const int6
   if (!opt) return fail(SDSL_ERR_ARG, "options are NULL");
   if (m < 0 || n < 0 || m >= INT32_MAX || n >= INT32_MAX) return fail(SDSL_ERR_ARG, "m, n must be in [0, 2^31-1)");
   if (opt->form < SDSL_FORM_CSR || opt->form > SDSL_FORM_AUGMENTED) return fail(SDSL_ERR_ARG, "unknown form");
-  if (opt->method != SDSL_BJ_PCG && opt->method != SDSL_BBD_GMRES && opt->method != SDSL_BJ_BICGSTAB)
+  if (opt->method != SDSL_BJ_PCG && !bbd_method(opt->method) && opt->method != SDSL_BJ_BICGSTAB)
     return fail(SDSL_ERR_ARG, "unknown method");
   if (opt->factor_prec != 64 && opt->factor_prec != 32 && opt->factor_prec != 16)
     return fail(SDSL_ERR_ARG, "factor_prec must be 64, 32 or 16");
-  if (opt->factor_prec == 16 && opt->method == SDSL_BBD_GMRES)
+  if (opt->factor_prec == 16 && bbd_method(opt->method))
     return fail(SDSL_ERR_ARG, "BF16 factors are for the Block-Jacobi methods");
   if (opt->factor_prec == 16 && opt->apply_prec == 64)
     return fail(SDSL_ERR_ARG, "BF16 factors are applied in float-float (48) or FP32 (32) arithmetic");
@@ -2212,9 +2312,9 @@ sdsl_status sdsl_setup(const sdsl_options* opt, int64_t m, int64_t n, const int6
     return fail(SDSL_ERR_ARG, "tau, delta must be >= 0, rtol > 0, maxit >= 0");
   if (opt->form == SDSL_FORM_CSR && m != n) return fail(SDSL_ERR_ARG, "CSR form needs a square matrix");
   if (opt->form != SDSL_FORM_CSR && !theta) return fail(SDSL_ERR_ARG, "theta is NULL");
-  if (opt->form == SDSL_FORM_AUGMENTED && opt->method != SDSL_BBD_GMRES)
+  if (opt->form == SDSL_FORM_AUGMENTED && !bbd_method(opt->method))
     return fail(SDSL_ERR_ARG, "the augmented (indefinite) form needs the BBD-GMRES method");
-  if (opt->method == SDSL_BBD_GMRES && opt->form != SDSL_FORM_AUGMENTED)
+  if (bbd_method(opt->method) && opt->form != SDSL_FORM_AUGMENTED)
     return fail(SDSL_ERR_ARG, "BBD-GMRES is implemented for the augmented form");
   const int64_t nb = opt->nblocks < 1 ? 1 : opt->nblocks;
   const int64_t dimS = opt->form == SDSL_FORM_AUGMENTED ? m + n : m;
@@ -2612,7 +2712,7 @@ sdsl_status sdsl_export_levels(sdsl_handle h, int which, int32_t* nlev, int64_t*
 
 sdsl_status sdsl_export_schur(sdsl_handle h, double* sb) {
   if (!h || !sb) return fail(SDSL_ERR_ARG, "NULL argument");
-  if (h->method != SDSL_BBD_GMRES || !h->factored) return fail(SDSL_ERR_STATE, "no Schur complement (BBD, factored)");
+  if (!bbd_method(h->method) || !h->factored) return fail(SDSL_ERR_STATE, "no Schur complement (BBD, factored)");
   Scope scope(h);
   if (h->nbord > 0) TRY(to_host(h, sb, h->SB, h->nbord * h->nbord));
   return sync(h, "export schur");
@@ -2620,7 +2720,7 @@ sdsl_status sdsl_export_schur(sdsl_handle h, double* sb) {
 
 sdsl_status sdsl_export_schur_lu(sdsl_handle h, int32_t* ipiv, double* pivots) {
   if (!h) return fail(SDSL_ERR_ARG, "handle is NULL");
-  if (h->method != SDSL_BBD_GMRES || !h->factored) return fail(SDSL_ERR_STATE, "no Schur complement (BBD, factored)");
+  if (!bbd_method(h->method) || !h->factored) return fail(SDSL_ERR_STATE, "no Schur complement (BBD, factored)");
   Scope scope(h);
   const int64_t m = h->nbord;
   if (m == 0) return SDSL_OK;
@@ -2653,7 +2753,7 @@ sdsl_status sdsl_precond_apply(sdsl_handle h, const double* r, double* z) {
   if (!h || !r || !z) return fail(SDSL_ERR_ARG, "NULL argument");
   if (!h->factored) return fail(SDSL_ERR_STATE, "no preconditioner yet");
   Scope scope(h);
-  if (h->method == SDSL_BBD_GMRES) return bbd_apply(h, r, z);
+  if (bbd_method(h->method)) return bbd_apply(h, r, z);
   TRY_CUDA(precond_apply(h->M, r, z, nullptr, h->part_blk, h->state, 2, h->st));
   return SDSL_OK;
 }

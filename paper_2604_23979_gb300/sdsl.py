@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(HERE, "libsdsl.so")
 
 OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_BREAKDOWN, ERR_NOT_CONVERGED, ERR_TIMEOUT, ERR_STATE = range(8)
 FORM_CSR, FORM_NORMAL, FORM_AUGMENTED = 0, 1, 2
-BJ_PCG, BBD_GMRES, BJ_BICGSTAB = 0, 1, 2
+BJ_PCG, BBD_GMRES, BJ_BICGSTAB, BBD_GCR = 0, 1, 2, 3
 MEM_HOST, MEM_DEVICE = 0, 1
 
 

@@ -279,3 +279,84 @@ def test_bbd_exact_blocks_one_iteration():
     finally:
         sdsl.sdsl_free(h)
     assert st.status == 0 and st.iters == 1
+
+
+# ---- GCR(m) with the BBD preconditioner (the paper's IGCR(m), Sec. 4.2-4.3)
+
+def gcr_ref(p, ref, **kw):
+    args = dict(rtol=p.rtol, maxit=p.maxit, restart=p.restart)
+    args.update(kw)
+    return oracle.gcr(ref["K"], p.b, oracle.PRE_BBD, ref["P"], ref["F"], ref["kbp"], ref["lu"], ref["ipiv"], **args)
+
+
+def gcr_gpu(p, **over):
+    h, keep = gpu_setup(p, method=sdsl.BBD_GCR, **over)
+    try:
+        sdsl.sdsl_factor(h)
+        x = np.zeros(len(p.b))
+        st = sdsl.sdsl_solve(h, p.b, x, allow=(0, 4, 5))
+    finally:
+        sdsl.sdsl_free(h)
+    return x, st
+
+
+@pytest.mark.parametrize("k", [1, 2, 5, 12])
+def test_bbd_gcr_first_steps_match_oracle(k):
+    """Stopped after k steps (tolerance out of reach), the GPU iterate equals
+    the oracle's GCR iterate to rounding: every part of a step (the BBD
+    apply, the product, the Gram-Schmidt coefficients applied to q and p,
+    the normalisation, the x and r updates) is checked."""
+    p = kkt(seed=5)
+    ref = oracle_bbd(p)
+    res = gcr_ref(p, ref, maxit=k, rtol=1e-300)
+    assert res.status == oracle.NOT_CONVERGED and res.iters == k
+    x, st = gcr_gpu(p, maxit=k, rtol=1e-300)
+    assert st.status == 5 and st.iters == k
+    assert rel(x, res.x) <= 1e-9, rel(x, res.x)
+    assert abs(st.rel_res_rec - res.relres_rec) <= 1e-9 * max(1.0, res.relres_rec)
+
+
+@pytest.mark.parametrize("seed", [5, 3])
+def test_bbd_gcr_few_restarts(seed):
+    """theta in [0.1, 10], rho = 1: GCR(30) converges in a few cycles, where
+    the count is stable under rounding: true residual <= 1e-8 (oracle SpMV),
+    x within 1e-6 of the oracle's, count within max(1, 5 %)."""
+    p = kkt(seed=seed)
+    rng = np.random.default_rng(0)
+    p.theta = np.exp(rng.uniform(np.log(0.1), np.log(10.0), len(p.theta)))
+    p.rho = 1.0
+    ref = oracle_bbd(p)
+    res = gcr_ref(p, ref)
+    assert res.status == 0
+    x, st = gcr_gpu(p)
+    assert st.status == 0 and relres(ref["K"], x, p.b) <= p.rtol
+    assert rel(x, res.x) <= 1e-6
+    assert iters_close(st.iters, res.iters), (st.iters, res.iters)
+
+
+def test_bbd_gcr_mild_case_within_oracle_spread():
+    """The mildly conditioned KKT case needs dozens of restarted cycles, where
+    the count is chaotic: the GPU count lies within the oracle's own spread
+    under 1e-14 perturbations of b (widened by 5 %), and the solution meets
+    the residual and 1e-6 bars."""
+    p = kkt(seed=5)
+    ref = oracle_bbd(p)
+    res = gcr_ref(p, ref)
+    assert res.status == 0
+    x, st = gcr_gpu(p)
+    assert st.status == 0 and relres(ref["K"], x, p.b) <= p.rtol
+    assert rel(x, res.x) <= 1e-6
+    counts = [res.iters]
+    b0 = p.b.copy()
+    for k in range(1, 10):
+        p.b = b0 * (1 + 1e-14 * np.random.default_rng(k).standard_normal(len(b0)))
+        counts.append(gcr_ref(p, ref).iters)
+    p.b = b0
+    assert 0.95 * min(counts) <= st.iters <= 1.05 * max(counts), (st.iters, counts)
+
+
+def test_bbd_gcr_zero_rhs():
+    p = kkt(seed=5)
+    p.b = np.zeros_like(p.b)
+    x, st = gcr_gpu(p)
+    assert st.status == 0 and st.iters == 0 and not np.any(x)
