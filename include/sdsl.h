@@ -202,6 +202,8 @@ typedef struct {
   int64_t n, nnz_system, nnz_precond, nblocks, border;
   int64_t levels_lower, levels_upper;
   int factored;
+  int64_t device_bytes;       /* device memory the handle holds now (its arenas) */
+  int64_t peak_device_bytes;  /* the most it has held at once, temporaries of setup and factor included */
 } sdsl_info;
 
 /* Fill *o with the defaults: BJ-PCG, normal form, tau 1e-3, delta 1e-12,

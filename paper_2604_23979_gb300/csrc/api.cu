@@ -70,6 +70,10 @@ sdsl_status cuda_fail(cudaError_t e, const char* where) {
 struct Arena {
   std::vector<void*> ptrs;
   cudaStream_t st = nullptr;
+  int64_t own = 0;               // bytes this arena holds
+  int64_t* live = nullptr;       // the owner's running total and its peak (optional)
+  int64_t* peak = nullptr;
+  void track(int64_t* l, int64_t* p) { live = l; peak = p; }
   template <typename T>
   sdsl_status get(T** out, size_t count) {
     *out = nullptr;
@@ -79,11 +83,18 @@ struct Arena {
     if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync");
     ptrs.push_back(p);
     *out = static_cast<T*>(p);
+    own += (int64_t)(count * sizeof(T));
+    if (live) {
+      *live += (int64_t)(count * sizeof(T));
+      if (peak && *live > *peak) *peak = *live;
+    }
     return SDSL_OK;
   }
   void release() {
     for (void* p : ptrs) cudaFreeAsync(p, st);
     ptrs.clear();
+    if (live) *live -= own;
+    own = 0;
   }
 };
 
@@ -125,6 +136,7 @@ struct sdsl_handle_s {
   int form = 0, method = 0;
   int64_t m = 0, n = 0, N = 0;  // input rows/cols, system dimension
   Arena sys, pc;
+  int64_t live_bytes = 0, peak_bytes = 0;  // device memory held by the handle's arenas (and its peak)
   // input A (normal / augmented) and its transpose
   int64_t a_nnz = 0;
   int64_t *a_rp = nullptr, *at_rp = nullptr;
@@ -315,6 +327,7 @@ sdsl_status transpose_input(sdsl_handle h) {
   int64_t* cursor = nullptr;
   Arena tmp;
   tmp.st = h->st;
+  tmp.track(&h->live_bytes, &h->peak_bytes);
   TRY(tmp.get(&cursor, h->n + 1));
   TRY_CUDA(transpose_csr(h->m, h->n, h->a_rp, h->a_ci, h->a_v, h->at_rp, h->at_ci, h->at_v, h->scan_scratch, h->st));
   TRY_CUDA(transpose_fill(h->m, h->n, h->a_rp, h->a_ci, h->a_v, h->at_rp, h->at_ci, h->at_v, cursor, h->st));
@@ -328,6 +341,7 @@ sdsl_status form_normal(sdsl_handle h) {
   int32_t* long_rows = nullptr;
   Arena tmp;
   tmp.st = h->st;
+  tmp.track(&h->live_bytes, &h->peak_bytes);
   TRY(tmp.get(&long_rows, m));
   TRY_CUDA(normal_symbolic_count(m, h->a_rp, h->a_ci, h->at_rp, h->at_ci, h->s_rp, long_rows, h->flag + 1, h->st));
   int nlong = 0;
@@ -361,6 +375,7 @@ sdsl_status form_augmented(sdsl_handle h, const int64_t* rbp, const int64_t* cbp
   int64_t *d_rbp, *d_cbp, *pos;
   Arena tmp;
   tmp.st = h->st;
+  tmp.track(&h->live_bytes, &h->peak_bytes);
   TRY(tmp.get(&d_rbp, nb + 1));
   TRY(tmp.get(&d_cbp, nb + 1));
   TRY(tmp.get(&pos, N));
@@ -737,6 +752,7 @@ sdsl_status build_sell(sdsl_handle h, int64_t nrows, const int64_t* rp, const in
   TRY(h->sys.get(&off, ns + 1));
   Arena tmp;
   tmp.st = h->st;
+  tmp.track(&h->live_bytes, &h->peak_bytes);
   struct Release {
     Arena& a;
     ~Release() { a.release(); }
@@ -846,6 +862,7 @@ sdsl_status build_bbd(sdsl_handle h) {
   TRY_CUDA(schur_init(m, h->b0, h->p_rp, h->p_ci, h->p_v, h->SB, h->st));
   Arena tmp;
   tmp.st = h->st;
+  tmp.track(&h->live_bytes, &h->peak_bytes);
   float* work;
   // Waves of blocks assembled at once: every block writes its own dense
   // contribution, then the wave's contributions are subtracted from S_B in
@@ -1206,6 +1223,7 @@ sdsl_status build_vtiles(sdsl_handle h, bool f32, int apply, int E, int gap, Are
   int64_t* d_len;
   Arena tmp;
   tmp.st = h->st;
+  tmp.track(&h->live_bytes, &h->peak_bytes);
   struct Release {
     Arena& a;
     ~Release() { a.release(); }
@@ -1409,6 +1427,7 @@ sdsl_status tune_sweep(sdsl_handle h, bool f32, int apply, int* E_out, int* gap_
   for (size_t c = 0; c < cand.size(); ++c) {
     Arena tmp;
     tmp.st = h->st;
+    tmp.track(&h->live_bytes, &h->peak_bytes);
     bool ok = false;
     sdsl_status s = build_vtiles(h, f32, apply, cand[c].first, cand[c].second, tmp, &ok);
     float ms = 1e30f;
@@ -1461,6 +1480,7 @@ sdsl_status factor_impl(sdsl_handle h) {
   int32_t *cnt, *fa, *fb, *nlev_d;
   Arena tmp;
   tmp.st = h->st;
+  tmp.track(&h->live_bytes, &h->peak_bytes);
   TRY(tmp.get(&cnt, N));
   TRY(h->pc.get(&h->row_lev_lo, N));
   TRY(h->pc.get(&h->row_lev_up, N));
@@ -2343,6 +2363,8 @@ sdsl_status sdsl_setup(const sdsl_options* opt, int64_t m, int64_t n, const int6
     return fail(SDSL_ERR_CUDA, "stream/event creation failed");
   }
   h->sys.st = h->pc.st = h->st;
+  h->sys.track(&h->live_bytes, &h->peak_bytes);
+  h->pc.track(&h->live_bytes, &h->peak_bytes);
   h->form = opt->form;
   h->method = opt->method;
   h->m = m;
@@ -2658,6 +2680,8 @@ sdsl_status sdsl_get_info(sdsl_handle h, sdsl_info* info) {
   info->levels_lower = h->factored ? h->tot_lo : 0;
   info->levels_upper = h->factored ? h->tot_up : 0;
   info->factored = h->factored ? 1 : 0;
+  info->device_bytes = h->live_bytes;
+  info->peak_device_bytes = h->peak_bytes;
   return SDSL_OK;
 }
 

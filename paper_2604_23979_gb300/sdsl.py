@@ -64,7 +64,7 @@ class sdsl_stats(C.Structure):
 class sdsl_info(C.Structure):
     _fields_ = [("n", C.c_int64), ("nnz_system", C.c_int64), ("nnz_precond", C.c_int64), ("nblocks", C.c_int64),
                 ("border", C.c_int64), ("levels_lower", C.c_int64), ("levels_upper", C.c_int64),
-                ("factored", C.c_int)]
+                ("factored", C.c_int), ("device_bytes", C.c_int64), ("peak_device_bytes", C.c_int64)]
 
 
 _lib = None

@@ -21,7 +21,9 @@ other.
 
 Admission by free HBM: the budget is the device's free memory at start
 (minus a reserve); a request is charged an upper-bound estimate of its
-device footprint (from the column counts of A) until it completes.  The
+device footprint (from the column counts of A) at admission, and its
+measured footprint (the handle's peak device bytes after its first
+factorization, plus its buffers) from then until it completes.  The
 queue is first-come first-served with backfill: when the head does not fit
 the remaining budget, a later request that fits may start.
 
@@ -102,16 +104,27 @@ class Scheduler:
         self.budget = int(budget_bytes)
         self.clock = clock
 
+    def recharge(self, i: int, cost: int) -> None:
+        """Replace request i's charge (admission estimate) by a measured one
+        while it runs; a lower charge frees budget for the queue at once."""
+        cv, state, costs = self._cv, self._state, self._costs
+        with cv:
+            state["used"] += int(cost) - costs[i]
+            costs[i] = int(cost)
+            cv.notify_all()
+
     def run(self, arrivals: Sequence[float], costs: Sequence[int],
             execute: Callable[[int, int], None]) -> tuple:
         n = len(arrivals)
         if any(c > self.budget for c in costs):
             raise ValueError("a request exceeds the whole memory budget")
+        costs = [int(c) for c in costs]
         order = sorted(range(n), key=lambda i: (arrivals[i], i))
         cv = threading.Condition()
         queue: List[int] = []          # arrived, not admitted (arrival order)
         free_slots = list(range(self.slots))
         state = {"used": 0, "running": 0, "max_running": 0, "error": None, "arrived": 0}
+        self._cv, self._state, self._costs = cv, state, costs
         admit = [0.0] * n
         done = [0.0] * n
         t0 = self.clock()
@@ -283,7 +296,8 @@ class GpuServer:
         self.n_batchers = max(1, batchers)
         self._batchers: List[_Batcher] = []
 
-    def _serve_one(self, req, stream, t0: float, slot: int = 0) -> List[SolveRecord]:
+    def _serve_one(self, req, stream, t0: float, slot: int = 0,
+                   recharge: Optional[Callable[[int], None]] = None) -> List[SolveRecord]:
         torch, sdsl = self.torch, self.sdsl
         prob = req.problem
         A = prob.A
@@ -302,6 +316,13 @@ class GpuServer:
             h = sdsl.sdsl_setup(o, A.nrows, A.ncols, d_rp, d_ci, d_v, d_th)
             try:
                 sdsl.sdsl_factor(h)
+                if recharge is not None:
+                    # the request's measured footprint replaces the estimate:
+                    # the handle's peak (temporaries of setup and factor
+                    # included) plus the input and solution buffers
+                    info = sdsl.sdsl_get_info(h)
+                    inputs = sum(t.numel() * t.element_size() for t in (d_rp, d_ci, d_v, d_th, d_b, d_x))
+                    recharge(int(1.1 * (info.peak_device_bytes + inputs)) + (8 << 20))
                 thetas = [None] + list(req.followups)
                 for k, th in enumerate(thetas):
                     if th is not None:
@@ -332,7 +353,8 @@ class GpuServer:
         t0_box = {}
 
         def execute(i: int, slot: int):
-            recs[i] = self._serve_one(requests[i], self.streams[slot], t0_box["t0"], slot)
+            recs[i] = self._serve_one(requests[i], self.streams[slot], t0_box["t0"], slot,
+                                      recharge=lambda c: sched.recharge(i, c))
 
         sched = Scheduler(self.slots, self.budget)
         self._batchers = ([_Batcher(self.sdsl, self.max_batch, self.graph_iters) for _ in range(self.n_batchers)]

@@ -68,3 +68,26 @@ def test_memory_budget_limits_the_mix():
     for t, _, _ in intervals:
         live = sum(c for a, d, c in intervals if a <= t < d)
         assert live <= budget
+
+
+def test_measured_footprint_below_the_admission_estimate():
+    """The handle's reported device memory: positive after setup, growing
+    with the factorization, its peak at least its current holding, and below
+    the column-count estimate the server admits a request on (so that the
+    measured charge, which replaces the estimate, frees budget)."""
+    rng = np.random.default_rng(5)
+    for m_hi in (5000, 40000):
+        req = W.serving_request(rng, 0.0, m_hi // 2, m_hi)
+        prob = req.problem
+        o, keep = sdsl.options_for(prob, factor_prec=32)
+        h = sdsl.sdsl_setup(o, prob.A.nrows, prob.A.ncols, prob.A.rowptr, prob.A.col, prob.A.val, prob.theta)
+        try:
+            i0 = sdsl.sdsl_get_info(h)
+            sdsl.sdsl_factor(h)
+            i1 = sdsl.sdsl_get_info(h)
+        finally:
+            sdsl.sdsl_free(h)
+        assert i0.device_bytes > 0 and i0.peak_device_bytes >= i0.device_bytes
+        assert i1.device_bytes > i0.device_bytes and i1.peak_device_bytes >= i1.device_bytes
+        est = serve.footprint_bytes(prob.A, 32)
+        assert i1.peak_device_bytes < est, (i1.peak_device_bytes, est)

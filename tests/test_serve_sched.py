@@ -84,3 +84,45 @@ def test_worker_error_is_raised():
 def test_request_larger_than_budget_is_rejected():
     with pytest.raises(ValueError):
         Scheduler(2, 10).run([0.0], [11], lambda i, s: None)
+
+
+def test_measured_charge_frees_budget_for_the_queue():
+    """A request admitted on an upper-bound estimate that recharges itself
+    with its measured footprint lets a waiting request start while it runs;
+    without the recharge the second request waits for the first to end."""
+    def run(recharge):
+        sched = Scheduler(4, 100)
+        started = {}
+
+        def execute(i, slot):
+            started[i] = time.perf_counter()
+            if i == 0:
+                if recharge:
+                    sched.recharge(0, 30)
+                time.sleep(0.4)
+            else:
+                time.sleep(0.05)
+
+        t0 = time.perf_counter()
+        admit, done, maxc = sched.run([0.0, 0.02], [90, 60], execute)
+        return admit, done, maxc
+
+    admit, done, maxc = run(True)
+    assert maxc == 2 and admit[1] < done[0]
+    admit, done, maxc = run(False)
+    assert maxc == 1 and admit[1] >= done[0]
+
+
+def test_recharge_above_the_estimate_holds_back_the_queue():
+    """A measured footprint larger than the estimate is charged in full."""
+    sched = Scheduler(4, 100)
+
+    def execute(i, slot):
+        if i == 0:
+            sched.recharge(0, 95)
+            time.sleep(0.3)
+        else:
+            time.sleep(0.02)
+
+    admit, done, maxc = sched.run([0.0, 0.05], [40, 40], execute)
+    assert maxc == 1 and admit[1] >= done[0]
