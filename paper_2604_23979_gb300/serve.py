@@ -125,6 +125,7 @@ class Scheduler:
         free_slots = list(range(self.slots))
         state = {"used": 0, "running": 0, "max_running": 0, "error": None, "arrived": 0}
         self._cv, self._state, self._costs = cv, state, costs
+        self.charged = []  # (time, budget in use) right after each admission
         admit = [0.0] * n
         done = [0.0] * n
         t0 = self.clock()
@@ -160,6 +161,7 @@ class Scheduler:
                             queue.pop(qi)
                             slot = free_slots.pop(0)
                             state["used"] += costs[i]
+                            self.charged.append((self.clock() - t0, state["used"]))
                             state["running"] += 1
                             state["max_running"] = max(state["max_running"], state["running"])
                             admit[i] = self.clock() - t0
@@ -357,6 +359,7 @@ class GpuServer:
                                       recharge=lambda c: sched.recharge(i, c))
 
         sched = Scheduler(self.slots, self.budget)
+        self.scheduler = sched
         self._batchers = ([_Batcher(self.sdsl, self.max_batch, self.graph_iters) for _ in range(self.n_batchers)]
                           if self.batch else [])
         t0_box["t0"] = time.perf_counter()

@@ -63,11 +63,12 @@ def test_memory_budget_limits_the_mix():
     for ra, rm in zip(alone, mixed):
         for sa, sm in zip(ra.solves, rm.solves):
             assert np.array_equal(sa.x, sm.x)
-    # the scheduler never charged more than the budget (checked on its record)
-    intervals = [(r.admitted_s, r.done_s, costs[r.index]) for r in mixed]
-    for t, _, _ in intervals:
-        live = sum(c for a, d, c in intervals if a <= t < d)
-        assert live <= budget
+    # the scheduler never charged more than the budget (its record after
+    # every admission), and the measured charges that replaced the
+    # estimates are smaller than them
+    sched = srv.scheduler
+    assert sched.charged and max(u for _, u in sched.charged) <= budget
+    assert all(0 < c < e for c, e in zip(sched._costs, costs))
 
 
 def test_measured_footprint_below_the_admission_estimate():
