@@ -73,3 +73,31 @@ def test_struct_layouts_match_header(lib):
                 part = re.sub(r"\[[^\]]*\]", "", part.strip())  # arrays: keep the name
                 names.append(re.findall(r"([A-Za-z_][A-Za-z_0-9]*)\s*$", part.strip())[0])
         assert names == [f for f, _ in cls._fields_], struct
+
+
+def test_enum_values_match_header():
+    """The binding's status, form, method and memory-space constants equal the
+    header's enumerators."""
+    from paper_2604_23979_gb300 import sdsl
+
+    text = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "sdsl.h")).read(), flags=re.S)
+    values = {}
+    for body in re.findall(r"enum\s*\{([^}]*)\}", text):
+        nxt = 0
+        for item in body.split(","):
+            item = item.strip()
+            if not item:
+                continue
+            name, _, val = item.partition("=")
+            nxt = int(val) if val.strip() else nxt
+            values[name.strip()] = nxt
+            nxt += 1
+    pairs = {"SDSL_OK": sdsl.OK, "SDSL_ERR_ARG": sdsl.ERR_ARG, "SDSL_ERR_OOM": sdsl.ERR_OOM,
+             "SDSL_ERR_CUDA": sdsl.ERR_CUDA, "SDSL_ERR_BREAKDOWN": sdsl.ERR_BREAKDOWN,
+             "SDSL_ERR_NOT_CONVERGED": sdsl.ERR_NOT_CONVERGED, "SDSL_ERR_TIMEOUT": sdsl.ERR_TIMEOUT,
+             "SDSL_ERR_STATE": sdsl.ERR_STATE, "SDSL_FORM_CSR": sdsl.FORM_CSR, "SDSL_FORM_NORMAL": sdsl.FORM_NORMAL,
+             "SDSL_FORM_AUGMENTED": sdsl.FORM_AUGMENTED, "SDSL_BJ_PCG": sdsl.BJ_PCG,
+             "SDSL_BBD_GMRES": sdsl.BBD_GMRES, "SDSL_BJ_BICGSTAB": sdsl.BJ_BICGSTAB, "SDSL_BBD_GCR": sdsl.BBD_GCR,
+             "SDSL_MEM_HOST": sdsl.MEM_HOST, "SDSL_MEM_DEVICE": sdsl.MEM_DEVICE}
+    for name, v in pairs.items():
+        assert values.get(name) == v, (name, values.get(name), v)
